@@ -1,0 +1,208 @@
+"""CPU FP64 oracle for the direction-restricted periodized DVM operator.
+
+TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline leg may import this package.  It shares no code
+with the CUDA implementation in ``paper_1201_3986_gb300``; the two meet only
+through the seeded inputs of ``synth``.
+
+The arithmetic lives in ``qdvm_oracle.c`` (plain C, FP64, Neumaier
+compensated sums, OpenMP over output points); this module compiles it with
+gcc on first use and marshals numpy arrays.
+
+Functions and the passages they follow:
+
+* ``lines(d, m)``            -- the line sets A^1 / A^2 of Section 3.2 (brute
+  force over [-m, m]^d).
+* ``q(...)`` / ``q_points``  -- eq. (DR) of Section 2.3 with the decoupled
+  weights of eq. (decoup) and the line restriction of eq. (decDVM).
+* ``jvp`` / ``vjp``          -- derivative of that quadratic form and the
+  transpose of its Jacobian (scattered term by term).
+* ``moments``                -- mass, momentum and energy of Section 2.1.
+* ``default_ntilde(N)``      -- Ntilde = floor(N / (3 + sqrt 2)), Section 4.
+
+Parity status: every function above is pinned by ``tests/test_oracle_*.py``
+(closed forms, invariants, brute force through the general DVM form of
+eq. (TypicalDVM), and the Fourier-side formula of eq. (sysDiff)).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qdvm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+KERNELS = {"unit": 0, "hp": 1}
+
+
+def build(force: bool = False) -> str:
+    """Compile qdvm_oracle.c into oracle/_build/liboracle.so (gcc, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", _SRC, "-o", tmp, "-lm"]
+    try:
+        subprocess.run(cmd, check=True, capture_output=True)
+    except (subprocess.CalledProcessError, FileNotFoundError):
+        cmd.remove("-fopenmp")
+        subprocess.run(cmd, check=True, capture_output=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        P = ctypes.POINTER
+        dbl_p = P(ctypes.c_double)
+        i64_p = P(ctypes.c_int64)
+        lib.oracle_default_ntilde.argtypes = [ctypes.c_int]
+        lib.oracle_default_ntilde.restype = ctypes.c_int
+        lib.oracle_lines.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_int), ctypes.c_int]
+        lib.oracle_lines.restype = ctypes.c_int
+        lib.oracle_terms_count.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        lib.oracle_terms_count.restype = ctypes.c_int
+        lib.oracle_q_points.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_double, dbl_p, i64_p, ctypes.c_int64, dbl_p, dbl_p, dbl_p, dbl_p]
+        lib.oracle_q_points.restype = ctypes.c_int
+        for name in ("oracle_jvp", "oracle_vjp"):
+            fn = getattr(lib, name)
+            fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                           ctypes.c_double, dbl_p, dbl_p, dbl_p]
+            fn.restype = ctypes.c_int
+        lib.oracle_moments.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dbl_p, dbl_p]
+        lib.oracle_moments.restype = ctypes.c_int
+        lib.oracle_max_threads.argtypes = []
+        lib.oracle_max_threads.restype = ctypes.c_int
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        lib.oracle_set_threads.restype = None
+        _lib = lib
+        return lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def default_ntilde(N: int) -> int:
+    return int(_load().oracle_default_ntilde(int(N)))
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+def set_threads(n: int) -> None:
+    _load().oracle_set_threads(int(n))
+
+
+def lines(d: int, m: int) -> np.ndarray:
+    """Primitive directions of [-m, m]^d up to sign, shape (count, d), ordered
+    by |e|_inf then lexicographically."""
+    lib = _load()
+    n = lib.oracle_lines(d, m, None, 0)
+    out = np.zeros((max(n, 1), d), dtype=np.int32)
+    lib.oracle_lines(d, m, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), n)
+    return out[:n]
+
+
+def terms_count(d: int, Ntilde: int, m: int) -> int:
+    return int(_load().oracle_terms_count(d, Ntilde, m))
+
+
+def _params(f: np.ndarray, L: float, Nbar: int, Ntilde: int | None):
+    d = f.ndim
+    N = f.shape[0]
+    if any(s != N for s in f.shape):
+        raise ValueError("f must be N^d")
+    Nt = default_ntilde(N) if Ntilde is None else int(Ntilde)
+    m = min(int(Nbar), Nt)
+    h = 2.0 * L / N
+    return d, N, Nt, m, h
+
+
+def q_points(f, L: float, Nbar: int, idx=None, kernel: str = "unit", Ntilde: int | None = None) -> dict:
+    """Q, gain, loss and scale = sum of |terms| at flat indices ``idx`` (all
+    points when None)."""
+    f = _f64(f)
+    d, N, Nt, m, h = _params(f, L, Nbar, Ntilde)
+    if idx is None:
+        n = f.size
+        ip = None
+    else:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        n = idx.size
+        ip = idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    Q, G, Lo, S = (np.zeros(n) for _ in range(4))
+    rc = _load().oracle_q_points(d, N, Nt, m, KERNELS[kernel], h, _dp(f), ip, n, _dp(Q), _dp(G), _dp(Lo), _dp(S))
+    if rc != 0:
+        raise RuntimeError(f"oracle_q_points failed ({rc})")
+    if idx is None:
+        Q, G, Lo, S = (a.reshape(f.shape) for a in (Q, G, Lo, S))
+    return {"Q": Q, "gain": G, "loss": Lo, "scale": S}
+
+
+def q(f, L: float, Nbar: int, kernel: str = "unit", Ntilde: int | None = None) -> dict:
+    return q_points(f, L, Nbar, None, kernel, Ntilde)
+
+
+def jvp(f, df, L: float, Nbar: int, kernel: str = "unit", Ntilde: int | None = None) -> np.ndarray:
+    f = _f64(f)
+    df = _f64(df)
+    d, N, Nt, m, h = _params(f, L, Nbar, Ntilde)
+    out = np.zeros_like(f)
+    rc = _load().oracle_jvp(d, N, Nt, m, KERNELS[kernel], h, _dp(f), _dp(df), _dp(out))
+    if rc != 0:
+        raise RuntimeError(f"oracle_jvp failed ({rc})")
+    return out
+
+
+def vjp(f, g, L: float, Nbar: int, kernel: str = "unit", Ntilde: int | None = None) -> np.ndarray:
+    f = _f64(f)
+    g = _f64(g)
+    d, N, Nt, m, h = _params(f, L, Nbar, Ntilde)
+    out = np.zeros_like(f)
+    rc = _load().oracle_vjp(d, N, Nt, m, KERNELS[kernel], h, _dp(f), _dp(g), _dp(out))
+    if rc != 0:
+        raise RuntimeError(f"oracle_vjp failed ({rc})")
+    return out
+
+
+def moments(Q, L: float) -> np.ndarray:
+    """h^d sum Q phi for phi = 1, v_0..v_{d-1}, |v|^2 (d + 2 values)."""
+    Q = _f64(Q)
+    d = Q.ndim
+    N = Q.shape[0]
+    out = np.zeros(d + 2)
+    rc = _load().oracle_moments(d, N, float(L), _dp(Q), _dp(out))
+    if rc != 0:
+        raise RuntimeError(f"oracle_moments failed ({rc})")
+    return out
+
+
+def rel_linf(Q, Qref, scale) -> float:
+    """max_i |Q_i - Qref_i| / max_i scale_i (error relative to the largest
+    sum of absolute terms, so that near-equilibrium data with Q ~ 0 stay
+    well posed)."""
+    Q = np.asarray(Q, dtype=np.float64)
+    Qref = np.asarray(Qref, dtype=np.float64)
+    s = float(np.max(np.abs(scale)))
+    if s == 0.0:
+        return float(np.max(np.abs(Q - Qref)))
+    return float(np.max(np.abs(Q - Qref)) / s)
