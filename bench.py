@@ -1,0 +1,369 @@
+"""Benchmark of the batched fast-summation collision operator.
+
+Workload (one step): evaluate Q(f) on 4096 independent 2D cells with N drawn
+uniformly from {16, 32, 48, 64} (seed 0), L = 8, Nbar = 8, unit kernel,
+each cell a two-Maxwellian mixture (random drifts in [-1,1]^2, temperatures
+in [0.5, 2]), FP32 arithmetic with compensated direction sums, plus the FP64
+moments (mass, momentum, energy) of every cell -- one persistent launch.
+
+Metric: Q evaluations per second counted in grid points, sum_cells N^d per
+second (whole job over all ranks).  Device time of exactly K steps between
+CUDA events, after W warm-up steps; 6 rotating copies of the batch (inputs +
+outputs 377 MB > 129 MB L2) so no step reads its inputs from L2.
+
+Also reported: an end-to-end figure through the public API with host
+buffers (pinned host -> device copy of f, evaluation, device -> host copy of
+Q and moments inside the timed region), the roofline of the dominant kernel,
+the plain single-cell FP64 GPU evaluation, the accuracy against the FP64
+oracle on sampled cells, the CPU oracle timed on the host cores, and the SM
+clocks sampled during the timed region.
+
+``--impl reference`` times the CPU oracle (the reference implementation of
+the method: direct FP64 sum) on a bounded sample of the same workload.
+Multi-GPU (torchrun): independent replicas, one batch per rank, no
+collective in the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "Q evals/s (cells×N^d pts/s) vs plain FP64 GPU; %HBM roofline; rel L∞ err vs FP64 oracle"
+UNIT = "pts/s"
+NS = (16, 32, 48, 64)
+N_CELLS = 4096
+NBAR = 8
+L = 8.0
+ROTATE = 6
+FLOPS_PER_POINT_PAIR = 11  # running windows W_e, W_e^perp, V_e (2 each) + assembly (5)
+ORACLE_SAMPLE_CELLS = 1024  # CPU baseline: ~10-30 s of oracle work
+REF_STEP_CELLS = 96  # reference arm: one step = the first 96 cells (~1 s)
+
+
+def workload_config(extra=None):
+    cfg = {"workload": "batched 2D DVM Q: 4096 cells, N~U{16,32,48,64} (seed 0), L=8, Nbar=8, unit kernel, "
+                       "two-Maxwellian mixtures, FP32 + compensated direction sums, FP64 moments",
+           "n_cells": N_CELLS, "Ns": list(NS), "Nbar": NBAR, "L": L, "prec": "f32_kahan",
+           "l2": f"{ROTATE} rotating input/output batch copies (> 129 MB L2)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def oracle_sample(cells: int):
+    import oracle
+
+    b = synth.batch_2d(N_CELLS, Ns=NS, L=L, seed=0)
+    n = min(cells, b.n_cells)
+    f32 = b.f.astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    pts = 0
+    for c in range(n):
+        oracle.q(b.cell(c, f32), L, NBAR)
+        pts += int(b.Ns[c]) ** 2
+    dt = time.perf_counter() - t0
+    return pts / dt, pts, dt, oracle.max_threads(), n
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(args.ref_cells)
+    t_all = 0.0
+    pts_all = 0
+    cores = 1
+    for _ in range(args.steps):
+        v, pts, dt, cores, n = oracle_sample(args.ref_cells)
+        vals.append(v)
+        t_all += dt
+        pts_all += pts
+    value = pts_all / t_all
+    sample = f"first {args.ref_cells} cells of the 4096-cell batch per step (same N mix), FP64 direct sum"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_all / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config({"sample_cells": args.ref_cells}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ clocks
+
+class ClockSampler:
+    def __init__(self, index: int):
+        self.proc = None
+        self.path = None
+        self.index = index
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ GPU arm
+
+def run_gpu(args):
+    import torch
+
+    import paper_1201_3986_gb300 as q
+
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    b = synth.batch_2d(N_CELLS, Ns=NS, L=L, seed=0)
+    plans = [q.Plan(2, n, NBAR, L, kernel="unit") for n in NS]
+    idx = {n: i for i, n in enumerate(NS)}
+    cp = torch.tensor([idx[int(n)] for n in b.Ns], dtype=torch.int32, device=dev)
+    co = torch.tensor(b.offsets, dtype=torch.int64, device=dev)
+    f_host = torch.from_numpy(b.f.astype(np.float32))
+    fs = [f_host.to(dev) for _ in range(ROTATE)]
+    Qs = [torch.empty_like(fs[0]) for _ in range(ROTATE)]
+    Ms = [torch.empty((N_CELLS, 4), dtype=torch.float64, device=dev) for _ in range(ROTATE)]
+    wsb = q.batched_workspace_bytes(plans, N_CELLS, "f32_kahan")
+    wss = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    total_pts = int((b.Ns ** 2).sum())
+    point_pairs = sum(int(n) ** 2 * (p.n_lines // 2) for n, p in zip(b.Ns, [plans[idx[int(n)]] for n in b.Ns]))
+
+    def step(k):
+        q.qdvm_eval_batched(plans, cp, co, fs[k % ROTATE], "f32_kahan", out=Qs[k % ROTATE], moments=Ms[k % ROTATE],
+                            workspace=wss)
+
+    stream = torch.cuda.current_stream(dev)
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for k in range(args.steps):
+            step(k)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    ms_per_step = ms / args.steps
+    value = ws * total_pts * args.steps / (ms / 1e3)
+    launches = 2 * args.steps  # schedule + persistent evaluator per step
+
+    # dominant-kernel time alone (persistent evaluator), events on the launching stream
+    kt = []
+    for k in range(max(3, min(args.steps, 10))):
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(k)
+        z.record(stream)
+        torch.cuda.synchronize(dev)
+        kt.append(a.elapsed_time(z))
+    kernel_ms = float(np.median(kt))
+
+    # end to end through the public API with host buffers
+    f_pin = f_host.pin_memory()
+    Q_pin = torch.empty_like(f_pin).pin_memory()
+    M_pin = torch.empty((N_CELLS, 4), dtype=torch.float64).pin_memory()
+    fdev, Qdev, Mdev = fs[0], Qs[0], Ms[0]
+
+    def e2e_step():
+        fdev.copy_(f_pin, non_blocking=True)
+        q.qdvm_eval_batched(plans, cp, co, fdev, "f32_kahan", out=Qdev, moments=Mdev, workspace=wss)
+        Q_pin.copy_(Qdev, non_blocking=True)
+        M_pin.copy_(Mdev, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_e2e = max(3, min(args.steps, 20))
+    a.record(stream)
+    for _ in range(n_e2e):
+        e2e_step()
+    z.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = a.elapsed_time(z) / n_e2e
+    h2d = f_pin.numel() * 4
+    d2h = Q_pin.numel() * 4 + M_pin.numel() * 8
+
+    # plain single-cell FP64 GPU evaluation (one launch per cell, no batching)
+    n_fp64 = 256
+    f64_cells = [torch.tensor(b.cell(c).astype(np.float32).astype(np.float64), device=dev) for c in range(n_fp64)]
+    pl = [plans[idx[int(b.Ns[c])]] for c in range(n_fp64)]
+    wsf = [torch.empty(max(p.eval_workspace("f64"), 1), dtype=torch.uint8, device=dev) for p in plans]
+    outs = [torch.empty_like(x) for x in f64_cells]
+    for c in range(n_fp64):
+        q.qdvm_eval(pl[c], f64_cells[c], "f64", out=outs[c], workspace=wsf[idx[int(b.Ns[c])]])
+    torch.cuda.synchronize(dev)
+    a.record(stream)
+    for c in range(n_fp64):
+        q.qdvm_eval(pl[c], f64_cells[c], "f64", out=outs[c], workspace=wsf[idx[int(b.Ns[c])]])
+    z.record(stream)
+    torch.cuda.synchronize(dev)
+    fp64_pts = int((b.Ns[:n_fp64] ** 2).sum())
+    fp64_value = fp64_pts / (a.elapsed_time(z) / 1e3)
+
+    # accuracy of the timed path against the FP64 oracle (sampled cells) and the
+    # conservation defect of mass on every cell
+    import oracle
+
+    Qn = Qs[0].cpu().numpy().astype(np.float64)
+    Mn = Ms[0].cpu().numpy()
+    f32 = b.f.astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(1)
+    picks = [int(rng.choice(np.nonzero(b.Ns == n)[0])) for n in NS]
+    errs = []
+    for c in picks:
+        r = oracle.q(b.cell(c, f32), L, NBAR)
+        errs.append(oracle.rel_linf(b.cell(c, Qn), r["Q"], r["scale"]))
+    mass_rel = []
+    for c in picks:
+        r = oracle.q(b.cell(c, f32), L, NBAR)
+        h2 = (2 * L / b.Ns[c]) ** 2
+        mass_rel.append(abs(Mn[c, 0]) / (h2 * r["scale"].sum()))
+
+    hbm_peak, peak_kind = peaks()
+    alg_bytes = total_pts * (4 + 4) + N_CELLS * 4 * 8
+    achieved_gbs = alg_bytes / (kernel_ms / 1e3) / 1e9
+    alg_flops = FLOPS_PER_POINT_PAIR * point_pairs
+    sm_peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12
+    achieved_tflops = alg_flops / (kernel_ms / 1e3) / 1e12
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": workload_config({"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}),
+        "e2e": {"value": total_pts / (e2e_ms / 1e3) * ws, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": sm_peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / sm_peak_tflops, "traffic": None,
+                     "kernel": "k_fused2d_batched", "kernel_ms": kernel_ms,
+                     "note": "FP32 peak = 152 SMs x 128 lanes x 2 x 2.07 GHz; algorithmic flops = 11 per point-pair"},
+        "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved_gbs / hbm_peak, "peak_kind": f"of {peak_kind}",
+                         "alg_bytes": alg_bytes},
+        "fp64_single_cell": {"value": fp64_value, "unit": UNIT, "cells": n_fp64,
+                             "speedup_of_batched_f32": value / ws / fp64_value},
+        "accuracy": {"rel_linf_vs_fp64_oracle_max": max(errs), "cells_checked": picks,
+                     "mass_defect_rel_max": max(mass_rel)},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        v, pts, dt, cores, n = oracle_sample(args.ref_cells)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"first {n} cells of the batch ({pts} points, {dt:.1f} s), FP64 direct sum"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="qdvm", choices=["qdvm", "reference"])
+    ap.add_argument("--ref-cells", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        args.ref_cells = args.ref_cells or REF_STEP_CELLS
+        run_reference(args)
+    else:
+        args.ref_cells = args.ref_cells or ORACLE_SAMPLE_CELLS
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

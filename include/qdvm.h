@@ -1,0 +1,186 @@
+/*
+ * qdvm.h -- C ABI of the GB300 (sm_103a) fast summation library for the
+ * periodized, direction-restricted discrete-velocity Boltzmann operator.
+ *
+ * Operator (Mouhot, Pareschi, Rey, "Convolutive decomposition and fast
+ * summation methods for discrete-velocity approximations of the Boltzmann
+ * equation"):
+ *
+ *   Q_i = sum_{e in A_m} c_e [ W_e(i) P_e(i) - f_i V_e(i) ]           eq. (decD)
+ *   W_e(i) = sum_{0<|j|<=J_e} f_{i+je}              (k in eZ: alpha_p)  eq. (decDVM)
+ *   P_e(i) = sum_{l in e^perp, 0<|l|_inf<=Ntilde} f_{i+l}  (alpha'_p)   eq. (decDVM)
+ *   V_e(i) = sum_{0<|j|<=J_e} P_e(i+je)             (the beta(L,L) part) eq. (betaKL)
+ *
+ * which equals, term by term, eq. (DR) of Section 2.3 restricted to the
+ * pairs (k, l), k.l = 0, whose k lies on a line e with |e|_inf <= m:
+ *   Q_i = sum Gamma_{k,l} [f_{i+k} f_{i+l} - f_i f_{i+k+l}],
+ *   Gamma_{k,l} = a(k) = c_e (decoupled kernel of eq. (decoup), b = 1).
+ * Here m = min(Nbar, Ntilde), J_e = floor(Ntilde / |e|_inf), A_m is the set
+ * of lines through 0 with a primitive direction in [-m, m]^d (the Farey-type
+ * sets A^1, A^2 of Section 3.2), and
+ *   c_e = 1                       (QDVM_KERNEL_UNIT, constant kernel),
+ *   c_e = h^(2d-1) |e|_2          (QDVM_KERNEL_HP: a(k) = h^(2d-1)|k|/gcd(k),
+ *                                  2D Maxwell molecules / 3D hard spheres).
+ *
+ * Grid: N points per axis on the periodic box [-L, L)^d, h = 2L/N, node j at
+ * v_j = -L + j h; indices are taken modulo N.  Arrays are row-major N^d with
+ * the last axis fastest.  Default Ntilde = floor(N / (3 + sqrt 2)) (Section 4).
+ *
+ * Conventions for every entry point:
+ *   - Array pointers are DEVICE pointers owned by the caller unless a
+ *     parameter says "host".  f is read only and must not alias any output.
+ *   - prec selects the arithmetic: QDVM_F64 (f, Q are double), QDVM_F32 or
+ *     QDVM_F32_KAHAN (f, Q are float; KAHAN compensates the sum over
+ *     directions).  Moments are always double.
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Evaluation entry points enqueue kernels only: they allocate nothing,
+ *     never synchronise the host and may be captured in a CUDA graph.
+ *   - workspace is caller-owned device memory of at least the size that the
+ *     matching *_workspace query returns (may be NULL when that size is 0).
+ *   - Errors are returned as qdvm_status, never by aborting.  A launch error
+ *     is reported as QDVM_ERR_CUDA; qdvm_last_error() gives details for the
+ *     calling host thread.
+ */
+#ifndef QDVM_H
+#define QDVM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qdvm_plan_s* qdvm_plan_t;
+
+typedef enum {
+    QDVM_OK = 0,
+    QDVM_ERR_INVALID_ARG = 1,
+    QDVM_ERR_UNSUPPORTED = 2,
+    QDVM_ERR_OOM = 3,
+    QDVM_ERR_CUDA = 4,
+    QDVM_ERR_TIMEOUT = 5,
+    QDVM_ERR_BAD_PLAN = 6
+} qdvm_status;
+
+enum { QDVM_KERNEL_UNIT = 0, QDVM_KERNEL_HP = 1 };
+enum { QDVM_F64 = 0, QDVM_F32 = 1, QDVM_F32_KAHAN = 2 };
+/* Line-sum engines.  DIRECT: gathers of each window from an on-chip copy of
+ * the cell.  SCAN: running (prefix) sums along the lattice lines of e.
+ * AUTO lets the library (and qdvm_tune) choose. */
+enum { QDVM_ENGINE_AUTO = 0, QDVM_ENGINE_DIRECT = 1, QDVM_ENGINE_SCAN = 2 };
+
+/* Maximum number of distinct plans in one batched call. */
+#define QDVM_MAX_BATCH_PLANS 16
+
+/* ------------------------------------------------------------------ plans */
+
+/* Build a plan: enumerate the lines of A_m on the GPU (Section 3.2, sets A^1 /
+ * A^2; Remark 3.4(1)), their window lengths J_e and weights c_e, the 2D
+ * pairing e <-> e^perp (Remark 3.4(3)) and the 3D plane offset lists of
+ * e^perp inside [-Ntilde, Ntilde]^3 (eq. (decDVM), alpha'_p).
+ *   out     host pointer receiving the plan (owned by the caller, release
+ *           with qdvm_plan_destroy).
+ *   d       2 or 3.
+ *   N       points per axis; 2D: 4 <= N <= 256, 3D: 4 <= N <= 64.
+ *   Nbar    Farey order >= 1; values above Ntilde are clamped (m = Ntilde is
+ *           the unrestricted operator, eq. (DR)).
+ *   Ntilde  truncation (|k|_inf, |l|_inf <= Ntilde); -1 selects the default
+ *           floor(N/(3+sqrt 2)); must satisfy 1 <= Ntilde and 2 Ntilde < N.
+ *   L       half-width of the box, > 0 (h = 2L/N).
+ *   kernel  QDVM_KERNEL_UNIT or QDVM_KERNEL_HP.
+ *   engine  QDVM_ENGINE_*.
+ * Synchronises the current device once (plan creation is not a hot path).
+ * Errors: INVALID_ARG for out-of-range arguments, OOM, CUDA. */
+qdvm_status qdvm_plan_create(qdvm_plan_t* out, int d, int N, int Nbar, double L, int kernel);
+qdvm_status qdvm_plan_create_ex(qdvm_plan_t* out, int d, int N, int Nbar, int Ntilde, double L,
+                                int kernel, int engine);
+
+/* Release a plan and its device tables.  NULL is accepted. */
+qdvm_status qdvm_plan_destroy(qdvm_plan_t plan);
+
+/* Plan facts (any pointer may be NULL): dimension, N, Ntilde, m = min(Nbar,
+ * Ntilde), number of lines in A_m, number of (k, l) terms per output point
+ * (the direct-sum cost). */
+qdvm_status qdvm_plan_info(qdvm_plan_t plan, int* d, int* N, int* Ntilde, int* m, int* n_lines,
+                           int64_t* n_terms);
+
+/* Copy the line table to HOST arrays of n_lines entries: dirs (3 ints per
+ * line, unused components 0, first non-zero component positive, ordered by
+ * |e|_inf then lexicographically), J (window half-length), c (weight). */
+qdvm_status qdvm_plan_lines(qdvm_plan_t plan, int* dirs, int* J, double* c);
+
+/* Bytes of workspace that qdvm_eval, qdvm_jvp and qdvm_vjp need for this plan
+ * and precision (0 is a valid answer).  Errors: BAD_PLAN, INVALID_ARG,
+ * UNSUPPORTED (no engine for this plan and precision). */
+qdvm_status qdvm_eval_workspace(qdvm_plan_t plan, int prec, size_t* bytes);
+
+/* Bytes of workspace that the batched entry points (eval, jvp, vjp) need for
+ * n_cells cells over these plans at this precision. */
+qdvm_status qdvm_batched_workspace(const qdvm_plan_t* plans, int n_plans, int n_cells, int prec, size_t* bytes);
+
+/* ------------------------------------------------------------- evaluation */
+
+/* Q = Q(f) for one cell (eq. (decD); the path: W_e, P_e, V_e and the gain /
+ * loss assembly of every line, fused on chip).  f and Q hold N^d elements of
+ * the precision's type.  Deterministic: lines are summed in a fixed order. */
+qdvm_status qdvm_eval(qdvm_plan_t plan, const void* f, void* Q, int prec, void* workspace,
+                      size_t workspace_bytes, void* stream);
+
+/* Batched evaluation of many independent cells (space-inhomogeneous
+ * setting; Section 3.3 notes the decomposition is fully parallel) in one
+ * persistent launch.  All plans must have the same d.
+ *   plans       HOST array of n_plans plans (n_plans <= QDVM_MAX_BATCH_PLANS).
+ *   cell_plan   DEVICE int[n_cells]: plan index of each cell.
+ *   cell_offset DEVICE int64[n_cells]: element offset of each cell in f / Q.
+ *   f, Q        DEVICE arrays holding the cells back to back.
+ *   moments     DEVICE double[n_cells * (d+2)] or NULL: per cell
+ *               h^d sum_i Q_i phi(v_i), phi = 1, v_0..v_{d-1}, |v|^2
+ *               (Section 2.1), reduced in FP64 from the stored Q.
+ * Cells are scheduled largest first through an atomic work counter kept in
+ * the workspace (size from qdvm_batched_workspace); results do not depend on
+ * the schedule.  Cells whose plan index is out of range are skipped (their
+ * outputs are left untouched).  Overlapping calls that share a workspace
+ * race.  n_cells == 0 is a no-op. */
+qdvm_status qdvm_eval_batched(const qdvm_plan_t* plans, int n_plans, int n_cells, const int* cell_plan,
+                              const int64_t* cell_offset, const void* f, void* Q, double* moments,
+                              int prec, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Directional derivative dQ = Q'(f) df (Q is quadratic in f, eq. (DR)):
+ *   dQ = sum_e c_e [ W_e[df] P_e[f] + W_e[f] P_e[df] - df V_e[f] - f V_e[df] ]. */
+qdvm_status qdvm_jvp(qdvm_plan_t plan, const void* f, const void* df, void* dQ, int prec, void* workspace,
+                     size_t workspace_bytes, void* stream);
+
+/* Vector-Jacobian product grad = Q'(f)^T g.  The window and plane operators
+ * are symmetric on the torus, so
+ *   grad = sum_e c_e [ W_e[g P_e] - g V_e + P_e[ g W_e - W_e[g f] ] ]
+ * with W_e[x], P_e[x] the line window and plane sum of x. */
+qdvm_status qdvm_vjp(qdvm_plan_t plan, const void* f, const void* g, void* grad, int prec, void* workspace,
+                     size_t workspace_bytes, void* stream);
+
+/* Batched JVP / VJP with the same cell layout as qdvm_eval_batched. */
+qdvm_status qdvm_jvp_batched(const qdvm_plan_t* plans, int n_plans, int n_cells, const int* cell_plan,
+                             const int64_t* cell_offset, const void* f, const void* df, void* dQ, int prec,
+                             void* workspace, size_t workspace_bytes, void* stream);
+qdvm_status qdvm_vjp_batched(const qdvm_plan_t* plans, int n_plans, int n_cells, const int* cell_plan,
+                             const int64_t* cell_offset, const void* f, const void* g, void* grad, int prec,
+                             void* workspace, size_t workspace_bytes, void* stream);
+
+/* Moments of one cell: m[0..d+1] = h^d sum_i Q_i phi(v_i), phi = 1, v, |v|^2
+ * (Section 2.1), FP64 reduction of Q (double or float per prec).  m is a
+ * DEVICE array of d+2 doubles. */
+qdvm_status qdvm_moments(qdvm_plan_t plan, const void* Q, int prec, double* m, void* stream);
+
+/* --------------------------------------------------------------- utility */
+
+const char* qdvm_status_string(qdvm_status s);
+/* Detail of the last error on the calling host thread ("" if none). */
+const char* qdvm_last_error(void);
+/* Library version string. */
+const char* qdvm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QDVM_H */

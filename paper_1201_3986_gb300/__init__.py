@@ -1,0 +1,265 @@
+"""Python binding of the qdvm C ABI (include/qdvm.h).
+
+Argument marshalling only: every step of the evaluation runs in the CUDA
+kernels of ``libqdvm.so``.  PyTorch supplies device memory and the current
+stream; nothing here computes any part of the operator.  Importing this
+package loads the in-tree library and raises if it has not been built (there
+is no fallback).
+
+Names follow the C ABI: ``qdvm_plan_create``, ``qdvm_eval``,
+``qdvm_eval_batched``, ``qdvm_jvp``, ``qdvm_vjp``, ``qdvm_moments``.  ``Plan``
+wraps a plan handle, ``QdvmFunction`` exposes Q as a differentiable
+``torch.autograd.Function`` (backward = ``qdvm_vjp``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libqdvm.so")
+
+QDVM_KERNEL_UNIT, QDVM_KERNEL_HP = 0, 1
+QDVM_F64, QDVM_F32, QDVM_F32_KAHAN = 0, 1, 2
+QDVM_ENGINE_AUTO, QDVM_ENGINE_DIRECT, QDVM_ENGINE_SCAN = 0, 1, 2
+QDVM_MAX_BATCH_PLANS = 16
+
+KERNELS = {"unit": QDVM_KERNEL_UNIT, "hp": QDVM_KERNEL_HP}
+PRECS = {"f64": QDVM_F64, "f32": QDVM_F32, "f32_kahan": QDVM_F32_KAHAN}
+ENGINES = {"auto": QDVM_ENGINE_AUTO, "direct": QDVM_ENGINE_DIRECT, "scan": QDVM_ENGINE_SCAN}
+_DTYPE = {QDVM_F64: torch.float64, QDVM_F32: torch.float32, QDVM_F32_KAHAN: torch.float32}
+
+
+class QdvmError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        self.status = status
+        super().__init__(f"{where}: {detail}")
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"qdvm CUDA library not built ({LIB_PATH} missing); run "
+        "`python -c 'import __graft_entry__ as g; g.build()'` first")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_sz = ctypes.c_size_t
+_P = ctypes.POINTER
+
+
+def _sig(name, args):
+    fn = getattr(_lib, name)
+    fn.argtypes = args
+    fn.restype = ctypes.c_int
+    return fn
+
+
+_sig("qdvm_plan_create", [_P(_vp), _i, _i, _i, ctypes.c_double, _i])
+_sig("qdvm_plan_create_ex", [_P(_vp), _i, _i, _i, _i, ctypes.c_double, _i, _i])
+_sig("qdvm_plan_destroy", [_vp])
+_sig("qdvm_plan_info", [_vp, _P(_i), _P(_i), _P(_i), _P(_i), _P(_i), _P(ctypes.c_int64)])
+_sig("qdvm_plan_lines", [_vp, _P(_i), _P(_i), _P(ctypes.c_double)])
+_sig("qdvm_eval_workspace", [_vp, _i, _P(_sz)])
+_sig("qdvm_eval", [_vp, _vp, _vp, _i, _vp, _sz, _vp])
+_sig("qdvm_eval_batched", [_P(_vp), _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _sz, _vp])
+_sig("qdvm_jvp", [_vp, _vp, _vp, _vp, _i, _vp, _sz, _vp])
+_sig("qdvm_vjp", [_vp, _vp, _vp, _vp, _i, _vp, _sz, _vp])
+_sig("qdvm_batched_workspace", [_P(_vp), _i, _i, _i, _P(_sz)])
+_sig("qdvm_jvp_batched", [_P(_vp), _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _sz, _vp])
+_sig("qdvm_vjp_batched", [_P(_vp), _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _sz, _vp])
+_sig("qdvm_moments", [_vp, _vp, _i, _vp, _vp])
+_lib.qdvm_status_string.argtypes = [_i]
+_lib.qdvm_status_string.restype = ctypes.c_char_p
+_lib.qdvm_last_error.argtypes = []
+_lib.qdvm_last_error.restype = ctypes.c_char_p
+_lib.qdvm_version.argtypes = []
+_lib.qdvm_version.restype = ctypes.c_char_p
+
+
+def _check(status: int, where: str) -> None:
+    if status != 0:
+        s = _lib.qdvm_status_string(status).decode()
+        detail = _lib.qdvm_last_error().decode()
+        raise QdvmError(status, where, f"{s} ({detail})")
+
+
+def version() -> str:
+    return _lib.qdvm_version().decode()
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(device=None):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _prec(prec) -> int:
+    return PRECS[prec] if isinstance(prec, str) else int(prec)
+
+
+# ------------------------------------------------------------------- plans
+
+def qdvm_plan_create(d: int, N: int, Nbar: int, L: float, kernel="unit", Ntilde: int | None = None,
+                     engine="auto") -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    e = ENGINES[engine] if isinstance(engine, str) else int(engine)
+    _check(_lib.qdvm_plan_create_ex(ctypes.byref(h), d, N, Nbar, -1 if Ntilde is None else int(Ntilde),
+                                    float(L), k, e), "qdvm_plan_create")
+    return h
+
+
+class Plan:
+    """Owning wrapper of a qdvm plan (lines of A_m, windows, weights)."""
+
+    def __init__(self, d: int, N: int, Nbar: int, L: float, kernel="unit", Ntilde: int | None = None,
+                 engine="auto"):
+        self.handle = None
+        self.handle = qdvm_plan_create(d, N, Nbar, L, kernel, Ntilde, engine)
+        vals = [ctypes.c_int() for _ in range(5)]
+        nt = ctypes.c_int64()
+        _check(_lib.qdvm_plan_info(self.handle, *[ctypes.byref(v) for v in vals], ctypes.byref(nt)), "qdvm_plan_info")
+        self.d, self.N, self.Ntilde, self.m, self.n_lines = (v.value for v in vals)
+        self.n_terms = nt.value
+        self.L = float(L)
+        self.h = 2.0 * self.L / self.N
+        self.kernel = kernel
+
+    def lines(self):
+        """(dirs[n,3], J[n], c[n]) copied from the plan's tables."""
+        n = self.n_lines
+        dirs = np.zeros((n, 3), dtype=np.int32)
+        J = np.zeros(n, dtype=np.int32)
+        c = np.zeros(n, dtype=np.float64)
+        _check(_lib.qdvm_plan_lines(self.handle, dirs.ctypes.data_as(_P(_i)), J.ctypes.data_as(_P(_i)),
+                                    c.ctypes.data_as(_P(ctypes.c_double))), "qdvm_plan_lines")
+        return dirs[:, :self.d], J, c
+
+    def eval_workspace(self, prec) -> int:
+        b = ctypes.c_size_t()
+        _check(_lib.qdvm_eval_workspace(self.handle, _prec(prec), ctypes.byref(b)), "qdvm_eval_workspace")
+        return b.value
+
+    @property
+    def shape(self):
+        return (self.N,) * self.d
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.qdvm_plan_destroy(self.handle)
+            self.handle = None
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor | None:
+    if nbytes == 0:
+        return None
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+# -------------------------------------------------------------- evaluation
+
+def qdvm_eval(plan: Plan, f: torch.Tensor, prec="f64", out: torch.Tensor | None = None,
+              workspace: torch.Tensor | None = None) -> torch.Tensor:
+    p = _prec(prec)
+    if f.dtype != _DTYPE[p] or not f.is_cuda or not f.is_contiguous() or tuple(f.shape) != plan.shape:
+        raise ValueError(f"f must be a contiguous CUDA {_DTYPE[p]} tensor of shape {plan.shape}")
+    Q = torch.empty_like(f) if out is None else out
+    wsb = plan.eval_workspace(p)
+    ws = workspace if workspace is not None else _workspace(wsb, f.device)
+    _check(_lib.qdvm_eval(plan.handle, _ptr(f), _ptr(Q), p, _ptr(ws), 0 if ws is None else ws.numel(),
+                          _stream(f.device)), "qdvm_eval")
+    return Q
+
+
+def qdvm_moments(plan: Plan, Q: torch.Tensor, prec="f64") -> torch.Tensor:
+    p = _prec(prec)
+    m = torch.empty(plan.d + 2, dtype=torch.float64, device=Q.device)
+    _check(_lib.qdvm_moments(plan.handle, _ptr(Q), p, _ptr(m), _stream(Q.device)), "qdvm_moments")
+    return m
+
+
+def _plan_array(plans):
+    arr = (ctypes.c_void_p * len(plans))(*[p.handle.value for p in plans])
+    return arr
+
+
+def batched_workspace_bytes(plans, n_cells: int, prec) -> int:
+    b = ctypes.c_size_t()
+    _check(_lib.qdvm_batched_workspace(_plan_array(plans), len(plans), int(n_cells), _prec(prec), ctypes.byref(b)),
+           "qdvm_batched_workspace")
+    return b.value
+
+
+def qdvm_eval_batched(plans, cell_plan: torch.Tensor, cell_offset: torch.Tensor, f: torch.Tensor, prec="f32_kahan",
+                      out: torch.Tensor | None = None, moments: torch.Tensor | bool | None = True,
+                      workspace: torch.Tensor | None = None):
+    """Evaluate Q on a ragged batch of cells in one persistent launch.
+
+    Returns (Q, moments) where moments is an (n_cells, d+2) float64 tensor
+    (or None when ``moments`` is False)."""
+    p = _prec(prec)
+    n_cells = int(cell_plan.numel())
+    if cell_plan.dtype != torch.int32 or cell_offset.dtype != torch.int64:
+        raise ValueError("cell_plan must be int32 and cell_offset int64")
+    if f.dtype != _DTYPE[p] or not f.is_cuda or not f.is_contiguous():
+        raise ValueError(f"f must be a contiguous CUDA {_DTYPE[p]} tensor")
+    Q = torch.empty_like(f) if out is None else out
+    d = plans[0].d
+    mom = None
+    if isinstance(moments, torch.Tensor):
+        mom = moments
+    elif moments:
+        mom = torch.empty((n_cells, d + 2), dtype=torch.float64, device=f.device)
+    ws = workspace if workspace is not None else _workspace(batched_workspace_bytes(plans, n_cells, p), f.device)
+    arr = _plan_array(plans)
+    _check(_lib.qdvm_eval_batched(arr, len(plans), n_cells, _ptr(cell_plan), _ptr(cell_offset), _ptr(f), _ptr(Q),
+                                  _ptr(mom), p, _ptr(ws), 0 if ws is None else ws.numel(), _stream(f.device)),
+           "qdvm_eval_batched")
+    return Q, mom
+
+
+def qdvm_jvp(plan: Plan, f: torch.Tensor, df: torch.Tensor, prec="f64", out=None, workspace=None) -> torch.Tensor:
+    p = _prec(prec)
+    dQ = torch.empty_like(f) if out is None else out
+    wsb = plan.eval_workspace(p)
+    ws = workspace if workspace is not None else _workspace(wsb, f.device)
+    _check(_lib.qdvm_jvp(plan.handle, _ptr(f), _ptr(df), _ptr(dQ), p, _ptr(ws), 0 if ws is None else ws.numel(),
+                         _stream(f.device)), "qdvm_jvp")
+    return dQ
+
+
+def qdvm_vjp(plan: Plan, f: torch.Tensor, g: torch.Tensor, prec="f64", out=None, workspace=None) -> torch.Tensor:
+    p = _prec(prec)
+    gr = torch.empty_like(f) if out is None else out
+    wsb = plan.eval_workspace(p)
+    ws = workspace if workspace is not None else _workspace(wsb, f.device)
+    _check(_lib.qdvm_vjp(plan.handle, _ptr(f), _ptr(g), _ptr(gr), p, _ptr(ws), 0 if ws is None else ws.numel(),
+                         _stream(f.device)), "qdvm_vjp")
+    return gr
+
+
+class QdvmFunction(torch.autograd.Function):
+    """Q(f) with a hand-written adjoint: backward calls qdvm_vjp."""
+
+    @staticmethod
+    def forward(ctx, f, plan, prec):
+        ctx.plan = plan
+        ctx.prec = prec
+        ctx.save_for_backward(f)
+        return qdvm_eval(plan, f.contiguous(), prec)
+
+    @staticmethod
+    def backward(ctx, g):
+        (f,) = ctx.saved_tensors
+        return qdvm_vjp(ctx.plan, f, g.contiguous(), ctx.prec), None, None
+
+
+def collision(f: torch.Tensor, plan: Plan, prec="f64") -> torch.Tensor:
+    """Differentiable Q(f)."""
+    return QdvmFunction.apply(f, plan, prec)

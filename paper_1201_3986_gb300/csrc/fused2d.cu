@@ -1,0 +1,379 @@
+// Fused 2D evaluation of the restricted periodized DVM operator, one cell per
+// CTA, everything on chip.
+//
+// For a pair of orthogonal lines {e, e^perp} (Remark 3.4(3): in 2D the lines
+// of A_m come in such pairs, with c_e = c_{e^perp} for the unit and
+// Heintz-Panferov weights), eq. (decD) contributes
+//     2 c_e [ W_e(i) W_{e^perp}(i) - f_i V_e(i) ],
+//     W_e(i)  = sum_{0<|j|<=J} f(i + j e)            (alpha_p of eq. (decDVM))
+//     P(i)    = W_{e^perp}(i)                        (alpha'_p: e^perp ∩ box)
+//     V_e(i)  = sum_{0<|j|<=J} P(i + j e)            (beta(L,L) of eq. (betaKL))
+// with J = floor(Ntilde / |e|_inf) for both lines.
+//
+// Layout: the cell is copied into shared memory with a periodic halo of width
+// H = Ntilde on every side (padded row stride congruent to N mod 32, see
+// pad2d_stride), so every window gather is base + j*step without any modulo,
+// and a warp of 32 consecutive points reads 32 distinct banks for every
+// direction.  Each thread owns the points tid + k*blockDim.x and keeps their
+// accumulators in registers for all pairs; P goes through shared memory
+// (with its halo images) because V gathers it along e.
+#include <algorithm>
+
+#include "qdvm_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// Deterministic block reduction of NV doubles per thread; result in out[] of
+// thread 0.  Uses a fixed tree (shuffle-down, then warps in order).
+template <int NV>
+__device__ __forceinline__ void block_reduce_fixed(double (&v)[NV], double* red /* smem, 32*NV */) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) red[wid * NV + i] = v[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += red[w * NV + i];
+            v[i] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// One cell, pairs [pb, pe).  Writes Q (or a partial sum of Q) to qcell and,
+// when mom != nullptr, the FP64 moments of the stored values to mom[0..3].
+template <typename T, bool KAHAN, int PPT>
+__device__ __forceinline__ void fused2d_body(const int N, const int H, const int4* __restrict__ pairs,
+                                             const double* __restrict__ pair_c, const int pb, const int pe,
+                                             const double h, const double L, const T* __restrict__ fcell,
+                                             T* __restrict__ qcell, double* __restrict__ mom, T* __restrict__ sF,
+                                             T* __restrict__ sP, double* red) {
+    const int RS = pad2d_stride(N, H), R = N + 2 * H;
+    const int NT = blockDim.x, tid = threadIdx.x;
+    const int NN = N * N;
+
+    // periodic fill of the padded cell
+    for (int p = tid; p < R * R; p += NT) {
+        const int py = p / R, px = p - py * R;
+        int sy = py - H, sx = px - H;
+        sy += sy < 0 ? N : 0;
+        sy -= sy >= N ? N : 0;
+        sx += sx < 0 ? N : 0;
+        sx -= sx >= N ? N : 0;
+        sF[py * RS + px] = fcell[sy * N + sx];
+    }
+
+    int addr[PPT];
+    unsigned img[PPT];
+    T fk[PPT], acc[PPT], cmp[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int idx = tid + k * NT;
+        const int y = idx / N, x = idx - (idx / N) * N;
+        addr[k] = idx < NN ? (y + H) * RS + x + H : -1;
+        unsigned msk = 0;
+        if (idx < NN) {
+            // image (dy, dx) of point (y, x) lies in the padded window iff the
+            // shifted coordinates stay in [-H, N+H)
+            const bool oy[3] = {y >= N - H, true, y < H};
+            const bool ox[3] = {x >= N - H, true, x < H};
+#pragma unroll
+            for (int b = 0; b < 9; ++b)
+                if (b != 4 && oy[b / 3] && ox[b % 3]) msk |= 1u << b;
+        }
+        img[k] = msk;
+        acc[k] = T(0);
+        cmp[k] = T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) fk[k] = addr[k] >= 0 ? sF[addr[k]] : T(0);
+
+    for (int pr = pb; pr < pe; ++pr) {
+        const int4 e = pairs[pr];
+        const T c2 = (T)(2.0 * pair_c[pr]);
+        const int se = e.x * RS + e.y;   // +e       (axis 0 = rows, axis 1 = columns)
+        const int sp = -e.y * RS + e.x;  // +e^perp = (-e1, e0)
+        const int J = e.z;
+        T W[PPT], Pv[PPT];
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            W[k] = T(0);
+            Pv[k] = T(0);
+            const int a = addr[k];
+            if (a >= 0) {
+                T w = T(0), pp = T(0);
+                int o = se, q = sp;
+                for (int j = 0; j < J; ++j) {
+                    w += sF[a + o] + sF[a - o];
+                    pp += sF[a + q] + sF[a - q];
+                    o += se;
+                    q += sp;
+                }
+                W[k] = w;
+                Pv[k] = pp;
+                sP[a] = pp;
+                unsigned msk = img[k];
+                while (msk) {
+                    const int b = __ffs(msk) - 1;
+                    msk &= msk - 1;
+                    sP[a + (b / 3 - 1) * N * RS + (b % 3 - 1) * N] = pp;
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            const int a = addr[k];
+            if (a >= 0) {
+                T v = T(0);
+                int o = se;
+                for (int j = 0; j < J; ++j) {
+                    v += sP[a + o] + sP[a - o];
+                    o += se;
+                }
+                const T t = c2 * (W[k] * Pv[k] - fk[k] * v);
+                comp_add<T, KAHAN>(acc[k], cmp[k], t);
+            }
+        }
+        __syncthreads();
+    }
+
+    double m[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int idx = tid + k * NT;
+        if (idx < NN) {
+            const T q = KAHAN ? acc[k] + cmp[k] : acc[k];
+            qcell[idx] = q;
+            if (mom) {
+                const int y = idx / N, x = idx - (idx / N) * N;
+                const double v0 = -L + y * h, v1 = -L + x * h, qd = (double)q;
+                m[0] += qd;
+                m[1] += qd * v0;
+                m[2] += qd * v1;
+                m[3] += qd * (v0 * v0 + v1 * v1);
+            }
+        }
+    }
+    if (mom) {
+        block_reduce_fixed<4>(m, red);
+        if (tid == 0) {
+            const double h2 = h * h;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) mom[i] = h2 * m[i];
+        }
+    }
+}
+
+template <typename T>
+__host__ __device__ inline size_t buf_elems(int N, int H) {
+    return (size_t)pad2d_rows(N, H) * (size_t)pad2d_stride(N, H);
+}
+
+template <typename T, bool KAHAN, int PPT>
+__global__ void __launch_bounds__(kThreads) k_fused2d_single(PlanDev P, const T* __restrict__ f, T* __restrict__ out,
+                                                             int pairs_per_cta, size_t slot_stride) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32 * 4];
+    const size_t be = buf_elems<T>(P.N, P.Ntilde);
+    T* sF = reinterpret_cast<T*>(smem_raw);
+    T* sP = sF + be;
+    const int pb = blockIdx.x * pairs_per_cta;
+    const int pe = min(pb + pairs_per_cta, P.n_pairs);
+    fused2d_body<T, KAHAN, PPT>(P.N, P.Ntilde, P.pairs, P.pair_c, pb, pe, P.h, P.L, f, out + blockIdx.x * slot_stride,
+                                nullptr, sF, sP, red);
+}
+
+// Deterministic sum of S partial results (fixed order s = 0..S-1).
+template <typename T, bool KAHAN>
+__global__ void k_reduce_partials(const T* __restrict__ part, int S, int n, T* __restrict__ Q) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T s = T(0), c = T(0);
+    for (int k = 0; k < S; ++k) comp_add<T, KAHAN>(s, c, part[(size_t)k * n + i]);
+    Q[i] = KAHAN ? s + c : s;
+}
+
+template <typename T, bool KAHAN, int PPT>
+__global__ void __launch_bounds__(kThreads) k_fused2d_batched(BatchDev B, int n_cells, const int* __restrict__ cell_plan,
+                                                              const int64_t* __restrict__ cell_offset,
+                                                              const int* __restrict__ order, int* counter,
+                                                              const T* __restrict__ f, T* __restrict__ Q,
+                                                              double* __restrict__ moments) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32 * 4];
+    __shared__ int s_cell;
+    __shared__ PlanDev s_plan;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int c = atomicAdd(counter, 1);
+            s_cell = c < n_cells ? order[c] : -1;
+            if (s_cell >= 0) {
+                const int pi = cell_plan[s_cell];
+#pragma unroll
+                for (int q = 0; q < QDVM_MAX_BATCH_PLANS; ++q)
+                    if (q == pi) s_plan = B.p[q];
+            }
+        }
+        __syncthreads();
+        const int cell = s_cell;
+        if (cell < 0) break;
+        const PlanDev P = s_plan;
+        const int64_t off = cell_offset[cell];
+        T* sF = reinterpret_cast<T*>(smem_raw);
+        T* sP = sF + buf_elems<T>(P.N, P.Ntilde);
+        fused2d_body<T, KAHAN, PPT>(P.N, P.Ntilde, P.pairs, P.pair_c, 0, P.n_pairs, P.h, P.L, f + off, Q + off,
+                                    moments ? moments + (size_t)cell * 4 : nullptr, sF, sP, red);
+        __syncthreads();
+    }
+}
+
+template <typename T, bool KAHAN, int PPT>
+void set_smem_attr(size_t smem) {
+    cudaFuncSetAttribute(k_fused2d_single<T, KAHAN, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_fused2d_batched<T, KAHAN, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <typename T, bool KAHAN, int PPT>
+qdvm_status launch_single_t(const qdvm_plan_s* p, const T* f, T* Q, T* part, int S, int ppc, size_t smem,
+                            cudaStream_t st) {
+    set_smem_attr<T, KAHAN, PPT>(smem);
+    const PlanDev P = plan_dev(p);
+    const int n = p->N * p->N;
+    if (S == 1) {
+        k_fused2d_single<T, KAHAN, PPT><<<1, kThreads, smem, st>>>(P, f, Q, ppc, 0);
+    } else {
+        k_fused2d_single<T, KAHAN, PPT><<<S, kThreads, smem, st>>>(P, f, part, ppc, (size_t)n);
+        k_reduce_partials<T, KAHAN><<<(n + 255) / 256, 256, 0, st>>>(part, S, n, Q);
+    }
+    QDVM_LAUNCH_CHECK("fused2d single-cell launch");
+    return QDVM_OK;
+}
+
+template <typename T, bool KAHAN>
+qdvm_status dispatch_single(const qdvm_plan_s* p, const void* f, void* Q, void* ws, int S, int ppc, size_t smem,
+                            cudaStream_t st) {
+    const int ppt = (p->N * p->N + kThreads - 1) / kThreads;
+    const T* fi = static_cast<const T*>(f);
+    T* qo = static_cast<T*>(Q);
+    T* part = static_cast<T*>(ws);
+    if (ppt <= 1) return launch_single_t<T, KAHAN, 1>(p, fi, qo, part, S, ppc, smem, st);
+    if (ppt <= 4) return launch_single_t<T, KAHAN, 4>(p, fi, qo, part, S, ppc, smem, st);
+    if (ppt <= 9) return launch_single_t<T, KAHAN, 9>(p, fi, qo, part, S, ppc, smem, st);
+    return launch_single_t<T, KAHAN, 16>(p, fi, qo, part, S, ppc, smem, st);
+}
+
+void split_pairs(int n_pairs, int max_ctas, int* S, int* ppc) {
+    int s = std::max(1, std::min(n_pairs, max_ctas));
+    int per = (n_pairs + s - 1) / s;
+    *ppc = per;
+    *S = (n_pairs + per - 1) / per;
+}
+
+template <typename T, bool KAHAN, int PPT>
+qdvm_status launch_batched_t(const BatchDev& b, int n_cells, const int* cell_plan, const int64_t* cell_offset,
+                             const int* order, int* counter, const T* f, T* Q, double* moments, size_t smem,
+                             cudaStream_t st) {
+    set_smem_attr<T, KAHAN, PPT>(smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused2d_batched<T, KAHAN, PPT>, kThreads, smem);
+    per_sm = std::max(per_sm, 1);
+    const int grid = std::max(1, std::min(n_cells, per_sm * qdvm_num_sms()));
+    k_fused2d_batched<T, KAHAN, PPT><<<grid, kThreads, smem, st>>>(b, n_cells, cell_plan, cell_offset, order, counter,
+                                                                    f, Q, moments);
+    QDVM_LAUNCH_CHECK("fused2d batched launch");
+    return QDVM_OK;
+}
+
+template <typename T, bool KAHAN>
+qdvm_status dispatch_batched(const BatchDev& b, int max_ppt, int n_cells, const int* cell_plan,
+                             const int64_t* cell_offset, const int* order, int* counter, const void* f, void* Q,
+                             double* moments, size_t smem, cudaStream_t st) {
+    const T* fi = static_cast<const T*>(f);
+    T* qo = static_cast<T*>(Q);
+    if (max_ppt <= 1)
+        return launch_batched_t<T, KAHAN, 1>(b, n_cells, cell_plan, cell_offset, order, counter, fi, qo, moments, smem, st);
+    if (max_ppt <= 4)
+        return launch_batched_t<T, KAHAN, 4>(b, n_cells, cell_plan, cell_offset, order, counter, fi, qo, moments, smem, st);
+    if (max_ppt <= 9)
+        return launch_batched_t<T, KAHAN, 9>(b, n_cells, cell_plan, cell_offset, order, counter, fi, qo, moments, smem, st);
+    return launch_batched_t<T, KAHAN, 16>(b, n_cells, cell_plan, cell_offset, order, counter, fi, qo, moments, smem, st);
+}
+
+}  // namespace
+
+size_t fused2d_smem_bytes(int N, int H, int prec) {
+    const size_t es = prec == QDVM_F64 ? sizeof(double) : sizeof(float);
+    return 2 * buf_elems<float>(N, H) * es;
+}
+
+int fused2d_supported(int N, int H, int prec) {
+    if (N * N > 16 * kThreads) return 0;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return fused2d_smem_bytes(N, H, prec) + 2048 <= (size_t)optin;
+}
+
+size_t fused2d_single_workspace(const qdvm_plan_s* p, int prec) {
+    int S, ppc;
+    split_pairs(p->n_pairs, qdvm_num_sms(), &S, &ppc);
+    if (S <= 1) return 0;
+    const size_t es = prec == QDVM_F64 ? sizeof(double) : sizeof(float);
+    return (size_t)S * p->N * p->N * es;
+}
+
+qdvm_status fused2d_eval_single(const qdvm_plan_s* p, const void* f, void* Q, int prec, void* ws, size_t ws_bytes,
+                                cudaStream_t st) {
+    int S, ppc;
+    split_pairs(p->n_pairs, qdvm_num_sms(), &S, &ppc);
+    const size_t need = fused2d_single_workspace(p, prec);
+    if (need > 0 && (ws == nullptr || ws_bytes < need))
+        return qdvm_fail(QDVM_ERR_INVALID_ARG, "workspace too small for qdvm_eval");
+    const size_t smem = fused2d_smem_bytes(p->N, p->Ntilde, prec);
+    switch (prec) {
+        case QDVM_F64: return dispatch_single<double, false>(p, f, Q, ws, S, ppc, smem, st);
+        case QDVM_F32: return dispatch_single<float, false>(p, f, Q, ws, S, ppc, smem, st);
+        default: return dispatch_single<float, true>(p, f, Q, ws, S, ppc, smem, st);
+    }
+}
+
+qdvm_status fused2d_eval_batched(const BatchDev& b, int max_N, int max_H, int n_cells, const int* cell_plan,
+                                 const int64_t* cell_offset, const void* f, void* Q, double* moments, int prec,
+                                 void* ws, cudaStream_t st) {
+    // workspace: [counter (int, padded to 256 B)] [order: n_cells ints]
+    int* counter = static_cast<int*>(ws);
+    int* order = reinterpret_cast<int*>(static_cast<char*>(ws) + 256);
+    qdvm_status s = schedule_launch(b, n_cells, cell_plan, order, counter, st);
+    if (s != QDVM_OK) return s;
+    size_t smem = 0;
+    int max_ppt = 1;
+    for (int i = 0; i < b.n_plans; ++i) {
+        smem = std::max(smem, fused2d_smem_bytes(b.p[i].N, b.p[i].Ntilde, prec));
+        max_ppt = std::max(max_ppt, (b.p[i].N * b.p[i].N + kThreads - 1) / kThreads);
+    }
+    (void)max_N;
+    (void)max_H;
+    switch (prec) {
+        case QDVM_F64:
+            return dispatch_batched<double, false>(b, max_ppt, n_cells, cell_plan, cell_offset, order, counter, f, Q,
+                                                   moments, smem, st);
+        case QDVM_F32:
+            return dispatch_batched<float, false>(b, max_ppt, n_cells, cell_plan, cell_offset, order, counter, f, Q,
+                                                  moments, smem, st);
+        default:
+            return dispatch_batched<float, true>(b, max_ppt, n_cells, cell_plan, cell_offset, order, counter, f, Q,
+                                                 moments, smem, st);
+    }
+}

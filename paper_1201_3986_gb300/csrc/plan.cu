@@ -1,0 +1,426 @@
+// Plan construction: the line set A_m of Section 3.2 (Farey-type series
+// F^1 / F^2, lines through 0 in [-m, m]^d), the window half-lengths
+// J_e = floor(Ntilde / |e|_inf), the decoupled weights c_e of eq. (decoup),
+// the 2D pairing e <-> e^perp of Remark 3.4(3) and the 3D plane lists
+// e^perp ∩ [-Ntilde, Ntilde]^3 of eq. (decDVM).  Every table is computed by a
+// kernel; the host only sizes allocations.
+#include <math.h>
+
+#include <mutex>
+#include <string>
+
+#include "qdvm_internal.cuh"
+
+// ------------------------------------------------------------ error state
+
+static thread_local std::string g_last_error;
+
+void qdvm_set_error(const std::string& msg) { g_last_error = msg; }
+
+qdvm_status qdvm_fail(qdvm_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+qdvm_status qdvm_cuda_status(cudaError_t e, const char* where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return QDVM_ERR_OOM;
+    return QDVM_ERR_CUDA;
+}
+
+bool qdvm_plan_ok(const qdvm_plan_s* p) { return p != nullptr && p->magic == QDVM_PLAN_MAGIC; }
+
+extern "C" const char* qdvm_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* qdvm_status_string(qdvm_status s) {
+    switch (s) {
+        case QDVM_OK: return "ok";
+        case QDVM_ERR_INVALID_ARG: return "invalid argument";
+        case QDVM_ERR_UNSUPPORTED: return "unsupported configuration";
+        case QDVM_ERR_OOM: return "out of device memory";
+        case QDVM_ERR_CUDA: return "CUDA error";
+        case QDVM_ERR_TIMEOUT: return "timeout";
+        case QDVM_ERR_BAD_PLAN: return "bad plan handle";
+    }
+    return "unknown status";
+}
+
+extern "C" const char* qdvm_version(void) { return "qdvm 0.1 (sm_103a)"; }
+
+int qdvm_num_sms() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 1;
+    return n;
+}
+
+// ------------------------------------------------------------ device helpers
+
+__device__ __forceinline__ int iabs(int x) { return x < 0 ? -x : x; }
+
+__device__ __forceinline__ int gcd_dev(int a, int b) {
+    a = iabs(a);
+    b = iabs(b);
+    while (b) {
+        int t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// Candidate number idx of the lexicographic enumeration of [-n, n]^d
+// (first axis slowest).
+__device__ __forceinline__ void cand_vec(int idx, int d, int n, int v[3]) {
+    int w = 2 * n + 1;
+    v[0] = v[1] = v[2] = 0;
+    for (int a = d - 1; a >= 0; --a) {
+        v[a] = idx % w - n;
+        idx /= w;
+    }
+}
+
+// True if v is a canonical primitive direction on the shell |v|_inf == n.
+__device__ __forceinline__ bool is_line_rep(const int v[3], int d, int n) {
+    int linf = 0, g = 0, first = 0;
+    for (int a = 0; a < d; ++a) {
+        linf = max(linf, iabs(v[a]));
+        g = gcd_dev(g, v[a]);
+        if (first == 0) first = v[a];
+    }
+    return linf == n && g == 1 && first > 0;
+}
+
+// Block-wide exclusive scan of one int per thread (blockDim multiple of 32,
+// at most 1024).  Returns the exclusive prefix; *total gets the block sum.
+__device__ int block_exclusive_scan(int x, int* total) {
+    __shared__ int warp_sums[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_sums[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int s = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) warp_sums[lane] = s;  // inclusive warp prefix
+    }
+    __syncthreads();
+    int base = wid > 0 ? warp_sums[wid - 1] : 0;
+    int tot = warp_sums[nw - 1];
+    __syncthreads();
+    *total = tot;
+    return base + incl - x;
+}
+
+// One block per shell n = blockIdx.x + 1: number of line representatives.
+__global__ void k_shell_count(int d, int* counts) {
+    const int n = blockIdx.x + 1;
+    int w = 2 * n + 1, total = w * w;
+    if (d == 3) total *= w;
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    int local = 0;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        int v[3];
+        cand_vec(i, d, n, v);
+        local += is_line_rep(v, d, n) ? 1 : 0;
+    }
+    atomicAdd(&cnt, local);
+    __syncthreads();
+    if (threadIdx.x == 0) counts[blockIdx.x] = cnt;
+}
+
+// One block per shell: write the representatives of the shell in
+// lexicographic order at offsets[shell].
+__global__ void k_shell_emit(int d, const int* offsets, int4* lines) {
+    const int n = blockIdx.x + 1;
+    int w = 2 * n + 1, total = w * w;
+    if (d == 3) total *= w;
+    int base = offsets[blockIdx.x];
+    for (int c0 = 0; c0 < total; c0 += blockDim.x) {
+        int i = c0 + threadIdx.x;
+        int v[3] = {0, 0, 0};
+        bool ok = false;
+        if (i < total) {
+            cand_vec(i, d, n, v);
+            ok = is_line_rep(v, d, n);
+        }
+        int tot;
+        int r = block_exclusive_scan(ok ? 1 : 0, &tot);
+        if (ok) lines[base + r] = make_int4(v[0], v[1], v[2], 0);
+        base += tot;
+    }
+}
+
+// J_e and c_e per line.
+__global__ void k_line_tables(int d, int n_lines, int Ntilde, int kernel, double h, int4* lines, double* c) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_lines) return;
+    int4 e = lines[i];
+    int linf = max(iabs(e.x), max(iabs(e.y), iabs(e.z)));
+    e.w = Ntilde / linf;
+    lines[i] = e;
+    double w = 1.0;
+    if (kernel == QDVM_KERNEL_HP) {
+        double hp = 1.0;
+        for (int a = 0; a < 2 * d - 1; ++a) hp *= h;
+        double n2 = (double)e.x * e.x + (double)e.y * e.y + (double)e.z * e.z;
+        w = hp * sqrt(n2);
+    }
+    c[i] = w;
+}
+
+// 2D: keep e when it precedes its canonical partner e^perp = (-e1, e0)
+// lexicographically (both lie on the same shell |.|_inf).  Single block.
+__global__ void k_pairs(int n_lines, const int4* lines, const double* c, int4* pairs, double* pair_c, int cap,
+                        int* n_out) {
+    int base = 0;
+    for (int c0 = 0; c0 < n_lines; c0 += blockDim.x) {
+        int i = c0 + threadIdx.x;
+        bool keep = false;
+        int4 e = make_int4(0, 0, 0, 0);
+        if (i < n_lines) {
+            e = lines[i];
+            int p0 = -e.y, p1 = e.x;
+            if (p0 < 0 || (p0 == 0 && p1 < 0)) {
+                p0 = -p0;
+                p1 = -p1;
+            }
+            keep = (e.x < p0) || (e.x == p0 && e.y < p1);
+        }
+        int tot;
+        int r = block_exclusive_scan(keep ? 1 : 0, &tot);
+        if (keep && base + r < cap) {
+            pairs[base + r] = make_int4(e.x, e.y, e.w, 0);
+            pair_c[base + r] = c[i];
+        }
+        base += tot;
+    }
+    if (threadIdx.x == 0) *n_out = base;
+}
+
+// 3D: size of e^perp ∩ [-Nt, Nt]^3 \ {0} per line (one block per line).
+__global__ void k_plane_count(int n_lines, const int4* lines, int Nt, int* counts) {
+    const int4 e = lines[blockIdx.x];
+    const int w = 2 * Nt + 1, total = w * w * w;
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    int local = 0;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        int v[3];
+        cand_vec(i, 3, Nt, v);
+        bool nz = v[0] | v[1] | v[2];
+        local += (nz && v[0] * e.x + v[1] * e.y + v[2] * e.z == 0) ? 1 : 0;
+    }
+    atomicAdd(&cnt, local);
+    __syncthreads();
+    if (threadIdx.x == 0) counts[blockIdx.x] = cnt;
+}
+
+__global__ void k_plane_emit(int n_lines, const int4* lines, int Nt, const int* start, char4* plane) {
+    const int4 e = lines[blockIdx.x];
+    const int w = 2 * Nt + 1, total = w * w * w;
+    int base = start[blockIdx.x];
+    for (int c0 = 0; c0 < total; c0 += blockDim.x) {
+        int i = c0 + threadIdx.x;
+        int v[3] = {0, 0, 0};
+        bool ok = false;
+        if (i < total) {
+            cand_vec(i, 3, Nt, v);
+            bool nz = v[0] | v[1] | v[2];
+            ok = nz && (v[0] * e.x + v[1] * e.y + v[2] * e.z == 0);
+        }
+        int tot;
+        int r = block_exclusive_scan(ok ? 1 : 0, &tot);
+        if (ok) plane[base + r] = make_char4((signed char)v[0], (signed char)v[1], (signed char)v[2], 0);
+        base += tot;
+    }
+}
+
+// ------------------------------------------------------------ plan lifecycle
+
+static void plan_free(qdvm_plan_s* p) {
+    if (!p) return;
+    cudaFree(p->d_lines);
+    cudaFree(p->d_c);
+    cudaFree(p->d_pairs);
+    cudaFree(p->d_pair_c);
+    cudaFree(p->d_plane_start);
+    cudaFree(p->d_plane);
+    p->magic = 0;
+    delete p;
+}
+
+int qdvm_default_ntilde(int N) { return (int)floor((double)N / (3.0 + sqrt(2.0))); }
+
+static qdvm_status build_tables(qdvm_plan_s* p) {
+    const int d = p->d, m = p->m;
+    int* d_counts = nullptr;
+    int* d_offsets = nullptr;
+    int* d_tmp = nullptr;
+    qdvm_status st = QDVM_OK;
+    std::vector<int> counts(m), offsets(m);
+    auto fail = [&](qdvm_status s) {
+        cudaFree(d_counts);
+        cudaFree(d_offsets);
+        cudaFree(d_tmp);
+        return s;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&d_counts, m * sizeof(int))) != cudaSuccess) return fail(qdvm_cuda_status(e, "plan counts"));
+    if ((e = cudaMalloc(&d_offsets, m * sizeof(int))) != cudaSuccess) return fail(qdvm_cuda_status(e, "plan offsets"));
+    k_shell_count<<<m, 256>>>(d, d_counts);
+    if ((e = cudaMemcpy(counts.data(), d_counts, m * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return fail(qdvm_cuda_status(e, "k_shell_count"));
+    int total = 0;
+    for (int i = 0; i < m; ++i) {
+        offsets[i] = total;
+        total += counts[i];
+    }
+    p->n_lines = total;
+    if ((e = cudaMemcpy(d_offsets, offsets.data(), m * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(qdvm_cuda_status(e, "plan offsets upload"));
+    if ((e = cudaMalloc(&p->d_lines, total * sizeof(int4))) != cudaSuccess) return fail(qdvm_cuda_status(e, "lines"));
+    if ((e = cudaMalloc(&p->d_c, total * sizeof(double))) != cudaSuccess) return fail(qdvm_cuda_status(e, "c"));
+    k_shell_emit<<<m, 256>>>(d, d_offsets, p->d_lines);
+    k_line_tables<<<(total + 255) / 256, 256>>>(d, total, p->Ntilde, p->kernel, p->h, p->d_lines, p->d_c);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(qdvm_cuda_status(e, "line tables"));
+
+    p->h_lines.resize(total);
+    p->h_c.resize(total);
+    if ((e = cudaMemcpy(p->h_lines.data(), p->d_lines, total * sizeof(int4), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return fail(qdvm_cuda_status(e, "lines readback"));
+    if ((e = cudaMemcpy(p->h_c.data(), p->d_c, total * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return fail(qdvm_cuda_status(e, "c readback"));
+
+    if (d == 2) {
+        int np = total / 2;
+        if ((e = cudaMalloc(&p->d_pairs, np * sizeof(int4))) != cudaSuccess) return fail(qdvm_cuda_status(e, "pairs"));
+        if ((e = cudaMalloc(&p->d_pair_c, np * sizeof(double))) != cudaSuccess)
+            return fail(qdvm_cuda_status(e, "pair c"));
+        if ((e = cudaMalloc(&d_tmp, sizeof(int))) != cudaSuccess) return fail(qdvm_cuda_status(e, "tmp"));
+        k_pairs<<<1, 1024>>>(total, p->d_lines, p->d_c, p->d_pairs, p->d_pair_c, np, d_tmp);
+        int got = -1;
+        if ((e = cudaMemcpy(&got, d_tmp, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return fail(qdvm_cuda_status(e, "k_pairs"));
+        if (got != np || 2 * np != total) return fail(qdvm_fail(QDVM_ERR_CUDA, "2D line pairing is inconsistent"));
+        p->n_pairs = np;
+        int64_t terms = 0;
+        for (int i = 0; i < total; ++i) terms += (int64_t)(2 * p->h_lines[i].w) * (2 * p->h_lines[i].w);
+        p->n_terms = terms;
+    } else {
+        if ((e = cudaMalloc(&d_tmp, total * sizeof(int))) != cudaSuccess) return fail(qdvm_cuda_status(e, "plane counts"));
+        k_plane_count<<<total, 256>>>(total, p->d_lines, p->Ntilde, d_tmp);
+        std::vector<int> pc(total);
+        if ((e = cudaMemcpy(pc.data(), d_tmp, total * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return fail(qdvm_cuda_status(e, "k_plane_count"));
+        p->h_plane_start.assign(total + 1, 0);
+        int64_t terms = 0;
+        int mx = 0;
+        for (int i = 0; i < total; ++i) {
+            p->h_plane_start[i + 1] = p->h_plane_start[i] + pc[i];
+            terms += (int64_t)(2 * p->h_lines[i].w) * pc[i];
+            mx = pc[i] > mx ? pc[i] : mx;
+        }
+        p->n_plane = p->h_plane_start[total];
+        p->max_plane = mx;
+        p->n_terms = terms;
+        if ((e = cudaMalloc(&p->d_plane_start, (total + 1) * sizeof(int))) != cudaSuccess)
+            return fail(qdvm_cuda_status(e, "plane start"));
+        if ((e = cudaMalloc(&p->d_plane, (size_t)p->n_plane * sizeof(char4))) != cudaSuccess)
+            return fail(qdvm_cuda_status(e, "plane"));
+        if ((e = cudaMemcpy(p->d_plane_start, p->h_plane_start.data(), (total + 1) * sizeof(int),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return fail(qdvm_cuda_status(e, "plane start upload"));
+        k_plane_emit<<<total, 256>>>(total, p->d_lines, p->Ntilde, p->d_plane_start, p->d_plane);
+    }
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(qdvm_cuda_status(e, "plan build"));
+    return fail(st);
+}
+
+extern "C" qdvm_status qdvm_plan_create_ex(qdvm_plan_t* out, int d, int N, int Nbar, int Ntilde, double L,
+                                           int kernel, int engine) {
+    if (!out) return qdvm_fail(QDVM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (d != 2 && d != 3) return qdvm_fail(QDVM_ERR_INVALID_ARG, "d must be 2 or 3");
+    if (N < 4 || (d == 2 && N > 256) || (d == 3 && N > 64))
+        return qdvm_fail(QDVM_ERR_INVALID_ARG, "N out of range (2D: 4..256, 3D: 4..64)");
+    if (Nbar < 1) return qdvm_fail(QDVM_ERR_INVALID_ARG, "Nbar must be >= 1");
+    if (!(L > 0.0) || !isfinite(L)) return qdvm_fail(QDVM_ERR_INVALID_ARG, "L must be positive and finite");
+    if (kernel != QDVM_KERNEL_UNIT && kernel != QDVM_KERNEL_HP)
+        return qdvm_fail(QDVM_ERR_INVALID_ARG, "unknown kernel");
+    if (engine < QDVM_ENGINE_AUTO || engine > QDVM_ENGINE_SCAN)
+        return qdvm_fail(QDVM_ERR_INVALID_ARG, "unknown engine");
+    int Nt = Ntilde < 0 ? qdvm_default_ntilde(N) : Ntilde;
+    if (Nt < 1 || 2 * Nt >= N) return qdvm_fail(QDVM_ERR_INVALID_ARG, "Ntilde must satisfy 1 <= Ntilde, 2 Ntilde < N");
+
+    qdvm_plan_s* p = new (std::nothrow) qdvm_plan_s();
+    if (!p) return qdvm_fail(QDVM_ERR_OOM, "host allocation");
+    p->magic = QDVM_PLAN_MAGIC;
+    p->d = d;
+    p->N = N;
+    p->Nbar = Nbar;
+    p->Ntilde = Nt;
+    p->m = Nbar < Nt ? Nbar : Nt;
+    p->kernel = kernel;
+    p->engine = engine;
+    p->L = L;
+    p->h = 2.0 * L / N;
+    cudaGetDevice(&p->device);
+    qdvm_status s = build_tables(p);
+    if (s != QDVM_OK) {
+        plan_free(p);
+        return s;
+    }
+    *out = p;
+    return QDVM_OK;
+}
+
+extern "C" qdvm_status qdvm_plan_create(qdvm_plan_t* out, int d, int N, int Nbar, double L, int kernel) {
+    return qdvm_plan_create_ex(out, d, N, Nbar, -1, L, kernel, QDVM_ENGINE_AUTO);
+}
+
+extern "C" qdvm_status qdvm_plan_destroy(qdvm_plan_t plan) {
+    if (!plan) return QDVM_OK;
+    if (!qdvm_plan_ok(plan)) return qdvm_fail(QDVM_ERR_BAD_PLAN, "bad plan handle");
+    plan_free(plan);
+    return QDVM_OK;
+}
+
+extern "C" qdvm_status qdvm_plan_info(qdvm_plan_t p, int* d, int* N, int* Ntilde, int* m, int* n_lines,
+                                      int64_t* n_terms) {
+    if (!qdvm_plan_ok(p)) return qdvm_fail(QDVM_ERR_BAD_PLAN, "bad plan handle");
+    if (d) *d = p->d;
+    if (N) *N = p->N;
+    if (Ntilde) *Ntilde = p->Ntilde;
+    if (m) *m = p->m;
+    if (n_lines) *n_lines = p->n_lines;
+    if (n_terms) *n_terms = p->n_terms;
+    return QDVM_OK;
+}
+
+extern "C" qdvm_status qdvm_plan_lines(qdvm_plan_t p, int* dirs, int* J, double* c) {
+    if (!qdvm_plan_ok(p)) return qdvm_fail(QDVM_ERR_BAD_PLAN, "bad plan handle");
+    for (int i = 0; i < p->n_lines; ++i) {
+        const int4 e = p->h_lines[i];
+        if (dirs) {
+            dirs[3 * i + 0] = e.x;
+            dirs[3 * i + 1] = e.y;
+            dirs[3 * i + 2] = e.z;
+        }
+        if (J) J[i] = e.w;
+        if (c) c[i] = p->h_c[i];
+    }
+    return QDVM_OK;
+}

@@ -1,0 +1,139 @@
+// Internal definitions shared by the qdvm CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "qdvm.h"
+
+#define QDVM_PLAN_MAGIC 0x51445650u  // "QDVP"
+
+// Plan object behind the opaque qdvm_plan_t.
+struct qdvm_plan_s {
+    uint32_t magic;
+    int d, N, Nbar, Ntilde, m, kernel, engine;
+    double L, h;
+    int n_lines;     // lines of A_m
+    int n_pairs;     // 2D: pairs {e, e^perp}
+    int n_plane;     // 3D: total entries of the plane offset lists
+    int max_plane;   // 3D: largest plane list
+    int64_t n_terms; // (k, l) terms per output point
+    int device;
+    // device tables (owned)
+    int4* d_lines;        // (e0, e1, e2, J)
+    double* d_c;          // c_e
+    int4* d_pairs;        // 2D: (e0, e1, J, 0), one per pair
+    double* d_pair_c;     // 2D: c_e (= c_{e^perp})
+    int* d_plane_start;   // 3D: n_lines + 1 offsets into d_plane
+    char4* d_plane;       // 3D: (l0, l1, l2, 0), l in e^perp, 0 < |l|_inf <= Ntilde
+    // host copies
+    std::vector<int4> h_lines;
+    std::vector<double> h_c;
+    std::vector<int> h_plane_start;
+};
+
+// Plain-data view of a plan for kernels (passed by value).
+struct PlanDev {
+    int d, N, Ntilde, n_lines, n_pairs;
+    double h, L;
+    const int4* lines;
+    const double* c;
+    const int4* pairs;
+    const double* pair_c;
+    const int* plane_start;
+    const char4* plane;
+};
+
+struct BatchDev {
+    int n_plans;
+    PlanDev p[QDVM_MAX_BATCH_PLANS];
+};
+
+inline PlanDev plan_dev(const qdvm_plan_s* p) {
+    PlanDev v;
+    v.d = p->d;
+    v.N = p->N;
+    v.Ntilde = p->Ntilde;
+    v.n_lines = p->n_lines;
+    v.n_pairs = p->n_pairs;
+    v.h = p->h;
+    v.L = p->L;
+    v.lines = p->d_lines;
+    v.c = p->d_c;
+    v.pairs = p->d_pairs;
+    v.pair_c = p->d_pair_c;
+    v.plane_start = p->d_plane_start;
+    v.plane = p->d_plane;
+    return v;
+}
+
+// ------------------------------------------------------------ error state
+void qdvm_set_error(const std::string& msg);
+qdvm_status qdvm_fail(qdvm_status s, const std::string& msg);
+qdvm_status qdvm_cuda_status(cudaError_t e, const char* where);
+bool qdvm_plan_ok(const qdvm_plan_s* p);
+
+#define QDVM_CUDA_TRY(expr)                                                        \
+    do {                                                                           \
+        cudaError_t _e = (expr);                                                   \
+        if (_e != cudaSuccess) return qdvm_cuda_status(_e, #expr);                 \
+    } while (0)
+
+#define QDVM_LAUNCH_CHECK(where)                                                   \
+    do {                                                                           \
+        cudaError_t _e = cudaGetLastError();                                       \
+        if (_e != cudaSuccess) return qdvm_cuda_status(_e, where);                 \
+    } while (0)
+
+// Compensated accumulation s + c += x (Neumaier's TwoSum form of Kahan
+// summation) when KAHAN, plain s += x otherwise.
+template <typename T, bool KAHAN>
+__device__ __forceinline__ void comp_add(T& s, T& c, T x) {
+    if (KAHAN) {
+        T t = s + x;
+        T bp = t - s;
+        T err = (s - (t - bp)) + (x - bp);
+        c += err;
+        s = t;
+    } else {
+        s += x;
+    }
+}
+
+// ------------------------------------------------------------ 2D fused engine
+// Padded on-chip layout of a 2D cell: rows/cols [-H, N+H) with the periodic
+// halo replicated; the row stride is congruent to N modulo 32 so that a warp
+// of 32 consecutive points never hits the same bank twice, even when it
+// straddles two rows (N = 16, 48).
+__host__ __device__ inline int pad2d_stride(int N, int H) {
+    int w = N + 2 * H;
+    int r = ((N % 32) - (w % 32) + 32) % 32;
+    return w + r;
+}
+__host__ __device__ inline int pad2d_rows(int N, int H) { return N + 2 * H; }
+
+size_t fused2d_smem_bytes(int N, int H, int prec);
+int fused2d_supported(int N, int H, int prec);
+
+qdvm_status fused2d_eval_single(const qdvm_plan_s* p, const void* f, void* Q, int prec, void* ws,
+                                size_t ws_bytes, cudaStream_t st);
+size_t fused2d_single_workspace(const qdvm_plan_s* p, int prec);
+qdvm_status fused2d_eval_batched(const BatchDev& b, int max_N, int max_H, int n_cells, const int* cell_plan,
+                                 const int64_t* cell_offset, const void* f, void* Q, double* moments, int prec,
+                                 void* ws, cudaStream_t st);
+
+qdvm_status moments_launch(int d, int N, double L, const void* Q, int prec, double* m, cudaStream_t st);
+qdvm_status schedule_launch(const BatchDev& b, int n_cells, const int* cell_plan, int* order, int* counter,
+                            cudaStream_t st);
+
+int qdvm_num_sms();
+
+// ------------------------------------------------------------ 3D engine
+size_t gen3d_workspace(const BatchDev& b, int n_cells, int prec, bool single);
+qdvm_status gen3d_eval(const BatchDev& b, int n_cells, const int* cell_plan, const int64_t* cell_offset,
+                       const void* f, void* Q, double* moments, int prec, void* ws, size_t ws_bytes, bool single,
+                       cudaStream_t st);
+int gen3d_supported(const qdvm_plan_s* p, int prec);
