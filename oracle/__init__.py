@@ -16,7 +16,8 @@ Functions and the passages they follow:
 * ``q(...)`` / ``q_points``  -- eq. (DR) of Section 2.3 with the decoupled
   weights of eq. (decoup) and the line restriction of eq. (decDVM).
 * ``jvp`` / ``vjp``          -- derivative of that quadratic form and the
-  transpose of its Jacobian (scattered term by term).
+  transpose of its Jacobian (scattered term by term); ``jvp_points`` /
+  ``vjp_points`` the same at selected points (the VJP as a gather).
 * ``moments``                -- mass, momentum and energy of Section 2.1.
 * ``default_ntilde(N)``      -- Ntilde = floor(N / (3 + sqrt 2)), Section 4.
 
@@ -81,6 +82,14 @@ def _load():
             fn = getattr(lib, name)
             fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                            ctypes.c_double, dbl_p, dbl_p, dbl_p]
+            fn.restype = ctypes.c_int
+        lib.oracle_vjp_scale.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double, dbl_p, dbl_p, dbl_p, dbl_p]
+        lib.oracle_vjp_scale.restype = ctypes.c_int
+        for name in ("oracle_jvp_points", "oracle_vjp_points"):
+            fn = getattr(lib, name)
+            fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                           ctypes.c_double, dbl_p, dbl_p, i64_p, ctypes.c_int64, dbl_p, dbl_p]
             fn.restype = ctypes.c_int
         lib.oracle_moments.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dbl_p, dbl_p]
         lib.oracle_moments.restype = ctypes.c_int
@@ -173,15 +182,54 @@ def jvp(f, df, L: float, Nbar: int, kernel: str = "unit", Ntilde: int | None = N
     return out
 
 
-def vjp(f, g, L: float, Nbar: int, kernel: str = "unit", Ntilde: int | None = None) -> np.ndarray:
+def vjp(f, g, L: float, Nbar: int, kernel: str = "unit", Ntilde: int | None = None,
+        with_scale: bool = False):
+    """Transpose of the Jacobian applied to g (term-by-term scatter).  With
+    ``with_scale`` also returns the scattered sum of absolute values."""
     f = _f64(f)
     g = _f64(g)
     d, N, Nt, m, h = _params(f, L, Nbar, Ntilde)
     out = np.zeros_like(f)
-    rc = _load().oracle_vjp(d, N, Nt, m, KERNELS[kernel], h, _dp(f), _dp(g), _dp(out))
+    sc = np.zeros_like(f)
+    rc = _load().oracle_vjp_scale(d, N, Nt, m, KERNELS[kernel], h, _dp(f), _dp(g), _dp(out), _dp(sc))
     if rc != 0:
         raise RuntimeError(f"oracle_vjp failed ({rc})")
-    return out
+    return (out, sc) if with_scale else out
+
+
+def jvp_points(f, df, L: float, Nbar: int, idx=None, kernel: str = "unit", Ntilde: int | None = None):
+    """(dQ, scale) at flat indices ``idx`` (all points when None); scale is the
+    sum of absolute values of the four products of every term."""
+    f = _f64(f)
+    df = _f64(df)
+    d, N, Nt, m, h = _params(f, L, Nbar, Ntilde)
+    if idx is None:
+        n, ip = f.size, None
+    else:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        n, ip = idx.size, idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    out, sc = np.zeros(n), np.zeros(n)
+    rc = _load().oracle_jvp_points(d, N, Nt, m, KERNELS[kernel], h, _dp(f), _dp(df), ip, n, _dp(out), _dp(sc))
+    if rc != 0:
+        raise RuntimeError(f"oracle_jvp_points failed ({rc})")
+    if idx is None:
+        out, sc = out.reshape(f.shape), sc.reshape(f.shape)
+    return out, sc
+
+
+def vjp_points(f, g, L: float, Nbar: int, idx, kernel: str = "unit", Ntilde: int | None = None):
+    """(grad, scale) at flat indices ``idx``, summed as a gather over the
+    terms in which each selected f_p appears."""
+    f = _f64(f)
+    g = _f64(g)
+    d, N, Nt, m, h = _params(f, L, Nbar, Ntilde)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    out, sc = np.zeros(idx.size), np.zeros(idx.size)
+    rc = _load().oracle_vjp_points(d, N, Nt, m, KERNELS[kernel], h, _dp(f), _dp(g),
+                                   idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), idx.size, _dp(out), _dp(sc))
+    if rc != 0:
+        raise RuntimeError(f"oracle_vjp_points failed ({rc})")
+    return out, sc
 
 
 def moments(Q, L: float) -> np.ndarray:

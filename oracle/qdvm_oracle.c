@@ -292,42 +292,57 @@ int oracle_q(int d, int N, int Ntilde, int m, int kernel, double h, const double
 
 /* Directional derivative of Q at f along df (Q is quadratic in f):
  *   dQ_i = sum Gamma [df_{i+k} f_{i+l} + f_{i+k} df_{i+l}
- *                     - df_i f_{i+k+l} - f_i df_{i+k+l}]. */
-int oracle_jvp(int d, int N, int Ntilde, int m, int kernel, double h, const double* f,
-               const double* df, double* dQ) {
+ *                     - df_i f_{i+k+l} - f_i df_{i+k+l}],
+ * at the listed flat indices (all points if idx == NULL).  scale (may be
+ * NULL) receives the sum of the absolute values of the four products. */
+int oracle_jvp_points(int d, int N, int Ntilde, int m, int kernel, double h, const double* f, const double* df,
+                      const int64_t* idx, int64_t n_idx, double* dQ, double* scale) {
     if (check_args(d, N, Ntilde, m)) return -1;
     term_t* T = NULL;
     int nt = build_terms(d, Ntilde, m, kernel, h, &T);
     if (nt < 0) return -2;
     int64_t total = 1;
     for (int a = 0; a < d; ++a) total *= N;
+    int64_t n_out = idx ? n_idx : total;
 #pragma omp parallel for schedule(dynamic, 16)
-    for (int64_t i = 0; i < total; ++i) {
+    for (int64_t o = 0; o < n_out; ++o) {
+        int64_t i = idx ? idx[o] : o;
         int c[ORACLE_MAX_D];
         unflatten(i, d, N, c);
-        nsum_t s = {0, 0};
+        nsum_t s = {0, 0}, sc = {0, 0};
         for (int t = 0; t < nt; ++t) {
             int64_t ia = flat_shift(c, T[t].k, NULL, d, N);
             int64_t ib = flat_shift(c, T[t].l, NULL, d, N);
             int64_t ie = flat_shift(c, T[t].k, T[t].l, d, N);
             double w = T[t].w;
-            nsum_add(&s, w * df[ia] * f[ib]);
-            nsum_add(&s, w * f[ia] * df[ib]);
-            nsum_add(&s, -w * df[i] * f[ie]);
-            nsum_add(&s, -w * f[i] * df[ie]);
+            double p1 = w * df[ia] * f[ib], p2 = w * f[ia] * df[ib];
+            double p3 = w * df[i] * f[ie], p4 = w * f[i] * df[ie];
+            nsum_add(&s, p1);
+            nsum_add(&s, p2);
+            nsum_add(&s, -p3);
+            nsum_add(&s, -p4);
+            nsum_add(&sc, fabs(p1) + fabs(p2));
+            nsum_add(&sc, fabs(p3) + fabs(p4));
         }
-        dQ[i] = nsum_value(&s);
+        dQ[o] = nsum_value(&s);
+        if (scale) scale[o] = nsum_value(&sc);
     }
     free(T);
     return 0;
 }
 
+int oracle_jvp(int d, int N, int Ntilde, int m, int kernel, double h, const double* f, const double* df,
+               double* dQ) {
+    return oracle_jvp_points(d, N, Ntilde, m, kernel, h, f, df, NULL, 0, dQ, NULL);
+}
+
 /* Transpose of the Jacobian applied to g, by scattering the four partial
  * derivatives of every term:
  *   grad[i+k] += w g_i f_{i+l},   grad[i+l]   += w g_i f_{i+k},
- *   grad[i]   -= w g_i f_{i+k+l}, grad[i+k+l] -= w g_i f_i. */
-int oracle_vjp(int d, int N, int Ntilde, int m, int kernel, double h, const double* f,
-               const double* g, double* grad) {
+ *   grad[i]   -= w g_i f_{i+k+l}, grad[i+k+l] -= w g_i f_i.
+ * scale (may be NULL) receives the scattered absolute values. */
+int oracle_vjp_scale(int d, int N, int Ntilde, int m, int kernel, double h, const double* f, const double* g,
+                     double* grad, double* scale) {
     if (check_args(d, N, Ntilde, m)) return -1;
     term_t* T = NULL;
     int nt = build_terms(d, Ntilde, m, kernel, h, &T);
@@ -335,7 +350,7 @@ int oracle_vjp(int d, int N, int Ntilde, int m, int kernel, double h, const doub
     int64_t total = 1;
     for (int a = 0; a < d; ++a) total *= N;
     int nthr = oracle_max_threads();
-    nsum_t* part = (nsum_t*)calloc((size_t)nthr * (size_t)total, sizeof(nsum_t));
+    nsum_t* part = (nsum_t*)calloc((size_t)nthr * (size_t)total * 2, sizeof(nsum_t));
     if (!part) {
         free(T);
         return -2;
@@ -347,7 +362,8 @@ int oracle_vjp(int d, int N, int Ntilde, int m, int kernel, double h, const doub
 #else
         int tid = 0;
 #endif
-        nsum_t* acc = part + (size_t)tid * (size_t)total;
+        nsum_t* acc = part + (size_t)tid * (size_t)total * 2;
+        nsum_t* sca = acc + total;
 #pragma omp for schedule(static)
         for (int64_t i = 0; i < total; ++i) {
             int c[ORACLE_MAX_D];
@@ -357,22 +373,78 @@ int oracle_vjp(int d, int N, int Ntilde, int m, int kernel, double h, const doub
                 int64_t ib = flat_shift(c, T[t].l, NULL, d, N);
                 int64_t ie = flat_shift(c, T[t].k, T[t].l, d, N);
                 double wg = T[t].w * g[i];
-                nsum_add(&acc[ia], wg * f[ib]);
-                nsum_add(&acc[ib], wg * f[ia]);
-                nsum_add(&acc[i], -wg * f[ie]);
-                nsum_add(&acc[ie], -wg * f[i]);
+                double pa = wg * f[ib], pb = wg * f[ia], pi = wg * f[ie], pe = wg * f[i];
+                nsum_add(&acc[ia], pa);
+                nsum_add(&acc[ib], pb);
+                nsum_add(&acc[i], -pi);
+                nsum_add(&acc[ie], -pe);
+                nsum_add(&sca[ia], fabs(pa));
+                nsum_add(&sca[ib], fabs(pb));
+                nsum_add(&sca[i], fabs(pi));
+                nsum_add(&sca[ie], fabs(pe));
             }
         }
     }
     for (int64_t i = 0; i < total; ++i) {
-        nsum_t s = {0, 0};
+        nsum_t s = {0, 0}, sc = {0, 0};
         for (int t = 0; t < nthr; ++t) {
-            nsum_add(&s, part[(size_t)t * (size_t)total + i].s);
-            nsum_add(&s, part[(size_t)t * (size_t)total + i].c);
+            const nsum_t* acc = part + (size_t)t * (size_t)total * 2;
+            nsum_add(&s, acc[i].s);
+            nsum_add(&s, acc[i].c);
+            nsum_add(&sc, acc[total + i].s);
+            nsum_add(&sc, acc[total + i].c);
         }
         grad[i] = nsum_value(&s);
+        if (scale) scale[i] = nsum_value(&sc);
     }
     free(part);
+    free(T);
+    return 0;
+}
+
+int oracle_vjp(int d, int N, int Ntilde, int m, int kernel, double h, const double* f, const double* g,
+               double* grad) {
+    return oracle_vjp_scale(d, N, Ntilde, m, kernel, h, f, g, grad, NULL);
+}
+
+/* The same transpose at selected points, summed as a gather: point p
+ * receives, from every term (k, l), the derivative of the terms in which f_p
+ * appears:
+ *   grad_p = sum Gamma [ g_{p-k} f_{p-k+l} + g_{p-l} f_{p-l+k}
+ *                        - g_p f_{p+k+l} - g_{p-k-l} f_{p-k-l} ]. */
+int oracle_vjp_points(int d, int N, int Ntilde, int m, int kernel, double h, const double* f, const double* g,
+                      const int64_t* idx, int64_t n_idx, double* grad, double* scale) {
+    if (check_args(d, N, Ntilde, m)) return -1;
+    term_t* T = NULL;
+    int nt = build_terms(d, Ntilde, m, kernel, h, &T);
+    if (nt < 0) return -2;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t o = 0; o < n_idx; ++o) {
+        int64_t p = idx[o];
+        int c[ORACLE_MAX_D];
+        unflatten(p, d, N, c);
+        nsum_t s = {0, 0}, sc = {0, 0};
+        for (int t = 0; t < nt; ++t) {
+            int mk[ORACLE_MAX_D], ml[ORACLE_MAX_D];
+            for (int a = 0; a < d; ++a) {
+                mk[a] = -T[t].k[a];
+                ml[a] = -T[t].l[a];
+            }
+            double w = T[t].w;
+            double t1 = w * g[flat_shift(c, mk, NULL, d, N)] * f[flat_shift(c, mk, T[t].l, d, N)];
+            double t2 = w * g[flat_shift(c, ml, NULL, d, N)] * f[flat_shift(c, ml, T[t].k, d, N)];
+            double t3 = w * g[p] * f[flat_shift(c, T[t].k, T[t].l, d, N)];
+            double t4 = w * g[flat_shift(c, mk, ml, d, N)] * f[flat_shift(c, mk, ml, d, N)];
+            nsum_add(&s, t1);
+            nsum_add(&s, t2);
+            nsum_add(&s, -t3);
+            nsum_add(&s, -t4);
+            nsum_add(&sc, fabs(t1) + fabs(t2));
+            nsum_add(&sc, fabs(t3) + fabs(t4));
+        }
+        grad[o] = nsum_value(&s);
+        if (scale) scale[o] = nsum_value(&sc);
+    }
     free(T);
     return 0;
 }

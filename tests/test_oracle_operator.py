@@ -361,3 +361,22 @@ def test_moments_of_gaussian_closed_form():
         assert abs(m[0] - 1.3) < 1e-10
         assert np.allclose(m[1:1 + d], 1.3 * u, atol=1e-10)
         assert abs(m[d + 1] - 1.3 * (u @ u + d * T)) < 1e-9
+
+
+@pytest.mark.parametrize("d,N,Nbar,kernel", [(2, 11, 2, "hp"), (3, 7, 1, "unit")])
+def test_points_variants_match_full_arrays(d, N, Nbar, kernel):
+    """jvp_points equals jvp; vjp_points (gather) equals vjp (scatter)."""
+    rs = np.random.default_rng(51)
+    f = rs.uniform(0.1, 1.0, (N,) * d)
+    g = rs.standard_normal((N,) * d)
+    dl = rs.standard_normal((N,) * d)
+    idx = np.array([0, 3, N ** d // 2, N ** d - 1])
+    J = oracle.jvp(f, dl, 2.0, Nbar, kernel=kernel)
+    Jp, Js = oracle.jvp_points(f, dl, 2.0, Nbar, idx, kernel=kernel)
+    assert np.allclose(Jp, J.ravel()[idx], rtol=0, atol=1e-14 * np.max(Js))
+    G, Gs = oracle.vjp(f, g, 2.0, Nbar, kernel=kernel, with_scale=True)
+    Gp, Gps = oracle.vjp_points(f, g, 2.0, Nbar, idx, kernel=kernel)
+    assert np.allclose(Gp, G.ravel()[idx], rtol=0, atol=1e-14 * np.max(Gs))
+    assert np.allclose(Gps, Gs.ravel()[idx], rtol=1e-13)
+    # the scales bound the values
+    assert np.all(np.abs(G) <= Gs * (1 + 1e-12)) and np.all(np.abs(Jp) <= Js * (1 + 1e-12))
