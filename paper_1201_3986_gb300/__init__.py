@@ -244,6 +244,33 @@ def qdvm_vjp(plan: Plan, f: torch.Tensor, g: torch.Tensor, prec="f64", out=None,
     return gr
 
 
+def _derivative_batched(fn, name, plans, cell_plan, cell_offset, f, a, prec, out, workspace):
+    p = _prec(prec)
+    n_cells = int(cell_plan.numel())
+    if cell_plan.dtype != torch.int32 or cell_offset.dtype != torch.int64:
+        raise ValueError("cell_plan must be int32 and cell_offset int64")
+    for t in (f, a):
+        if t.dtype != _DTYPE[p] or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"inputs must be contiguous CUDA {_DTYPE[p]} tensors")
+    res = torch.empty_like(f) if out is None else out
+    ws = workspace if workspace is not None else _workspace(batched_workspace_bytes(plans, n_cells, p), f.device)
+    _check(fn(_plan_array(plans), len(plans), n_cells, _ptr(cell_plan), _ptr(cell_offset), _ptr(f), _ptr(a),
+              _ptr(res), p, _ptr(ws), 0 if ws is None else ws.numel(), _stream(f.device)), name)
+    return res
+
+
+def qdvm_jvp_batched(plans, cell_plan, cell_offset, f, df, prec="f32", out=None, workspace=None):
+    """dQ = Q'(f) df for every cell of a ragged batch."""
+    return _derivative_batched(_lib.qdvm_jvp_batched, "qdvm_jvp_batched", plans, cell_plan, cell_offset, f, df,
+                               prec, out, workspace)
+
+
+def qdvm_vjp_batched(plans, cell_plan, cell_offset, f, g, prec="f32", out=None, workspace=None):
+    """grad = Q'(f)^T g for every cell of a ragged batch."""
+    return _derivative_batched(_lib.qdvm_vjp_batched, "qdvm_vjp_batched", plans, cell_plan, cell_offset, f, g,
+                               prec, out, workspace)
+
+
 class QdvmFunction(torch.autograd.Function):
     """Q(f) with a hand-written adjoint: backward calls qdvm_vjp."""
 

@@ -38,15 +38,15 @@ BatchDev single_batch(const qdvm_plan_s* p) {
 extern "C" qdvm_status qdvm_eval_workspace(qdvm_plan_t p, int prec, size_t* bytes) {
     if (!qdvm_plan_ok(p)) return qdvm_fail(QDVM_ERR_BAD_PLAN, "bad plan handle");
     if (!prec_ok(prec) || !bytes) return qdvm_fail(QDVM_ERR_INVALID_ARG, "bad precision or NULL bytes");
+    const BatchDev b = single_batch(p);
+    const size_t der = std::max(engine_workspace(QDVM_MODE_JVP, b, 1, prec, true),
+                                engine_workspace(QDVM_MODE_VJP, b, 1, prec, true));
     if (p->d == 2 && fused2d_supported(p->N, p->Ntilde, prec)) {
-        *bytes = fused2d_single_workspace(p, prec);
+        *bytes = std::max(fused2d_single_workspace(p, prec), der);
         return QDVM_OK;
     }
-    if (p->d == 3) {
-        *bytes = gen3d_workspace(single_batch(p), 1, prec, true);
-        return QDVM_OK;
-    }
-    return qdvm_fail(QDVM_ERR_UNSUPPORTED, "no engine for this plan and precision");
+    *bytes = std::max(engine_workspace(QDVM_MODE_FWD, b, 1, prec, true), der);
+    return QDVM_OK;
 }
 
 extern "C" qdvm_status qdvm_eval(qdvm_plan_t p, const void* f, void* Q, int prec, void* ws, size_t ws_bytes,
@@ -57,9 +57,8 @@ extern "C" qdvm_status qdvm_eval(qdvm_plan_t p, const void* f, void* Q, int prec
     if (f == Q) return qdvm_fail(QDVM_ERR_INVALID_ARG, "f must not alias Q");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (p->d == 2 && fused2d_supported(p->N, p->Ntilde, prec)) return fused2d_eval_single(p, f, Q, prec, ws, ws_bytes, st);
-    if (p->d == 3)
-        return gen3d_eval(single_batch(p), 1, nullptr, nullptr, f, Q, nullptr, prec, ws, ws_bytes, true, st);
-    return qdvm_fail(QDVM_ERR_UNSUPPORTED, "no engine for this plan and precision");
+    return engine_run(QDVM_MODE_FWD, single_batch(p), 1, nullptr, nullptr, f, nullptr, Q, nullptr, prec, ws, ws_bytes,
+                      true, st);
 }
 
 static bool all_fused2d(const qdvm_plan_t* plans, int n_plans, int d, int prec) {
@@ -75,15 +74,12 @@ extern "C" qdvm_status qdvm_batched_workspace(const qdvm_plan_t* plans, int n_pl
     int d = 0;
     qdvm_status s = build_batch(plans, n_plans, &b, &d);
     if (s != QDVM_OK) return s;
-    if (all_fused2d(plans, n_plans, d, prec)) {
-        *bytes = 256 + round256((size_t)std::max(n_cells, 1) * sizeof(int));
-        return QDVM_OK;
-    }
-    if (d == 3) {
-        *bytes = gen3d_workspace(b, n_cells, prec, false);
-        return QDVM_OK;
-    }
-    return qdvm_fail(QDVM_ERR_UNSUPPORTED, "no batched engine for these plans and precision");
+    const size_t der = std::max(engine_workspace(QDVM_MODE_JVP, b, n_cells, prec, false),
+                                engine_workspace(QDVM_MODE_VJP, b, n_cells, prec, false));
+    const size_t fwd = all_fused2d(plans, n_plans, d, prec) ? 256 + round256((size_t)std::max(n_cells, 1) * sizeof(int))
+                                                            : engine_workspace(QDVM_MODE_FWD, b, n_cells, prec, false);
+    *bytes = std::max(fwd, der);
+    return QDVM_OK;
 }
 
 extern "C" qdvm_status qdvm_eval_batched(const qdvm_plan_t* plans, int n_plans, int n_cells, const int* cell_plan,
@@ -110,9 +106,8 @@ extern "C" qdvm_status qdvm_eval_batched(const qdvm_plan_t* plans, int n_plans, 
     }
     if (all_fused2d(plans, n_plans, d, prec))
         return fused2d_eval_batched(b, maxN, maxH, n_cells, cell_plan, cell_offset, f, Q, moments, prec, ws, st);
-    if (d == 3)
-        return gen3d_eval(b, n_cells, cell_plan, cell_offset, f, Q, moments, prec, ws, ws_bytes, false, st);
-    return qdvm_fail(QDVM_ERR_UNSUPPORTED, "no batched engine for these plans and precision");
+    return engine_run(QDVM_MODE_FWD, b, n_cells, cell_plan, cell_offset, f, nullptr, Q, moments, prec, ws, ws_bytes,
+                      false, st);
 }
 
 extern "C" qdvm_status qdvm_moments(qdvm_plan_t p, const void* Q, int prec, double* m, void* stream) {
@@ -121,32 +116,52 @@ extern "C" qdvm_status qdvm_moments(qdvm_plan_t p, const void* Q, int prec, doub
     return moments_launch(p->d, p->N, p->L, Q, prec, m, static_cast<cudaStream_t>(stream));
 }
 
+static qdvm_status derivative_single(int mode, qdvm_plan_t p, const void* f, const void* a, void* out, int prec,
+                                     void* ws, size_t ws_bytes, void* stream) {
+    if (!qdvm_plan_ok(p)) return qdvm_fail(QDVM_ERR_BAD_PLAN, "bad plan handle");
+    if (!prec_ok(prec)) return qdvm_fail(QDVM_ERR_INVALID_ARG, "bad precision");
+    if (!f || !a || !out) return qdvm_fail(QDVM_ERR_INVALID_ARG, "NULL device array");
+    if (out == f || out == a) return qdvm_fail(QDVM_ERR_INVALID_ARG, "the output must not alias an input");
+    return engine_run(mode, single_batch(p), 1, nullptr, nullptr, f, a, out, nullptr, prec, ws, ws_bytes, true,
+                      static_cast<cudaStream_t>(stream));
+}
+
+static qdvm_status derivative_batched(int mode, const qdvm_plan_t* plans, int n_plans, int n_cells,
+                                      const int* cell_plan, const int64_t* cell_offset, const void* f, const void* a,
+                                      void* out, int prec, void* ws, size_t ws_bytes, void* stream) {
+    if (n_cells < 0) return qdvm_fail(QDVM_ERR_INVALID_ARG, "n_cells < 0");
+    if (!prec_ok(prec)) return qdvm_fail(QDVM_ERR_INVALID_ARG, "bad precision");
+    BatchDev b;
+    int d = 0;
+    qdvm_status s = build_batch(plans, n_plans, &b, &d);
+    if (s != QDVM_OK) return s;
+    if (n_cells == 0) return QDVM_OK;
+    if (!cell_plan || !cell_offset || !f || !a || !out) return qdvm_fail(QDVM_ERR_INVALID_ARG, "NULL device array");
+    if (out == f || out == a) return qdvm_fail(QDVM_ERR_INVALID_ARG, "the output must not alias an input");
+    return engine_run(mode, b, n_cells, cell_plan, cell_offset, f, a, out, nullptr, prec, ws, ws_bytes, false,
+                      static_cast<cudaStream_t>(stream));
+}
+
 extern "C" qdvm_status qdvm_jvp(qdvm_plan_t p, const void* f, const void* df, void* dQ, int prec, void* ws,
                                 size_t ws_bytes, void* stream) {
-    (void)f, (void)df, (void)dQ, (void)prec, (void)ws, (void)ws_bytes, (void)stream;
-    if (!qdvm_plan_ok(p)) return qdvm_fail(QDVM_ERR_BAD_PLAN, "bad plan handle");
-    return qdvm_fail(QDVM_ERR_UNSUPPORTED, "jvp not available");
+    return derivative_single(QDVM_MODE_JVP, p, f, df, dQ, prec, ws, ws_bytes, stream);
 }
 
 extern "C" qdvm_status qdvm_vjp(qdvm_plan_t p, const void* f, const void* g, void* grad, int prec, void* ws,
                                 size_t ws_bytes, void* stream) {
-    (void)f, (void)g, (void)grad, (void)prec, (void)ws, (void)ws_bytes, (void)stream;
-    if (!qdvm_plan_ok(p)) return qdvm_fail(QDVM_ERR_BAD_PLAN, "bad plan handle");
-    return qdvm_fail(QDVM_ERR_UNSUPPORTED, "vjp not available");
+    return derivative_single(QDVM_MODE_VJP, p, f, g, grad, prec, ws, ws_bytes, stream);
 }
 
 extern "C" qdvm_status qdvm_jvp_batched(const qdvm_plan_t* plans, int n_plans, int n_cells, const int* cell_plan,
                                         const int64_t* cell_offset, const void* f, const void* df, void* dQ, int prec,
                                         void* ws, size_t ws_bytes, void* stream) {
-    (void)plans, (void)n_plans, (void)n_cells, (void)cell_plan, (void)cell_offset, (void)f, (void)df, (void)dQ;
-    (void)prec, (void)ws, (void)ws_bytes, (void)stream;
-    return qdvm_fail(QDVM_ERR_UNSUPPORTED, "batched jvp not available");
+    return derivative_batched(QDVM_MODE_JVP, plans, n_plans, n_cells, cell_plan, cell_offset, f, df, dQ, prec, ws,
+                              ws_bytes, stream);
 }
 
 extern "C" qdvm_status qdvm_vjp_batched(const qdvm_plan_t* plans, int n_plans, int n_cells, const int* cell_plan,
                                         const int64_t* cell_offset, const void* f, const void* g, void* grad, int prec,
                                         void* ws, size_t ws_bytes, void* stream) {
-    (void)plans, (void)n_plans, (void)n_cells, (void)cell_plan, (void)cell_offset, (void)f, (void)g, (void)grad;
-    (void)prec, (void)ws, (void)ws_bytes, (void)stream;
-    return qdvm_fail(QDVM_ERR_UNSUPPORTED, "batched vjp not available");
+    return derivative_batched(QDVM_MODE_VJP, plans, n_plans, n_cells, cell_plan, cell_offset, f, g, grad, prec, ws,
+                              ws_bytes, stream);
 }

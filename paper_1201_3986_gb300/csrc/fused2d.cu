@@ -11,10 +11,11 @@
 // with J = floor(Ntilde / |e|_inf) for both lines.
 //
 // Layout: the cell is copied into shared memory with a periodic halo of width
-// H = Ntilde on every side (padded row stride congruent to N mod 32, see
+// 2H (H = Ntilde) on every side (padded row stride congruent to N mod 32, see
 // pad2d_stride), so every window gather is base + j*step without any modulo,
 // and a warp of 32 consecutive points reads 32 distinct banks for every
-// direction.  Each thread owns the points tid + k*blockDim.x and keeps their
+// direction.  Pairs with J = 1 read V_e straight from the cell at
+// i +- e +- e^perp (|e +- e^perp|_inf <= 2|e|_inf <= 2H) with no barrier.  Each thread owns the points tid + k*blockDim.x and keeps their
 // accumulators in registers for all pairs; P goes through shared memory
 // (with its halo images) because V gathers it along e.
 #include <algorithm>
@@ -58,14 +59,17 @@ __device__ __forceinline__ void fused2d_body(const int N, const int H, const int
                                              const double h, const double L, const T* __restrict__ fcell,
                                              T* __restrict__ qcell, double* __restrict__ mom, T* __restrict__ sF,
                                              T* __restrict__ sP, double* red) {
-    const int RS = pad2d_stride(N, H), R = N + 2 * H;
+    const int RS = pad2d_stride(N, H), RF = pad2d_rows_f(N, H), HF = 2 * H;
     const int NT = blockDim.x, tid = threadIdx.x;
     const int NN = N * N;
+    // P buffer viewed in the f buffer's coordinates (P rows start H rows and
+    // H columns later than f rows)
+    T* const sPf = sP - (H * RS + H);
 
-    // periodic fill of the padded cell
-    for (int p = tid; p < R * R; p += NT) {
-        const int py = p / R, px = p - py * R;
-        int sy = py - H, sx = px - H;
+    // periodic fill of the padded cell, rows/cols [-2H, N+2H)
+    for (int p = tid; p < RF * RF; p += NT) {
+        const int py = p / RF, px = p - py * RF;
+        int sy = py - HF, sx = px - HF;
         sy += sy < 0 ? N : 0;
         sy -= sy >= N ? N : 0;
         sx += sx < 0 ? N : 0;
@@ -73,31 +77,31 @@ __device__ __forceinline__ void fused2d_body(const int N, const int H, const int
         sF[py * RS + px] = fcell[sy * N + sx];
     }
 
-    int addr[PPT];
-    unsigned img[PPT];
-    T fk[PPT], acc[PPT], cmp[PPT];
+    // per owned point: padded address (low 16 bits) and the mask of its halo
+    // images (bits 16..24), or -1 when the slot is past the end of the cell
+    int pk[PPT];
+    T acc[PPT], cmp[PPT];
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         const int idx = tid + k * NT;
         const int y = idx / N, x = idx - (idx / N) * N;
-        addr[k] = idx < NN ? (y + H) * RS + x + H : -1;
-        unsigned msk = 0;
+        int v = -1;
         if (idx < NN) {
             // image (dy, dx) of point (y, x) lies in the padded window iff the
             // shifted coordinates stay in [-H, N+H)
             const bool oy[3] = {y >= N - H, true, y < H};
             const bool ox[3] = {x >= N - H, true, x < H};
+            unsigned msk = 0;
 #pragma unroll
             for (int b = 0; b < 9; ++b)
                 if (b != 4 && oy[b / 3] && ox[b % 3]) msk |= 1u << b;
+            v = (y + HF) * RS + x + HF + (int)(msk << 16);
         }
-        img[k] = msk;
+        pk[k] = v;
         acc[k] = T(0);
         cmp[k] = T(0);
     }
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) fk[k] = addr[k] >= 0 ? sF[addr[k]] : T(0);
 
     for (int pr = pb; pr < pe; ++pr) {
         const int4 e = pairs[pr];
@@ -105,44 +109,74 @@ __device__ __forceinline__ void fused2d_body(const int N, const int H, const int
         const int se = e.x * RS + e.y;   // +e       (axis 0 = rows, axis 1 = columns)
         const int sp = -e.y * RS + e.x;  // +e^perp = (-e1, e0)
         const int J = e.z;
+        if (J == 1) {
+            // one step along each line: V_e(i) = sum of f at i +- e +- e^perp,
+            // read directly from the cell -- no P buffer, no barrier
+            const int d1 = se + sp, d2 = se - sp;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (pk[k] >= 0) {
+                    const int a = pk[k] & 0xFFFF;
+                    const T w = sF[a + se] + sF[a - se];
+                    const T pp = sF[a + sp] + sF[a - sp];
+                    const T v = (sF[a + d1] + sF[a - d1]) + (sF[a + d2] + sF[a - d2]);
+                    const T t = c2 * w * pp - c2 * sF[a] * v;
+                    comp_add<T, KAHAN>(acc[k], cmp[k], t);
+                }
+            }
+            continue;
+        }
+        // (A) W_e and P = W_{e^perp}; j outside, points inside: PPT independent
+        // accumulator pairs per thread
         T W[PPT], Pv[PPT];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
             W[k] = T(0);
             Pv[k] = T(0);
-            const int a = addr[k];
-            if (a >= 0) {
-                T w = T(0), pp = T(0);
-                int o = se, q = sp;
-                for (int j = 0; j < J; ++j) {
-                    w += sF[a + o] + sF[a - o];
-                    pp += sF[a + q] + sF[a - q];
-                    o += se;
-                    q += sp;
-                }
-                W[k] = w;
-                Pv[k] = pp;
-                sP[a] = pp;
-                unsigned msk = img[k];
-                while (msk) {
-                    const int b = __ffs(msk) - 1;
-                    msk &= msk - 1;
-                    sP[a + (b / 3 - 1) * N * RS + (b % 3 - 1) * N] = pp;
+        }
+        for (int j = 1; j <= J; ++j) {
+            const int o = j * se, q = j * sp;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (pk[k] >= 0) {
+                    const int a = pk[k] & 0xFFFF;
+                    W[k] += sF[a + o] + sF[a - o];
+                    Pv[k] += sF[a + q] + sF[a - q];
                 }
             }
         }
-        __syncthreads();
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-            const int a = addr[k];
-            if (a >= 0) {
-                T v = T(0);
-                int o = se;
-                for (int j = 0; j < J; ++j) {
-                    v += sP[a + o] + sP[a - o];
-                    o += se;
+            if (pk[k] >= 0) {
+                const int a = pk[k] & 0xFFFF;
+                sPf[a] = Pv[k];
+                unsigned msk = (unsigned)pk[k] >> 16;
+                while (msk) {
+                    const int b = __ffs(msk) - 1;
+                    msk &= msk - 1;
+                    sPf[a + (b / 3 - 1) * N * RS + (b % 3 - 1) * N] = Pv[k];
                 }
-                const T t = c2 * (W[k] * Pv[k] - fk[k] * v);
+                W[k] = c2 * W[k] * Pv[k];  // gain, 2 c_e W_e W_{e^perp}
+                Pv[k] = T(0);
+            }
+        }
+        __syncthreads();
+        // (B) V_e = window of P along e; loss 2 c_e f V_e
+        for (int j = 1; j <= J; ++j) {
+            const int o = j * se;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (pk[k] >= 0) {
+                    const int a = pk[k] & 0xFFFF;
+                    Pv[k] += sPf[a + o] + sPf[a - o];
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            if (pk[k] >= 0) {
+                const int a = pk[k] & 0xFFFF;
+                const T t = W[k] - c2 * sF[a] * Pv[k];
                 comp_add<T, KAHAN>(acc[k], cmp[k], t);
             }
         }
@@ -176,19 +210,21 @@ __device__ __forceinline__ void fused2d_body(const int N, const int H, const int
     }
 }
 
-template <typename T>
-__host__ __device__ inline size_t buf_elems(int N, int H) {
-    return (size_t)pad2d_rows(N, H) * (size_t)pad2d_stride(N, H);
+// elements of the f buffer; the P buffer follows it
+__host__ __device__ inline size_t buf_f_elems(int N, int H) {
+    return (size_t)pad2d_rows_f(N, H) * (size_t)pad2d_stride(N, H);
+}
+__host__ __device__ inline size_t buf_p_elems(int N, int H) {
+    return (size_t)pad2d_rows_p(N, H) * (size_t)pad2d_stride(N, H);
 }
 
 template <typename T, bool KAHAN, int PPT>
-__global__ void __launch_bounds__(kThreads) k_fused2d_single(PlanDev P, const T* __restrict__ f, T* __restrict__ out,
+__global__ void __launch_bounds__(kThreads, 2) k_fused2d_single(PlanDev P, const T* __restrict__ f, T* __restrict__ out,
                                                              int pairs_per_cta, size_t slot_stride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32 * 4];
-    const size_t be = buf_elems<T>(P.N, P.Ntilde);
     T* sF = reinterpret_cast<T*>(smem_raw);
-    T* sP = sF + be;
+    T* sP = sF + buf_f_elems(P.N, P.Ntilde);
     const int pb = blockIdx.x * pairs_per_cta;
     const int pe = min(pb + pairs_per_cta, P.n_pairs);
     fused2d_body<T, KAHAN, PPT>(P.N, P.Ntilde, P.pairs, P.pair_c, pb, pe, P.h, P.L, f, out + blockIdx.x * slot_stride,
@@ -206,7 +242,7 @@ __global__ void k_reduce_partials(const T* __restrict__ part, int S, int n, T* _
 }
 
 template <typename T, bool KAHAN, int PPT>
-__global__ void __launch_bounds__(kThreads) k_fused2d_batched(BatchDev B, int n_cells, const int* __restrict__ cell_plan,
+__global__ void __launch_bounds__(kThreads, 2) k_fused2d_batched(BatchDev B, int n_cells, const int* __restrict__ cell_plan,
                                                               const int64_t* __restrict__ cell_offset,
                                                               const int* __restrict__ order, int* counter,
                                                               const T* __restrict__ f, T* __restrict__ Q,
@@ -232,9 +268,22 @@ __global__ void __launch_bounds__(kThreads) k_fused2d_batched(BatchDev B, int n_
         const PlanDev P = s_plan;
         const int64_t off = cell_offset[cell];
         T* sF = reinterpret_cast<T*>(smem_raw);
-        T* sP = sF + buf_elems<T>(P.N, P.Ntilde);
-        fused2d_body<T, KAHAN, PPT>(P.N, P.Ntilde, P.pairs, P.pair_c, 0, P.n_pairs, P.h, P.L, f + off, Q + off,
-                                    moments ? moments + (size_t)cell * 4 : nullptr, sF, sP, red);
+        T* sP = sF + buf_f_elems(P.N, P.Ntilde);
+        double* mc = moments ? moments + (size_t)cell * 4 : nullptr;
+        // the smallest body that covers this cell: no predicated-off slots
+        const int need = (P.N * P.N + kThreads - 1) / kThreads;
+        if (need <= 1 || PPT == 1)
+            fused2d_body<T, KAHAN, 1>(P.N, P.Ntilde, P.pairs, P.pair_c, 0, P.n_pairs, P.h, P.L, f + off, Q + off, mc,
+                                      sF, sP, red);
+        else if (need <= 4 || PPT == 4)
+            fused2d_body<T, KAHAN, (PPT < 4 ? PPT : 4)>(P.N, P.Ntilde, P.pairs, P.pair_c, 0, P.n_pairs, P.h, P.L,
+                                                        f + off, Q + off, mc, sF, sP, red);
+        else if (need <= 9 || PPT == 9)
+            fused2d_body<T, KAHAN, (PPT < 9 ? PPT : 9)>(P.N, P.Ntilde, P.pairs, P.pair_c, 0, P.n_pairs, P.h, P.L,
+                                                        f + off, Q + off, mc, sF, sP, red);
+        else
+            fused2d_body<T, KAHAN, PPT>(P.N, P.Ntilde, P.pairs, P.pair_c, 0, P.n_pairs, P.h, P.L, f + off, Q + off,
+                                        mc, sF, sP, red);
         __syncthreads();
     }
 }
@@ -315,7 +364,7 @@ qdvm_status dispatch_batched(const BatchDev& b, int max_ppt, int n_cells, const 
 
 size_t fused2d_smem_bytes(int N, int H, int prec) {
     const size_t es = prec == QDVM_F64 ? sizeof(double) : sizeof(float);
-    return 2 * buf_elems<float>(N, H) * es;
+    return (buf_f_elems(N, H) + buf_p_elems(N, H)) * es;
 }
 
 int fused2d_supported(int N, int H, int prec) {

@@ -6,6 +6,7 @@
 // kernel; the host only sizes allocations.
 #include <math.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 
@@ -209,17 +210,17 @@ __global__ void k_pairs(int n_lines, const int4* lines, const double* c, int4* p
     if (threadIdx.x == 0) *n_out = base;
 }
 
-// 3D: size of e^perp ∩ [-Nt, Nt]^3 \ {0} per line (one block per line).
-__global__ void k_plane_count(int n_lines, const int4* lines, int Nt, int* counts) {
+// Size of e^perp ∩ [-Nt, Nt]^d \ {0} per line (one block per line).
+__global__ void k_plane_count(int d, int n_lines, const int4* lines, int Nt, int* counts) {
     const int4 e = lines[blockIdx.x];
-    const int w = 2 * Nt + 1, total = w * w * w;
+    const int w = 2 * Nt + 1, total = d == 3 ? w * w * w : w * w;
     __shared__ int cnt;
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
     int local = 0;
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
         int v[3];
-        cand_vec(i, 3, Nt, v);
+        cand_vec(i, d, Nt, v);
         bool nz = v[0] | v[1] | v[2];
         local += (nz && v[0] * e.x + v[1] * e.y + v[2] * e.z == 0) ? 1 : 0;
     }
@@ -228,16 +229,17 @@ __global__ void k_plane_count(int n_lines, const int4* lines, int Nt, int* count
     if (threadIdx.x == 0) counts[blockIdx.x] = cnt;
 }
 
-__global__ void k_plane_emit(int n_lines, const int4* lines, int Nt, const int* start, char4* plane) {
+// The plane list of each line in lexicographic order of l (one block per line).
+__global__ void k_plane_emit(int d, int n_lines, const int4* lines, int Nt, const int* start, char4* plane) {
     const int4 e = lines[blockIdx.x];
-    const int w = 2 * Nt + 1, total = w * w * w;
+    const int w = 2 * Nt + 1, total = d == 3 ? w * w * w : w * w;
     int base = start[blockIdx.x];
     for (int c0 = 0; c0 < total; c0 += blockDim.x) {
         int i = c0 + threadIdx.x;
         int v[3] = {0, 0, 0};
         bool ok = false;
         if (i < total) {
-            cand_vec(i, 3, Nt, v);
+            cand_vec(i, d, Nt, v);
             bool nz = v[0] | v[1] | v[2];
             ok = nz && (v[0] * e.x + v[1] * e.y + v[2] * e.z == 0);
         }
@@ -316,35 +318,34 @@ static qdvm_status build_tables(qdvm_plan_s* p) {
             return fail(qdvm_cuda_status(e, "k_pairs"));
         if (got != np || 2 * np != total) return fail(qdvm_fail(QDVM_ERR_CUDA, "2D line pairing is inconsistent"));
         p->n_pairs = np;
-        int64_t terms = 0;
-        for (int i = 0; i < total; ++i) terms += (int64_t)(2 * p->h_lines[i].w) * (2 * p->h_lines[i].w);
-        p->n_terms = terms;
-    } else {
-        if ((e = cudaMalloc(&d_tmp, total * sizeof(int))) != cudaSuccess) return fail(qdvm_cuda_status(e, "plane counts"));
-        k_plane_count<<<total, 256>>>(total, p->d_lines, p->Ntilde, d_tmp);
-        std::vector<int> pc(total);
-        if ((e = cudaMemcpy(pc.data(), d_tmp, total * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
-            return fail(qdvm_cuda_status(e, "k_plane_count"));
-        p->h_plane_start.assign(total + 1, 0);
-        int64_t terms = 0;
-        int mx = 0;
-        for (int i = 0; i < total; ++i) {
-            p->h_plane_start[i + 1] = p->h_plane_start[i] + pc[i];
-            terms += (int64_t)(2 * p->h_lines[i].w) * pc[i];
-            mx = pc[i] > mx ? pc[i] : mx;
-        }
-        p->n_plane = p->h_plane_start[total];
-        p->max_plane = mx;
-        p->n_terms = terms;
-        if ((e = cudaMalloc(&p->d_plane_start, (total + 1) * sizeof(int))) != cudaSuccess)
-            return fail(qdvm_cuda_status(e, "plane start"));
-        if ((e = cudaMalloc(&p->d_plane, (size_t)p->n_plane * sizeof(char4))) != cudaSuccess)
-            return fail(qdvm_cuda_status(e, "plane"));
-        if ((e = cudaMemcpy(p->d_plane_start, p->h_plane_start.data(), (total + 1) * sizeof(int),
-                            cudaMemcpyHostToDevice)) != cudaSuccess)
-            return fail(qdvm_cuda_status(e, "plane start upload"));
-        k_plane_emit<<<total, 256>>>(total, p->d_lines, p->Ntilde, p->d_plane_start, p->d_plane);
+        cudaFree(d_tmp);
+        d_tmp = nullptr;
     }
+    // plane lists e^perp ∩ [-Ntilde, Ntilde]^d \ {0} (in 2D: the segment along e^perp)
+    if ((e = cudaMalloc(&d_tmp, total * sizeof(int))) != cudaSuccess) return fail(qdvm_cuda_status(e, "plane counts"));
+    k_plane_count<<<total, 256>>>(d, total, p->d_lines, p->Ntilde, d_tmp);
+    std::vector<int> pc(total);
+    if ((e = cudaMemcpy(pc.data(), d_tmp, total * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return fail(qdvm_cuda_status(e, "k_plane_count"));
+    p->h_plane_start.assign(total + 1, 0);
+    int64_t terms = 0;
+    int mx = 0;
+    for (int i = 0; i < total; ++i) {
+        p->h_plane_start[i + 1] = p->h_plane_start[i] + pc[i];
+        terms += (int64_t)(2 * p->h_lines[i].w) * pc[i];
+        mx = pc[i] > mx ? pc[i] : mx;
+    }
+    p->n_plane = p->h_plane_start[total];
+    p->max_plane = mx;
+    p->n_terms = terms;
+    if ((e = cudaMalloc(&p->d_plane_start, (total + 1) * sizeof(int))) != cudaSuccess)
+        return fail(qdvm_cuda_status(e, "plane start"));
+    if ((e = cudaMalloc(&p->d_plane, (size_t)std::max(p->n_plane, 1) * sizeof(char4))) != cudaSuccess)
+        return fail(qdvm_cuda_status(e, "plane"));
+    if ((e = cudaMemcpy(p->d_plane_start, p->h_plane_start.data(), (total + 1) * sizeof(int),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(qdvm_cuda_status(e, "plane start upload"));
+    k_plane_emit<<<total, 256>>>(d, total, p->d_lines, p->Ntilde, p->d_plane_start, p->d_plane);
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(qdvm_cuda_status(e, "plan build"));
     return fail(st);
 }

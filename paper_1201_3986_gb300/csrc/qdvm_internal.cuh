@@ -104,16 +104,20 @@ __device__ __forceinline__ void comp_add(T& s, T& c, T x) {
 }
 
 // ------------------------------------------------------------ 2D fused engine
-// Padded on-chip layout of a 2D cell: rows/cols [-H, N+H) with the periodic
-// halo replicated; the row stride is congruent to N modulo 32 so that a warp
+// Padded on-chip layout of a 2D cell.  The f buffer holds rows/cols
+// [-2H, N+2H) with the periodic halo replicated (H = Ntilde): a pair with
+// J = 1 reads f at i +- e +- e^perp, up to 2H away.  The P buffer holds rows
+// [-H, N+H) on the same row stride, so a point's P address is its f address
+// minus H*(stride+1).  The stride is congruent to N modulo 32 so that a warp
 // of 32 consecutive points never hits the same bank twice, even when it
 // straddles two rows (N = 16, 48).
 __host__ __device__ inline int pad2d_stride(int N, int H) {
-    int w = N + 2 * H;
+    int w = N + 4 * H;
     int r = ((N % 32) - (w % 32) + 32) % 32;
     return w + r;
 }
-__host__ __device__ inline int pad2d_rows(int N, int H) { return N + 2 * H; }
+__host__ __device__ inline int pad2d_rows_f(int N, int H) { return N + 4 * H; }
+__host__ __device__ inline int pad2d_rows_p(int N, int H) { return N + 2 * H; }
 
 size_t fused2d_smem_bytes(int N, int H, int prec);
 int fused2d_supported(int N, int H, int prec);
@@ -131,9 +135,10 @@ qdvm_status schedule_launch(const BatchDev& b, int n_cells, const int* cell_plan
 
 int qdvm_num_sms();
 
-// ------------------------------------------------------------ 3D engine
-size_t gen3d_workspace(const BatchDev& b, int n_cells, int prec, bool single);
-qdvm_status gen3d_eval(const BatchDev& b, int n_cells, const int* cell_plan, const int64_t* cell_offset,
-                       const void* f, void* Q, double* moments, int prec, void* ws, size_t ws_bytes, bool single,
-                       cudaStream_t st);
-int gen3d_supported(const qdvm_plan_s* p, int prec);
+// ------------------------------------------------------------ generic engine
+// mode: 0 forward, 1 JVP (aux = tangent), 2 VJP (aux = cotangent)
+enum { QDVM_MODE_FWD = 0, QDVM_MODE_JVP = 1, QDVM_MODE_VJP = 2 };
+size_t engine_workspace(int mode, const BatchDev& b, int n_cells, int prec, bool single);
+qdvm_status engine_run(int mode, const BatchDev& b, int n_cells, const int* cell_plan, const int64_t* cell_offset,
+                       const void* f, const void* aux, void* out, double* moments, int prec, void* ws,
+                       size_t ws_bytes, bool single, cudaStream_t st);
