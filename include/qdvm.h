@@ -146,6 +146,32 @@ qdvm_status qdvm_eval_batched(const qdvm_plan_t* plans, int n_plans, int n_cells
                               const int64_t* cell_offset, const void* f, void* Q, double* moments,
                               int prec, void* workspace, size_t workspace_bytes, void* stream);
 
+/* Largest batch accepted by qdvm_eval_batched_noalloc. */
+#define QDVM_NOALLOC_MAX_CELLS 65536
+
+/* Allocation-free batched 2D evaluation.  The paper has no counterpart: this
+ * is an interface for callers that cannot allocate device memory -- a solver
+ * that owns a fixed device-memory budget and passes the library only its own
+ * arrays, or a plug-in called inside another framework's time loop, where a
+ * cudaMalloc would synchronise the device mid-step.  Same arguments and
+ * results as qdvm_eval_batched, without the workspace: the work counter and
+ * the cell schedule live in a 256 KB array inside the library that every GPU
+ * loading the library keeps until the process exits.
+ *   - Only the on-chip 2D evaluator (all plans d = 2, N <= 64) is covered;
+ *     other plans return QDVM_ERR_UNSUPPORTED.
+ *   - n_cells <= QDVM_NOALLOC_MAX_CELLS, else QDVM_ERR_INVALID_ARG (nothing
+ *     is launched).
+ *   - Allocates nothing (no cudaMalloc / cudaFree / allocating library call).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) once for that device; make that first call
+ *     before any stream capture.
+ *   - All calls share the array (the counter is reset by every call), so
+ *     calls that overlap on the GPU -- on different streams, or from
+ *     different host threads -- race; serialise them. */
+qdvm_status qdvm_eval_batched_noalloc(const qdvm_plan_t* plans, int n_plans, int n_cells, const int* cell_plan,
+                                      const int64_t* cell_offset, const void* f, void* Q, double* moments, int prec,
+                                      void* stream);
+
 /* Directional derivative dQ = Q'(f) df (Q is quadratic in f, eq. (DR)):
  *   dQ = sum_e c_e [ W_e[df] P_e[f] + W_e[f] P_e[df] - df V_e[f] - f V_e[df] ]. */
 qdvm_status qdvm_jvp(qdvm_plan_t plan, const void* f, const void* df, void* dQ, int prec, void* workspace,

@@ -72,6 +72,8 @@ _sig("qdvm_batched_workspace", [_P(_vp), _i, _i, _i, _P(_sz)])
 _sig("qdvm_jvp_batched", [_P(_vp), _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _sz, _vp])
 _sig("qdvm_vjp_batched", [_P(_vp), _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _sz, _vp])
 _sig("qdvm_moments", [_vp, _vp, _i, _vp, _vp])
+_sig("qdvm_eval_batched_noalloc", [_P(_vp), _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp])
+QDVM_NOALLOC_MAX_CELLS = 65536
 _lib.qdvm_status_string.argtypes = [_i]
 _lib.qdvm_status_string.restype = ctypes.c_char_p
 _lib.qdvm_last_error.argtypes = []
@@ -222,6 +224,22 @@ def qdvm_eval_batched(plans, cell_plan: torch.Tensor, cell_offset: torch.Tensor,
                                   _ptr(mom), p, _ptr(ws), 0 if ws is None else ws.numel(), _stream(f.device)),
            "qdvm_eval_batched")
     return Q, mom
+
+
+def qdvm_eval_batched_noalloc(plans, cell_plan: torch.Tensor, cell_offset: torch.Tensor, f: torch.Tensor, Q: torch.Tensor,
+                              moments: torch.Tensor | None, prec="f32_kahan") -> None:
+    """Batched 2D evaluation through the allocation-free entry point: the
+    caller passes every array (f, Q, moments or None); the library uses its
+    own static scratch and allocates nothing."""
+    p = _prec(prec)
+    if cell_plan.dtype != torch.int32 or cell_offset.dtype != torch.int64:
+        raise ValueError("cell_plan must be int32 and cell_offset int64")
+    for t in (f, Q):
+        if t.dtype != _DTYPE[p] or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"f and Q must be contiguous CUDA {_DTYPE[p]} tensors")
+    _check(_lib.qdvm_eval_batched_noalloc(_plan_array(plans), len(plans), int(cell_plan.numel()), _ptr(cell_plan),
+                                          _ptr(cell_offset), _ptr(f), _ptr(Q), _ptr(moments), p, _stream(f.device)),
+           "qdvm_eval_batched_noalloc")
 
 
 def qdvm_jvp(plan: Plan, f: torch.Tensor, df: torch.Tensor, prec="f64", out=None, workspace=None) -> torch.Tensor:

@@ -1,0 +1,82 @@
+// Allocation-free variant of the batched 2D evaluator.
+//
+// Some callers cannot allocate device memory at all: a solver that owns a
+// fixed device-memory budget and hands the library only its own arrays, a
+// plug-in called from inside another framework's time loop where any
+// cudaMalloc would synchronise the device in the middle of a step, or an
+// embedding whose memory manager forbids foreign allocations.  They still
+// pass f, Q, the cell layout and the moments array, but no workspace.  The
+// only scratch the batched 2D evaluator needs (its atomic work counter and
+// the cost-ordered cell list) then lives in the file-scope array below,
+// which every GPU that loads this library holds until the process exits.
+#include <mutex>
+
+#include "qdvm_internal.cuh"
+
+// Scratch layout (the same as the caller-provided workspace of
+// qdvm_eval_batched for the 2D on-chip evaluator): the work counter in the
+// first 256 bytes, then one int per cell for the schedule.  256 KB + 256 B.
+static __device__ __align__(256) int g_batch_scratch[64 + QDVM_NOALLOC_MAX_CELLS];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mutex;
+void* g_scratch_ptr[kMaxDevices] = {nullptr};
+
+// Device address of g_batch_scratch for the current device.  In host code
+// the array's name is only a host-side stand-in, so the address comes from
+// cudaGetSymbolAddress, once per device, with that device current.
+qdvm_status scratch_address(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return qdvm_cuda_status(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return qdvm_fail(QDVM_ERR_UNSUPPORTED, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_batch_scratch);
+        if (e != cudaSuccess || !p) return qdvm_cuda_status(e, "cudaGetSymbolAddress(g_batch_scratch)");
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return QDVM_OK;
+}
+
+}  // namespace
+
+extern "C" qdvm_status qdvm_eval_batched_noalloc(const qdvm_plan_t* plans, int n_plans, int n_cells,
+                                                 const int* cell_plan, const int64_t* cell_offset, const void* f,
+                                                 void* Q, double* moments, int prec, void* stream) {
+    if (n_cells < 0) return qdvm_fail(QDVM_ERR_INVALID_ARG, "n_cells < 0");
+    if (n_cells > QDVM_NOALLOC_MAX_CELLS)
+        return qdvm_fail(QDVM_ERR_INVALID_ARG, "qdvm_eval_batched_noalloc: n_cells exceeds QDVM_NOALLOC_MAX_CELLS "
+                                               "(65536); split the batch or use qdvm_eval_batched with a workspace");
+    if (prec != QDVM_F64 && prec != QDVM_F32 && prec != QDVM_F32_KAHAN)
+        return qdvm_fail(QDVM_ERR_INVALID_ARG, "bad precision");
+    if (!plans || n_plans < 1 || n_plans > QDVM_MAX_BATCH_PLANS)
+        return qdvm_fail(QDVM_ERR_INVALID_ARG, "n_plans must be in [1, QDVM_MAX_BATCH_PLANS]");
+    BatchDev b;
+    for (int i = 0; i < QDVM_MAX_BATCH_PLANS; ++i) b.p[i] = PlanDev();
+    b.n_plans = n_plans;
+    int maxN = 0, maxH = 0;
+    for (int i = 0; i < n_plans; ++i) {
+        if (!qdvm_plan_ok(plans[i])) return qdvm_fail(QDVM_ERR_BAD_PLAN, "bad plan handle in batch");
+        if (plans[i]->d != 2 || !fused2d_supported(plans[i]->N, plans[i]->Ntilde, prec))
+            return qdvm_fail(QDVM_ERR_UNSUPPORTED,
+                             "qdvm_eval_batched_noalloc covers the on-chip 2D evaluator only (d = 2, N <= 64)");
+        b.p[i] = plan_dev(plans[i]);
+        maxN = plans[i]->N > maxN ? plans[i]->N : maxN;
+        maxH = plans[i]->Ntilde > maxH ? plans[i]->Ntilde : maxH;
+    }
+    if (n_cells == 0) return QDVM_OK;
+    if (!cell_plan || !cell_offset || !f || !Q) return qdvm_fail(QDVM_ERR_INVALID_ARG, "NULL device array");
+    if (f == Q) return qdvm_fail(QDVM_ERR_INVALID_ARG, "f must not alias Q");
+    void* scratch = nullptr;
+    qdvm_status s = scratch_address(&scratch);
+    if (s != QDVM_OK) return s;
+    // The schedule kernel zeroes the work counter at the start of every call;
+    // the order list is rewritten in full.
+    return fused2d_eval_batched(b, maxN, maxH, n_cells, cell_plan, cell_offset, f, Q, moments, prec, scratch,
+                                static_cast<cudaStream_t>(stream));
+}
