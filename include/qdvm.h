@@ -52,6 +52,7 @@ extern "C" {
 #endif
 
 typedef struct qdvm_plan_s* qdvm_plan_t;
+typedef struct qdvm_graph_s* qdvm_graph_t;
 
 typedef enum {
     QDVM_OK = 0,
@@ -72,6 +73,20 @@ enum { QDVM_ENGINE_AUTO = 0, QDVM_ENGINE_DIRECT = 1, QDVM_ENGINE_SCAN = 2 };
 
 /* Maximum number of distinct plans in one batched call. */
 #define QDVM_MAX_BATCH_PLANS 16
+
+/* Launch parameters of the evaluators.  They change speed, never the set of
+ * terms summed; results agree to rounding (and bit for bit on integer data).
+ *   threads     CTA size of the on-chip 2D evaluator: 256 or 512.
+ *   direct_j    2D pairs with window half-length J <= direct_j (0, 1 or 2)
+ *               read V_e straight from the cell ((2J)^2 loads, no barrier);
+ *               longer windows go through the on-chip P buffer.
+ *   line_chunks generic (3D) engine: chunks of lines per cell, each a work
+ *               item summed afterwards in a fixed order; 0 = automatic. */
+typedef struct {
+    int threads;
+    int direct_j;
+    int line_chunks;
+} qdvm_tuning;
 
 /* ------------------------------------------------------------------ plans */
 
@@ -110,6 +125,11 @@ qdvm_status qdvm_plan_info(qdvm_plan_t plan, int* d, int* N, int* Ntilde, int* m
  * |e|_inf then lexicographically), J (window half-length), c (weight). */
 qdvm_status qdvm_plan_lines(qdvm_plan_t plan, int* dirs, int* J, double* c);
 
+/* Read / set a plan's launch parameters (defaults: 256, 2, 0).  A batched
+ * call uses the parameters of plans[0].  Errors: BAD_PLAN, INVALID_ARG. */
+qdvm_status qdvm_plan_get_tuning(qdvm_plan_t plan, qdvm_tuning* t);
+qdvm_status qdvm_plan_set_tuning(qdvm_plan_t plan, const qdvm_tuning* t);
+
 /* Bytes of workspace that qdvm_eval, qdvm_jvp and qdvm_vjp need for this plan
  * and precision (0 is a valid answer).  Errors: BAD_PLAN, INVALID_ARG,
  * UNSUPPORTED (no engine for this plan and precision). */
@@ -145,6 +165,27 @@ qdvm_status qdvm_eval(qdvm_plan_t plan, const void* f, void* Q, int prec, void* 
 qdvm_status qdvm_eval_batched(const qdvm_plan_t* plans, int n_plans, int n_cells, const int* cell_plan,
                               const int64_t* cell_offset, const void* f, void* Q, double* moments,
                               int prec, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Autotuner: time every candidate launch configuration of
+ * qdvm_eval_batched on this batch (CUDA events on `stream`, synchronises the
+ * host; not for a hot path), keep the fastest in every plan of the batch and
+ * return it in *best (may be NULL).  Arguments as for qdvm_eval_batched; Q
+ * is overwritten.  Candidates that would need more workspace than given are
+ * skipped. */
+qdvm_status qdvm_tune_batched(const qdvm_plan_t* plans, int n_plans, int n_cells, const int* cell_plan,
+                              const int64_t* cell_offset, const void* f, void* Q, int prec, void* workspace,
+                              size_t workspace_bytes, void* stream, qdvm_tuning* best);
+
+/* Capture one qdvm_eval_batched call (same arguments, all pointers fixed)
+ * into an executable CUDA graph; qdvm_graph_launch replays it on a stream
+ * (one launch per step), qdvm_graph_destroy releases it.  Capture itself
+ * launches nothing; the graph owns no device memory (the workspace stays the
+ * caller's and must outlive the graph). */
+qdvm_status qdvm_graph_capture_batched(qdvm_graph_t* out, const qdvm_plan_t* plans, int n_plans, int n_cells,
+                                       const int* cell_plan, const int64_t* cell_offset, const void* f, void* Q,
+                                       double* moments, int prec, void* workspace, size_t workspace_bytes);
+qdvm_status qdvm_graph_launch(qdvm_graph_t graph, void* stream);
+qdvm_status qdvm_graph_destroy(qdvm_graph_t graph);
 
 /* Largest batch accepted by qdvm_eval_batched_noalloc. */
 #define QDVM_NOALLOC_MAX_CELLS 65536

@@ -72,6 +72,16 @@ _sig("qdvm_batched_workspace", [_P(_vp), _i, _i, _i, _P(_sz)])
 _sig("qdvm_jvp_batched", [_P(_vp), _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _sz, _vp])
 _sig("qdvm_vjp_batched", [_P(_vp), _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _sz, _vp])
 _sig("qdvm_moments", [_vp, _vp, _i, _vp, _vp])
+class QdvmTuning(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int), ("direct_j", ctypes.c_int), ("line_chunks", ctypes.c_int)]
+
+
+_sig("qdvm_plan_get_tuning", [_vp, _P(QdvmTuning)])
+_sig("qdvm_plan_set_tuning", [_vp, _P(QdvmTuning)])
+_sig("qdvm_tune_batched", [_P(_vp), _i, _i, _vp, _vp, _vp, _vp, _i, _vp, _sz, _vp, _P(QdvmTuning)])
+_sig("qdvm_graph_capture_batched", [_P(_vp), _P(_vp), _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _sz])
+_sig("qdvm_graph_launch", [_vp, _vp])
+_sig("qdvm_graph_destroy", [_vp])
 _sig("qdvm_eval_batched_noalloc", [_P(_vp), _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp])
 QDVM_NOALLOC_MAX_CELLS = 65536
 _lib.qdvm_status_string.argtypes = [_i]
@@ -147,6 +157,18 @@ class Plan:
         b = ctypes.c_size_t()
         _check(_lib.qdvm_eval_workspace(self.handle, _prec(prec), ctypes.byref(b)), "qdvm_eval_workspace")
         return b.value
+
+    def tuning(self) -> dict:
+        t = QdvmTuning()
+        _check(_lib.qdvm_plan_get_tuning(self.handle, ctypes.byref(t)), "qdvm_plan_get_tuning")
+        return {"threads": t.threads, "direct_j": t.direct_j, "line_chunks": t.line_chunks}
+
+    def set_tuning(self, threads=None, direct_j=None, line_chunks=None) -> None:
+        cur = self.tuning()
+        t = QdvmTuning(cur["threads"] if threads is None else int(threads),
+                       cur["direct_j"] if direct_j is None else int(direct_j),
+                       cur["line_chunks"] if line_chunks is None else int(line_chunks))
+        _check(_lib.qdvm_plan_set_tuning(self.handle, ctypes.byref(t)), "qdvm_plan_set_tuning")
 
     @property
     def shape(self):
@@ -224,6 +246,50 @@ def qdvm_eval_batched(plans, cell_plan: torch.Tensor, cell_offset: torch.Tensor,
                                   _ptr(mom), p, _ptr(ws), 0 if ws is None else ws.numel(), _stream(f.device)),
            "qdvm_eval_batched")
     return Q, mom
+
+
+class BatchedGraph:
+    """qdvm_eval_batched captured once into a CUDA graph (fixed tensors);
+    ``launch()`` replays it on the current stream."""
+
+    def __init__(self, plans, cell_plan, cell_offset, f, Q, moments, prec="f32_kahan", workspace=None):
+        p = _prec(prec)
+        n_cells = int(cell_plan.numel())
+        self._keep = (plans, cell_plan, cell_offset, f, Q, moments)
+        self.workspace = workspace if workspace is not None else _workspace(
+            batched_workspace_bytes(plans, n_cells, p), f.device)
+        self.handle = None
+        h = ctypes.c_void_p()
+        _check(_lib.qdvm_graph_capture_batched(ctypes.byref(h), _plan_array(plans), len(plans), n_cells,
+                                               _ptr(cell_plan), _ptr(cell_offset), _ptr(f), _ptr(Q), _ptr(moments), p,
+                                               _ptr(self.workspace),
+                                               0 if self.workspace is None else self.workspace.numel()),
+               "qdvm_graph_capture_batched")
+        self.handle = h
+        self.device = f.device
+
+    def launch(self):
+        _check(_lib.qdvm_graph_launch(self.handle, _stream(self.device)), "qdvm_graph_launch")
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.qdvm_graph_destroy(self.handle)
+            self.handle = None
+
+
+def qdvm_tune_batched(plans, cell_plan: torch.Tensor, cell_offset: torch.Tensor, f: torch.Tensor, prec="f32_kahan",
+                      workspace: torch.Tensor | None = None) -> dict:
+    """Time the candidate launch configurations on this batch, keep the
+    fastest in every plan and return it."""
+    p = _prec(prec)
+    n_cells = int(cell_plan.numel())
+    Q = torch.empty_like(f)
+    ws = workspace if workspace is not None else _workspace(batched_workspace_bytes(plans, n_cells, p), f.device)
+    t = QdvmTuning()
+    _check(_lib.qdvm_tune_batched(_plan_array(plans), len(plans), n_cells, _ptr(cell_plan), _ptr(cell_offset), _ptr(f),
+                                  _ptr(Q), p, _ptr(ws), 0 if ws is None else ws.numel(), _stream(f.device),
+                                  ctypes.byref(t)), "qdvm_tune_batched")
+    return {"threads": t.threads, "direct_j": t.direct_j, "line_chunks": t.line_chunks}
 
 
 def qdvm_eval_batched_noalloc(plans, cell_plan: torch.Tensor, cell_offset: torch.Tensor, f: torch.Tensor, Q: torch.Tensor,

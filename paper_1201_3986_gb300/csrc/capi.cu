@@ -1,5 +1,6 @@
 // C ABI entry points: argument checks and dispatch to the engines.
 #include <algorithm>
+#include <vector>
 
 #include "qdvm_internal.cuh"
 
@@ -39,13 +40,13 @@ extern "C" qdvm_status qdvm_eval_workspace(qdvm_plan_t p, int prec, size_t* byte
     if (!qdvm_plan_ok(p)) return qdvm_fail(QDVM_ERR_BAD_PLAN, "bad plan handle");
     if (!prec_ok(prec) || !bytes) return qdvm_fail(QDVM_ERR_INVALID_ARG, "bad precision or NULL bytes");
     const BatchDev b = single_batch(p);
-    const size_t der = std::max(engine_workspace(QDVM_MODE_JVP, b, 1, prec, true),
-                                engine_workspace(QDVM_MODE_VJP, b, 1, prec, true));
+    const size_t der = std::max(engine_workspace(QDVM_MODE_JVP, b, 1, prec, true, p->tune.line_chunks),
+                                engine_workspace(QDVM_MODE_VJP, b, 1, prec, true, p->tune.line_chunks));
     if (p->d == 2 && fused2d_supported(p->N, p->Ntilde, prec)) {
         *bytes = std::max(fused2d_single_workspace(p, prec), der);
         return QDVM_OK;
     }
-    *bytes = std::max(engine_workspace(QDVM_MODE_FWD, b, 1, prec, true), der);
+    *bytes = std::max(engine_workspace(QDVM_MODE_FWD, b, 1, prec, true, p->tune.line_chunks), der);
     return QDVM_OK;
 }
 
@@ -58,7 +59,7 @@ extern "C" qdvm_status qdvm_eval(qdvm_plan_t p, const void* f, void* Q, int prec
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (p->d == 2 && fused2d_supported(p->N, p->Ntilde, prec)) return fused2d_eval_single(p, f, Q, prec, ws, ws_bytes, st);
     return engine_run(QDVM_MODE_FWD, single_batch(p), 1, nullptr, nullptr, f, nullptr, Q, nullptr, prec, ws, ws_bytes,
-                      true, st);
+                      true, p->tune.line_chunks, st);
 }
 
 static bool all_fused2d(const qdvm_plan_t* plans, int n_plans, int d, int prec) {
@@ -74,10 +75,10 @@ extern "C" qdvm_status qdvm_batched_workspace(const qdvm_plan_t* plans, int n_pl
     int d = 0;
     qdvm_status s = build_batch(plans, n_plans, &b, &d);
     if (s != QDVM_OK) return s;
-    const size_t der = std::max(engine_workspace(QDVM_MODE_JVP, b, n_cells, prec, false),
-                                engine_workspace(QDVM_MODE_VJP, b, n_cells, prec, false));
+    const size_t der = std::max(engine_workspace(QDVM_MODE_JVP, b, n_cells, prec, false, plans[0]->tune.line_chunks),
+                                engine_workspace(QDVM_MODE_VJP, b, n_cells, prec, false, plans[0]->tune.line_chunks));
     const size_t fwd = all_fused2d(plans, n_plans, d, prec) ? 256 + round256((size_t)std::max(n_cells, 1) * sizeof(int))
-                                                            : engine_workspace(QDVM_MODE_FWD, b, n_cells, prec, false);
+                                                            : engine_workspace(QDVM_MODE_FWD, b, n_cells, prec, false, plans[0]->tune.line_chunks);
     *bytes = std::max(fwd, der);
     return QDVM_OK;
 }
@@ -99,15 +100,10 @@ extern "C" qdvm_status qdvm_eval_batched(const qdvm_plan_t* plans, int n_plans, 
     if (s != QDVM_OK) return s;
     if (!ws || ws_bytes < need) return qdvm_fail(QDVM_ERR_INVALID_ARG, "workspace too small for qdvm_eval_batched");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int maxN = 0, maxH = 0;
-    for (int i = 0; i < n_plans; ++i) {
-        maxN = std::max(maxN, plans[i]->N);
-        maxH = std::max(maxH, plans[i]->Ntilde);
-    }
     if (all_fused2d(plans, n_plans, d, prec))
-        return fused2d_eval_batched(b, maxN, maxH, n_cells, cell_plan, cell_offset, f, Q, moments, prec, ws, st);
+        return fused2d_eval_batched(b, plans[0]->tune, n_cells, cell_plan, cell_offset, f, Q, moments, prec, ws, st);
     return engine_run(QDVM_MODE_FWD, b, n_cells, cell_plan, cell_offset, f, nullptr, Q, moments, prec, ws, ws_bytes,
-                      false, st);
+                      false, plans[0]->tune.line_chunks, st);
 }
 
 extern "C" qdvm_status qdvm_moments(qdvm_plan_t p, const void* Q, int prec, double* m, void* stream) {
@@ -123,7 +119,7 @@ static qdvm_status derivative_single(int mode, qdvm_plan_t p, const void* f, con
     if (!f || !a || !out) return qdvm_fail(QDVM_ERR_INVALID_ARG, "NULL device array");
     if (out == f || out == a) return qdvm_fail(QDVM_ERR_INVALID_ARG, "the output must not alias an input");
     return engine_run(mode, single_batch(p), 1, nullptr, nullptr, f, a, out, nullptr, prec, ws, ws_bytes, true,
-                      static_cast<cudaStream_t>(stream));
+                      p->tune.line_chunks, static_cast<cudaStream_t>(stream));
 }
 
 static qdvm_status derivative_batched(int mode, const qdvm_plan_t* plans, int n_plans, int n_cells,
@@ -139,7 +135,7 @@ static qdvm_status derivative_batched(int mode, const qdvm_plan_t* plans, int n_
     if (!cell_plan || !cell_offset || !f || !a || !out) return qdvm_fail(QDVM_ERR_INVALID_ARG, "NULL device array");
     if (out == f || out == a) return qdvm_fail(QDVM_ERR_INVALID_ARG, "the output must not alias an input");
     return engine_run(mode, b, n_cells, cell_plan, cell_offset, f, a, out, nullptr, prec, ws, ws_bytes, false,
-                      static_cast<cudaStream_t>(stream));
+                      plans[0]->tune.line_chunks, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" qdvm_status qdvm_jvp(qdvm_plan_t p, const void* f, const void* df, void* dQ, int prec, void* ws,
@@ -164,4 +160,69 @@ extern "C" qdvm_status qdvm_vjp_batched(const qdvm_plan_t* plans, int n_plans, i
                                         void* ws, size_t ws_bytes, void* stream) {
     return derivative_batched(QDVM_MODE_VJP, plans, n_plans, n_cells, cell_plan, cell_offset, f, g, grad, prec, ws,
                               ws_bytes, stream);
+}
+
+extern "C" qdvm_status qdvm_tune_batched(const qdvm_plan_t* plans, int n_plans, int n_cells, const int* cell_plan,
+                                         const int64_t* cell_offset, const void* f, void* Q, int prec, void* ws,
+                                         size_t ws_bytes, void* stream, qdvm_tuning* best) {
+    if (!prec_ok(prec)) return qdvm_fail(QDVM_ERR_INVALID_ARG, "bad precision");
+    BatchDev b;
+    int d = 0;
+    qdvm_status s = build_batch(plans, n_plans, &b, &d);
+    if (s != QDVM_OK) return s;
+    if (n_cells <= 0) return qdvm_fail(QDVM_ERR_INVALID_ARG, "nothing to tune (n_cells <= 0)");
+    const qdvm_tuning saved = plans[0]->tune;
+    std::vector<qdvm_tuning> cand;
+    if (all_fused2d(plans, n_plans, d, prec)) {
+        for (int th : {256, 512})
+            for (int dj : {0, 1, 2}) cand.push_back(qdvm_tuning{th, dj, saved.line_chunks});
+    } else {
+        for (int c : {0, 1, 2, 3, 4, 6, 8}) {
+            if (engine_workspace(QDVM_MODE_FWD, b, n_cells, prec, false, c) <= ws_bytes)
+                cand.push_back(qdvm_tuning{saved.threads, saved.direct_j, c});
+        }
+    }
+    if (cand.empty()) return qdvm_fail(QDVM_ERR_INVALID_ARG, "workspace too small for every candidate");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    QDVM_CUDA_TRY(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return qdvm_cuda_status(ce, "cudaEventCreate");
+    }
+    float best_ms = 1e30f;
+    qdvm_tuning best_t = saved;
+    qdvm_status rs = QDVM_OK;
+    for (const qdvm_tuning& t : cand) {
+        for (int i = 0; i < n_plans; ++i) plans[i]->tune = t;
+        float times[3];
+        for (int rep = 0; rep < 4 && rs == QDVM_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            rs = qdvm_eval_batched(plans, n_plans, n_cells, cell_plan, cell_offset, f, Q, nullptr, prec, ws, ws_bytes,
+                                   stream);
+            cudaEventRecord(e1, st);
+            if (rs != QDVM_OK) break;
+            ce = cudaEventSynchronize(e1);
+            if (ce != cudaSuccess) {
+                rs = qdvm_cuda_status(ce, "tuning run");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) times[rep - 1] = ms;  // first run warms up
+        }
+        if (rs != QDVM_OK) break;
+        std::sort(times, times + 3);
+        if (times[1] < best_ms) {
+            best_ms = times[1];
+            best_t = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int i = 0; i < n_plans; ++i) plans[i]->tune = rs == QDVM_OK ? best_t : saved;
+    if (rs != QDVM_OK) return rs;
+    if (best) *best = best_t;
+    return QDVM_OK;
 }

@@ -35,7 +35,7 @@ void reduce(const Layout& g, const BatchDev& b, int n_cells, const int* cp, cons
 
 }  // namespace
 
-Layout make_layout(int mode, const BatchDev& b, int n_cells, int prec, bool single) {
+Layout make_layout(int mode, const BatchDev& b, int n_cells, int prec, bool single, int chunks) {
     Layout g{};
     g.mode = mode;
     const size_t es = prec == QDVM_F64 ? sizeof(double) : sizeof(float);
@@ -66,6 +66,7 @@ Layout make_layout(int mode, const BatchDev& b, int n_cells, int prec, bool sing
     else
         g.C = std::max(1, std::min(maxLines, (4 * slots + nc - 1) / nc));
     if (!single && nc >= 2 * slots) g.C = 1;
+    if (chunks > 0) g.C = std::max(1, std::min(maxLines, chunks));
     const long items = (long)nc * g.C;
     g.grid = (int)std::max(1L, std::min(items, (long)slots));
     g.scr_stride = a256(((size_t)n_fields(mode, g.stage) * padn + (kahan ? nn : 0)) * es);
@@ -78,16 +79,16 @@ Layout make_layout(int mode, const BatchDev& b, int n_cells, int prec, bool sing
 
 }  // namespace eng
 
-size_t engine_workspace(int mode, const BatchDev& b, int n_cells, int prec, bool single) {
-    return eng::make_layout(mode, b, single ? 1 : n_cells, prec, single).total;
+size_t engine_workspace(int mode, const BatchDev& b, int n_cells, int prec, bool single, int chunks) {
+    return eng::make_layout(mode, b, single ? 1 : n_cells, prec, single, chunks).total;
 }
 
 qdvm_status engine_run(int mode, const BatchDev& b, int n_cells, const int* cell_plan, const int64_t* cell_offset,
                        const void* f, const void* aux, void* out, double* moments, int prec, void* ws,
-                       size_t ws_bytes, bool single, cudaStream_t st) {
+                       size_t ws_bytes, bool single, int chunks, cudaStream_t st) {
     using namespace eng;
     const int nc = single ? 1 : n_cells;
-    const Layout g = make_layout(mode, b, nc, prec, single);
+    const Layout g = make_layout(mode, b, nc, prec, single, chunks);
     if (!ws || ws_bytes < g.total) return qdvm_fail(QDVM_ERR_INVALID_ARG, "workspace too small for the line engine");
     char* base = static_cast<char*>(ws);
     int* counter = reinterpret_cast<int*>(base);

@@ -58,7 +58,7 @@ __device__ __forceinline__ void fused2d_body(const int N, const int H, const int
                                              const double* __restrict__ pair_c, const int pb, const int pe,
                                              const double h, const double L, const T* __restrict__ fcell,
                                              T* __restrict__ qcell, double* __restrict__ mom, T* __restrict__ sF,
-                                             T* __restrict__ sP, double* red) {
+                                             T* __restrict__ sP, double* red, const int jd) {
     const int RS = pad2d_stride(N, H), RF = pad2d_rows_f(N, H), HF = 2 * H;
     const int NT = blockDim.x, tid = threadIdx.x;
     const int NN = N * N;
@@ -109,19 +109,43 @@ __device__ __forceinline__ void fused2d_body(const int N, const int H, const int
         const int se = e.x * RS + e.y;   // +e       (axis 0 = rows, axis 1 = columns)
         const int sp = -e.y * RS + e.x;  // +e^perp = (-e1, e0)
         const int J = e.z;
-        if (J == 1) {
-            // one step along each line: V_e(i) = sum of f at i +- e +- e^perp,
-            // read directly from the cell -- no P buffer, no barrier
-            const int d1 = se + sp, d2 = se - sp;
+        if (J <= jd) {
+            // short windows: V_e(i) = sum_{j,j'} f(i + j e + j' e^perp) read
+            // directly from the cell ((2J)^2 loads, |j e + j' e^perp|_inf <= 2H)
+            // -- no P buffer, no barrier
+            if (J == 1) {
+                const int d1 = se + sp, d2 = se - sp;
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                if (pk[k] >= 0) {
-                    const int a = pk[k] & 0xFFFF;
-                    const T w = sF[a + se] + sF[a - se];
-                    const T pp = sF[a + sp] + sF[a - sp];
-                    const T v = (sF[a + d1] + sF[a - d1]) + (sF[a + d2] + sF[a - d2]);
-                    const T t = c2 * w * pp - c2 * sF[a] * v;
-                    comp_add<T, KAHAN>(acc[k], cmp[k], t);
+                for (int k = 0; k < PPT; ++k) {
+                    if (pk[k] >= 0) {
+                        const int a = pk[k] & 0xFFFF;
+                        const T w = sF[a + se] + sF[a - se];
+                        const T pp = sF[a + sp] + sF[a - sp];
+                        const T v = (sF[a + d1] + sF[a - d1]) + (sF[a + d2] + sF[a - d2]);
+                        const T t = c2 * w * pp - c2 * sF[a] * v;
+                        comp_add<T, KAHAN>(acc[k], cmp[k], t);
+                    }
+                }
+            } else {  // J == 2
+                const int se2 = 2 * se, sp2 = 2 * sp;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    if (pk[k] >= 0) {
+                        const int a = pk[k] & 0xFFFF;
+                        const T w = (sF[a + se] + sF[a - se]) + (sF[a + se2] + sF[a - se2]);
+                        const T pp = (sF[a + sp] + sF[a - sp]) + (sF[a + sp2] + sF[a - sp2]);
+                        T v = T(0);
+#pragma unroll
+                        for (int j = 1; j <= 2; ++j) {
+#pragma unroll
+                            for (int jp = 1; jp <= 2; ++jp) {
+                                const int d1 = j * se + jp * sp, d2 = j * se - jp * sp;
+                                v += (sF[a + d1] + sF[a - d1]) + (sF[a + d2] + sF[a - d2]);
+                            }
+                        }
+                        const T t = c2 * w * pp - c2 * sF[a] * v;
+                        comp_add<T, KAHAN>(acc[k], cmp[k], t);
+                    }
                 }
             }
             continue;
@@ -210,6 +234,175 @@ __device__ __forceinline__ void fused2d_body(const int N, const int H, const int
     }
 }
 
+// Cell body specialised for a compile-time N and H = Ntilde (the common cell
+// sizes with the default truncation).  Thread t owns column x = t mod N and
+// rows y0 + k R (R = rows per step), so its k-th point sits k*R*stride words
+// after its first: one address add per window offset serves all of the
+// thread's points, each gather being a load with an immediate offset.
+template <int N, int H>
+struct Geo2 {
+    static constexpr int HF = 2 * H;
+    static constexpr int W = N + 4 * H;
+    static constexpr int RS = W + (((N % 32) - (W % 32) + 32) % 32);
+};
+
+template <typename T, bool KAHAN, int N, int H, int NT>
+__device__ __forceinline__ void fixed_body(const int4* __restrict__ pairs, const double* __restrict__ pair_c,
+                                           const int pb, const int pe, const double h, const double L,
+                                           const T* __restrict__ fcell, T* __restrict__ qcell,
+                                           double* __restrict__ mom, T* __restrict__ sF, T* __restrict__ sP,
+                                           double* red, const int jd) {
+    using G = Geo2<N, H>;
+    constexpr int RS = G::RS, HF = G::HF, WF = G::W;
+    constexpr int R = (NT / N < N) ? NT / N : N;  // rows per step
+    constexpr int PPT = (N + R - 1) / R;          // points per thread
+    constexpr int ACT = R * N;                    // threads that own points
+    constexpr int DK = R * RS;                    // address step between a thread's points
+    constexpr bool PARTIAL = (N % R) != 0;
+    static_assert(pad2d_rows_f(N, H) == WF, "layout");
+    const int tid = threadIdx.x;
+    T* const sPf = sP - (H * RS + H);
+
+    for (int p = tid; p < WF * WF; p += NT) {
+        const int py = p / WF, px = p - py * WF;
+        int sy = py - HF, sx = px - HF;
+        sy += sy < 0 ? N : 0;
+        sy -= sy >= N ? N : 0;
+        sx += sx < 0 ? N : 0;
+        sx -= sx >= N ? N : 0;
+        sF[py * RS + px] = fcell[sy * N + sx];
+    }
+    const bool active = tid < ACT;
+    const int x = tid % N, y0 = tid / N;
+    const int a0 = (y0 + HF) * RS + x + HF;
+    const bool last_ok = !PARTIAL || (y0 + (PPT - 1) * R < N);
+    const int ax = x < H ? N : (x >= N - H ? -N : 0);  // column image offset of P
+    T acc[PPT], cmp[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        acc[k] = T(0);
+        cmp[k] = T(0);
+    }
+    __syncthreads();
+
+    for (int pr = pb; pr < pe; ++pr) {
+        const int4 e = pairs[pr];
+        const T c2 = (T)(2.0 * pair_c[pr]);
+        const int se = e.x * RS + e.y;
+        const int sp = -e.y * RS + e.x;
+        const int J = e.z;
+        if (J <= jd) {
+            if (active) {
+                T w[PPT], pp[PPT], v[PPT];
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) w[k] = pp[k] = v[k] = T(0);
+                const T* b;
+#define QDVM_GATHER(arr, off)                                                           \
+    b = sF + a0 + (off);                                                                \
+    _Pragma("unroll") for (int k = 0; k < PPT; ++k) if (k < PPT - 1 || last_ok) arr[k] += b[k * DK];
+                for (int j = 1; j <= J; ++j) {
+                    QDVM_GATHER(w, j * se)
+                    QDVM_GATHER(w, -j * se)
+                    QDVM_GATHER(pp, j * sp)
+                    QDVM_GATHER(pp, -j * sp)
+                    for (int jp = 1; jp <= J; ++jp) {
+                        QDVM_GATHER(v, j * se + jp * sp)
+                        QDVM_GATHER(v, -j * se - jp * sp)
+                        QDVM_GATHER(v, j * se - jp * sp)
+                        QDVM_GATHER(v, -j * se + jp * sp)
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    if (k < PPT - 1 || last_ok) {
+                        const T t = c2 * w[k] * pp[k] - c2 * sF[a0 + k * DK] * v[k];
+                        comp_add<T, KAHAN>(acc[k], cmp[k], t);
+                    }
+                }
+            }
+            continue;
+        }
+        // (A) W_e and P = W_{e^perp} into registers and the P buffer
+        T W[PPT], Pv[PPT];
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) W[k] = Pv[k] = T(0);
+        if (active) {
+            const T* b;
+            for (int j = 1; j <= J; ++j) {
+                QDVM_GATHER(W, j * se)
+                QDVM_GATHER(W, -j * se)
+                QDVM_GATHER(Pv, j * sp)
+                QDVM_GATHER(Pv, -j * sp)
+            }
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (k < PPT - 1 || last_ok) {
+                    const int y = y0 + k * R;
+                    const int a = a0 + k * DK;
+                    const int ay = y < H ? N * RS : (y >= N - H ? -N * RS : 0);
+                    sPf[a] = Pv[k];
+                    if (ay) sPf[a + ay] = Pv[k];
+                    if (ax) sPf[a + ax] = Pv[k];
+                    if (ay && ax) sPf[a + ay + ax] = Pv[k];
+                    W[k] = c2 * W[k] * Pv[k];
+                    Pv[k] = T(0);
+                }
+            }
+        }
+        __syncthreads();
+        // (B) V_e = window of P along e
+        if (active) {
+            const T* b;
+            for (int j = 1; j <= J; ++j) {
+                b = sPf + a0 + j * se;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k)
+                    if (k < PPT - 1 || last_ok) Pv[k] += b[k * DK];
+                b = sPf + a0 - j * se;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k)
+                    if (k < PPT - 1 || last_ok) Pv[k] += b[k * DK];
+            }
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (k < PPT - 1 || last_ok) {
+                    const T t = W[k] - c2 * sF[a0 + k * DK] * Pv[k];
+                    comp_add<T, KAHAN>(acc[k], cmp[k], t);
+                }
+            }
+        }
+        __syncthreads();
+    }
+#undef QDVM_GATHER
+
+    double m[4] = {0.0, 0.0, 0.0, 0.0};
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            if (k < PPT - 1 || last_ok) {
+                const int y = y0 + k * R;
+                const T q = KAHAN ? acc[k] + cmp[k] : acc[k];
+                qcell[y * N + x] = q;
+                if (mom) {
+                    const double v0 = -L + y * h, v1 = -L + x * h, qd = (double)q;
+                    m[0] += qd;
+                    m[1] += qd * v0;
+                    m[2] += qd * v1;
+                    m[3] += qd * (v0 * v0 + v1 * v1);
+                }
+            }
+        }
+    }
+    if (mom) {
+        block_reduce_fixed<4>(m, red);
+        if (tid == 0) {
+            const double h2 = h * h;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) mom[i] = h2 * m[i];
+        }
+    }
+}
+
 // elements of the f buffer; the P buffer follows it
 __host__ __device__ inline size_t buf_f_elems(int N, int H) {
     return (size_t)pad2d_rows_f(N, H) * (size_t)pad2d_stride(N, H);
@@ -218,17 +411,58 @@ __host__ __device__ inline size_t buf_p_elems(int N, int H) {
     return (size_t)pad2d_rows_p(N, H) * (size_t)pad2d_stride(N, H);
 }
 
-template <typename T, bool KAHAN, int PPT>
-__global__ void __launch_bounds__(kThreads, 2) k_fused2d_single(PlanDev P, const T* __restrict__ f, T* __restrict__ out,
-                                                             int pairs_per_cta, size_t slot_stride) {
+// Points per thread instantiated for a CTA of NT threads (cells up to 64^2).
+template <int NT>
+__host__ __device__ constexpr int ppt_max() { return NT == 256 ? 16 : 8; }
+__host__ __device__ inline int ppt_pick(int NT, int need) {
+    if (NT == 256) return need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : need <= 9 ? 9 : 16;
+    return need <= 1 ? 1 : need <= 2 ? 2 : need <= 5 ? 5 : 8;
+}
+
+// One cell with the smallest body that covers it (no predicated-off slots).
+template <typename T, bool KAHAN, int NT>
+__device__ __forceinline__ void run_cell(const PlanDev& P, int pb, int pe, const T* f, T* q, double* mom, T* sF, T* sP,
+                                         double* red, int jd) {
+    // the common cell sizes with the default truncation floor(N/(3+sqrt 2))
+#define QDVM_FIXED(NN, HH)                                                                                  \
+    if (P.N == NN && P.Ntilde == HH) {                                                                      \
+        fixed_body<T, KAHAN, NN, HH, NT>(P.pairs, P.pair_c, pb, pe, P.h, P.L, f, q, mom, sF, sP, red, jd); \
+        return;                                                                                             \
+    }
+    QDVM_FIXED(64, 14)
+    QDVM_FIXED(48, 10)
+    QDVM_FIXED(32, 7)
+    QDVM_FIXED(16, 3)
+#undef QDVM_FIXED
+    const int k = ppt_pick(NT, (P.N * P.N + NT - 1) / NT);
+#define QDVM_BODY(K)                                                                                          \
+    fused2d_body<T, KAHAN, K>(P.N, P.Ntilde, P.pairs, P.pair_c, pb, pe, P.h, P.L, f, q, mom, sF, sP, red, jd); \
+    return
+    if (NT == 256) {
+        if (k == 1) { QDVM_BODY(1); }
+        if (k == 2) { QDVM_BODY(2); }
+        if (k == 4) { QDVM_BODY(4); }
+        if (k == 9) { QDVM_BODY(9); }
+        QDVM_BODY(ppt_max<NT>());
+    } else {
+        if (k == 1) { QDVM_BODY(1); }
+        if (k == 2) { QDVM_BODY(2); }
+        if (k == 5) { QDVM_BODY(5); }
+        QDVM_BODY(ppt_max<NT>());
+    }
+#undef QDVM_BODY
+}
+
+template <typename T, bool KAHAN, int NT>
+__global__ void __launch_bounds__(NT, 2) k_fused2d_single(PlanDev P, const T* __restrict__ f, T* __restrict__ out,
+                                                          int pairs_per_cta, size_t slot_stride, int jd) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32 * 4];
     T* sF = reinterpret_cast<T*>(smem_raw);
     T* sP = sF + buf_f_elems(P.N, P.Ntilde);
     const int pb = blockIdx.x * pairs_per_cta;
     const int pe = min(pb + pairs_per_cta, P.n_pairs);
-    fused2d_body<T, KAHAN, PPT>(P.N, P.Ntilde, P.pairs, P.pair_c, pb, pe, P.h, P.L, f, out + blockIdx.x * slot_stride,
-                                nullptr, sF, sP, red);
+    run_cell<T, KAHAN, NT>(P, pb, pe, f, out + blockIdx.x * slot_stride, nullptr, sF, sP, red, jd);
 }
 
 // Deterministic sum of S partial results (fixed order s = 0..S-1).
@@ -241,12 +475,12 @@ __global__ void k_reduce_partials(const T* __restrict__ part, int S, int n, T* _
     Q[i] = KAHAN ? s + c : s;
 }
 
-template <typename T, bool KAHAN, int PPT>
-__global__ void __launch_bounds__(kThreads, 2) k_fused2d_batched(BatchDev B, int n_cells, const int* __restrict__ cell_plan,
-                                                              const int64_t* __restrict__ cell_offset,
-                                                              const int* __restrict__ order, int* counter,
-                                                              const T* __restrict__ f, T* __restrict__ Q,
-                                                              double* __restrict__ moments) {
+template <typename T, bool KAHAN, int NT>
+__global__ void __launch_bounds__(NT, 2) k_fused2d_batched(BatchDev B, int n_cells, const int* __restrict__ cell_plan,
+                                                           const int64_t* __restrict__ cell_offset,
+                                                           const int* __restrict__ order, int* counter,
+                                                           const T* __restrict__ f, T* __restrict__ Q,
+                                                           double* __restrict__ moments, int jd) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32 * 4];
     __shared__ int s_cell;
@@ -269,41 +503,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused2d_batched(BatchDev B, int
         const int64_t off = cell_offset[cell];
         T* sF = reinterpret_cast<T*>(smem_raw);
         T* sP = sF + buf_f_elems(P.N, P.Ntilde);
-        double* mc = moments ? moments + (size_t)cell * 4 : nullptr;
-        // the smallest body that covers this cell: no predicated-off slots
-        const int need = (P.N * P.N + kThreads - 1) / kThreads;
-        if (need <= 1 || PPT == 1)
-            fused2d_body<T, KAHAN, 1>(P.N, P.Ntilde, P.pairs, P.pair_c, 0, P.n_pairs, P.h, P.L, f + off, Q + off, mc,
-                                      sF, sP, red);
-        else if (need <= 4 || PPT == 4)
-            fused2d_body<T, KAHAN, (PPT < 4 ? PPT : 4)>(P.N, P.Ntilde, P.pairs, P.pair_c, 0, P.n_pairs, P.h, P.L,
-                                                        f + off, Q + off, mc, sF, sP, red);
-        else if (need <= 9 || PPT == 9)
-            fused2d_body<T, KAHAN, (PPT < 9 ? PPT : 9)>(P.N, P.Ntilde, P.pairs, P.pair_c, 0, P.n_pairs, P.h, P.L,
-                                                        f + off, Q + off, mc, sF, sP, red);
-        else
-            fused2d_body<T, KAHAN, PPT>(P.N, P.Ntilde, P.pairs, P.pair_c, 0, P.n_pairs, P.h, P.L, f + off, Q + off,
-                                        mc, sF, sP, red);
+        run_cell<T, KAHAN, NT>(P, 0, P.n_pairs, f + off, Q + off, moments ? moments + (size_t)cell * 4 : nullptr, sF,
+                               sP, red, jd);
         __syncthreads();
     }
 }
 
-template <typename T, bool KAHAN, int PPT>
-void set_smem_attr(size_t smem) {
-    cudaFuncSetAttribute(k_fused2d_single<T, KAHAN, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_fused2d_batched<T, KAHAN, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
-
-template <typename T, bool KAHAN, int PPT>
-qdvm_status launch_single_t(const qdvm_plan_s* p, const T* f, T* Q, T* part, int S, int ppc, size_t smem,
+template <typename T, bool KAHAN, int NT>
+qdvm_status launch_single_t(const qdvm_plan_s* p, const T* f, T* Q, T* part, int S, int ppc, size_t smem, int jd,
                             cudaStream_t st) {
-    set_smem_attr<T, KAHAN, PPT>(smem);
+    cudaFuncSetAttribute(k_fused2d_single<T, KAHAN, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const PlanDev P = plan_dev(p);
     const int n = p->N * p->N;
     if (S == 1) {
-        k_fused2d_single<T, KAHAN, PPT><<<1, kThreads, smem, st>>>(P, f, Q, ppc, 0);
+        k_fused2d_single<T, KAHAN, NT><<<1, NT, smem, st>>>(P, f, Q, ppc, 0, jd);
     } else {
-        k_fused2d_single<T, KAHAN, PPT><<<S, kThreads, smem, st>>>(P, f, part, ppc, (size_t)n);
+        k_fused2d_single<T, KAHAN, NT><<<S, NT, smem, st>>>(P, f, part, ppc, (size_t)n, jd);
         k_reduce_partials<T, KAHAN><<<(n + 255) / 256, 256, 0, st>>>(part, S, n, Q);
     }
     QDVM_LAUNCH_CHECK("fused2d single-cell launch");
@@ -313,14 +528,12 @@ qdvm_status launch_single_t(const qdvm_plan_s* p, const T* f, T* Q, T* part, int
 template <typename T, bool KAHAN>
 qdvm_status dispatch_single(const qdvm_plan_s* p, const void* f, void* Q, void* ws, int S, int ppc, size_t smem,
                             cudaStream_t st) {
-    const int ppt = (p->N * p->N + kThreads - 1) / kThreads;
     const T* fi = static_cast<const T*>(f);
     T* qo = static_cast<T*>(Q);
     T* part = static_cast<T*>(ws);
-    if (ppt <= 1) return launch_single_t<T, KAHAN, 1>(p, fi, qo, part, S, ppc, smem, st);
-    if (ppt <= 4) return launch_single_t<T, KAHAN, 4>(p, fi, qo, part, S, ppc, smem, st);
-    if (ppt <= 9) return launch_single_t<T, KAHAN, 9>(p, fi, qo, part, S, ppc, smem, st);
-    return launch_single_t<T, KAHAN, 16>(p, fi, qo, part, S, ppc, smem, st);
+    const int jd = p->tune.direct_j;
+    if (p->tune.threads == 512) return launch_single_t<T, KAHAN, 512>(p, fi, qo, part, S, ppc, smem, jd, st);
+    return launch_single_t<T, KAHAN, 256>(p, fi, qo, part, S, ppc, smem, jd, st);
 }
 
 void split_pairs(int n_pairs, int max_ctas, int* S, int* ppc) {
@@ -330,34 +543,32 @@ void split_pairs(int n_pairs, int max_ctas, int* S, int* ppc) {
     *S = (n_pairs + per - 1) / per;
 }
 
-template <typename T, bool KAHAN, int PPT>
+template <typename T, bool KAHAN, int NT>
 qdvm_status launch_batched_t(const BatchDev& b, int n_cells, const int* cell_plan, const int64_t* cell_offset,
-                             const int* order, int* counter, const T* f, T* Q, double* moments, size_t smem,
+                             const int* order, int* counter, const T* f, T* Q, double* moments, size_t smem, int jd,
                              cudaStream_t st) {
-    set_smem_attr<T, KAHAN, PPT>(smem);
+    auto k = k_fused2d_batched<T, KAHAN, NT>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused2d_batched<T, KAHAN, PPT>, kThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem);
     per_sm = std::max(per_sm, 1);
     const int grid = std::max(1, std::min(n_cells, per_sm * qdvm_num_sms()));
-    k_fused2d_batched<T, KAHAN, PPT><<<grid, kThreads, smem, st>>>(b, n_cells, cell_plan, cell_offset, order, counter,
-                                                                    f, Q, moments);
+    k<<<grid, NT, smem, st>>>(b, n_cells, cell_plan, cell_offset, order, counter, f, Q, moments, jd);
     QDVM_LAUNCH_CHECK("fused2d batched launch");
     return QDVM_OK;
 }
 
 template <typename T, bool KAHAN>
-qdvm_status dispatch_batched(const BatchDev& b, int max_ppt, int n_cells, const int* cell_plan,
+qdvm_status dispatch_batched(const BatchDev& b, const qdvm_tuning& tu, int n_cells, const int* cell_plan,
                              const int64_t* cell_offset, const int* order, int* counter, const void* f, void* Q,
                              double* moments, size_t smem, cudaStream_t st) {
     const T* fi = static_cast<const T*>(f);
     T* qo = static_cast<T*>(Q);
-    if (max_ppt <= 1)
-        return launch_batched_t<T, KAHAN, 1>(b, n_cells, cell_plan, cell_offset, order, counter, fi, qo, moments, smem, st);
-    if (max_ppt <= 4)
-        return launch_batched_t<T, KAHAN, 4>(b, n_cells, cell_plan, cell_offset, order, counter, fi, qo, moments, smem, st);
-    if (max_ppt <= 9)
-        return launch_batched_t<T, KAHAN, 9>(b, n_cells, cell_plan, cell_offset, order, counter, fi, qo, moments, smem, st);
-    return launch_batched_t<T, KAHAN, 16>(b, n_cells, cell_plan, cell_offset, order, counter, fi, qo, moments, smem, st);
+    if (tu.threads == 512)
+        return launch_batched_t<T, KAHAN, 512>(b, n_cells, cell_plan, cell_offset, order, counter, fi, qo, moments,
+                                               smem, tu.direct_j, st);
+    return launch_batched_t<T, KAHAN, 256>(b, n_cells, cell_plan, cell_offset, order, counter, fi, qo, moments, smem,
+                                           tu.direct_j, st);
 }
 
 }  // namespace
@@ -368,7 +579,7 @@ size_t fused2d_smem_bytes(int N, int H, int prec) {
 }
 
 int fused2d_supported(int N, int H, int prec) {
-    if (N * N > 16 * kThreads) return 0;
+    if (N * N > 16 * 256) return 0;
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -398,7 +609,7 @@ qdvm_status fused2d_eval_single(const qdvm_plan_s* p, const void* f, void* Q, in
     }
 }
 
-qdvm_status fused2d_eval_batched(const BatchDev& b, int max_N, int max_H, int n_cells, const int* cell_plan,
+qdvm_status fused2d_eval_batched(const BatchDev& b, const qdvm_tuning& tu, int n_cells, const int* cell_plan,
                                  const int64_t* cell_offset, const void* f, void* Q, double* moments, int prec,
                                  void* ws, cudaStream_t st) {
     // workspace: [counter (int, padded to 256 B)] [order: n_cells ints]
@@ -407,22 +618,16 @@ qdvm_status fused2d_eval_batched(const BatchDev& b, int max_N, int max_H, int n_
     qdvm_status s = schedule_launch(b, n_cells, cell_plan, order, counter, st);
     if (s != QDVM_OK) return s;
     size_t smem = 0;
-    int max_ppt = 1;
-    for (int i = 0; i < b.n_plans; ++i) {
-        smem = std::max(smem, fused2d_smem_bytes(b.p[i].N, b.p[i].Ntilde, prec));
-        max_ppt = std::max(max_ppt, (b.p[i].N * b.p[i].N + kThreads - 1) / kThreads);
-    }
-    (void)max_N;
-    (void)max_H;
+    for (int i = 0; i < b.n_plans; ++i) smem = std::max(smem, fused2d_smem_bytes(b.p[i].N, b.p[i].Ntilde, prec));
     switch (prec) {
         case QDVM_F64:
-            return dispatch_batched<double, false>(b, max_ppt, n_cells, cell_plan, cell_offset, order, counter, f, Q,
+            return dispatch_batched<double, false>(b, tu, n_cells, cell_plan, cell_offset, order, counter, f, Q,
                                                    moments, smem, st);
         case QDVM_F32:
-            return dispatch_batched<float, false>(b, max_ppt, n_cells, cell_plan, cell_offset, order, counter, f, Q,
+            return dispatch_batched<float, false>(b, tu, n_cells, cell_plan, cell_offset, order, counter, f, Q,
                                                   moments, smem, st);
         default:
-            return dispatch_batched<float, true>(b, max_ppt, n_cells, cell_plan, cell_offset, order, counter, f, Q,
+            return dispatch_batched<float, true>(b, tu, n_cells, cell_plan, cell_offset, order, counter, f, Q,
                                                  moments, smem, st);
     }
 }

@@ -59,15 +59,12 @@ extern "C" qdvm_status qdvm_eval_batched_noalloc(const qdvm_plan_t* plans, int n
     BatchDev b;
     for (int i = 0; i < QDVM_MAX_BATCH_PLANS; ++i) b.p[i] = PlanDev();
     b.n_plans = n_plans;
-    int maxN = 0, maxH = 0;
     for (int i = 0; i < n_plans; ++i) {
         if (!qdvm_plan_ok(plans[i])) return qdvm_fail(QDVM_ERR_BAD_PLAN, "bad plan handle in batch");
         if (plans[i]->d != 2 || !fused2d_supported(plans[i]->N, plans[i]->Ntilde, prec))
             return qdvm_fail(QDVM_ERR_UNSUPPORTED,
                              "qdvm_eval_batched_noalloc covers the on-chip 2D evaluator only (d = 2, N <= 64)");
         b.p[i] = plan_dev(plans[i]);
-        maxN = plans[i]->N > maxN ? plans[i]->N : maxN;
-        maxH = plans[i]->Ntilde > maxH ? plans[i]->Ntilde : maxH;
     }
     if (n_cells == 0) return QDVM_OK;
     if (!cell_plan || !cell_offset || !f || !Q) return qdvm_fail(QDVM_ERR_INVALID_ARG, "NULL device array");
@@ -77,6 +74,6 @@ extern "C" qdvm_status qdvm_eval_batched_noalloc(const qdvm_plan_t* plans, int n
     if (s != QDVM_OK) return s;
     // The schedule kernel zeroes the work counter at the start of every call;
     // the order list is rewritten in full.
-    return fused2d_eval_batched(b, maxN, maxH, n_cells, cell_plan, cell_offset, f, Q, moments, prec, scratch,
+    return fused2d_eval_batched(b, plans[0]->tune, n_cells, cell_plan, cell_offset, f, Q, moments, prec, scratch,
                                 static_cast<cudaStream_t>(stream));
 }

@@ -378,6 +378,9 @@ extern "C" qdvm_status qdvm_plan_create_ex(qdvm_plan_t* out, int d, int N, int N
     p->engine = engine;
     p->L = L;
     p->h = 2.0 * L / N;
+    p->tune.threads = 256;
+    p->tune.direct_j = 2;
+    p->tune.line_chunks = 0;
     cudaGetDevice(&p->device);
     qdvm_status s = build_tables(p);
     if (s != QDVM_OK) {
@@ -423,5 +426,22 @@ extern "C" qdvm_status qdvm_plan_lines(qdvm_plan_t p, int* dirs, int* J, double*
         if (J) J[i] = e.w;
         if (c) c[i] = p->h_c[i];
     }
+    return QDVM_OK;
+}
+
+extern "C" qdvm_status qdvm_plan_get_tuning(qdvm_plan_t p, qdvm_tuning* t) {
+    if (!qdvm_plan_ok(p)) return qdvm_fail(QDVM_ERR_BAD_PLAN, "bad plan handle");
+    if (!t) return qdvm_fail(QDVM_ERR_INVALID_ARG, "NULL tuning");
+    *t = p->tune;
+    return QDVM_OK;
+}
+
+extern "C" qdvm_status qdvm_plan_set_tuning(qdvm_plan_t p, const qdvm_tuning* t) {
+    if (!qdvm_plan_ok(p)) return qdvm_fail(QDVM_ERR_BAD_PLAN, "bad plan handle");
+    if (!t) return qdvm_fail(QDVM_ERR_INVALID_ARG, "NULL tuning");
+    if (t->threads != 256 && t->threads != 512) return qdvm_fail(QDVM_ERR_INVALID_ARG, "threads must be 256 or 512");
+    if (t->direct_j < 0 || t->direct_j > 2) return qdvm_fail(QDVM_ERR_INVALID_ARG, "direct_j must be 0, 1 or 2");
+    if (t->line_chunks < 0) return qdvm_fail(QDVM_ERR_INVALID_ARG, "line_chunks must be >= 0");
+    p->tune = *t;
     return QDVM_OK;
 }

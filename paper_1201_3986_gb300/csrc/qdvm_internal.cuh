@@ -22,6 +22,7 @@ struct qdvm_plan_s {
     int max_plane;   // 3D: largest plane list
     int64_t n_terms; // (k, l) terms per output point
     int device;
+    qdvm_tuning tune;  // launch parameters (set by qdvm_plan_set_tuning / qdvm_tune_batched)
     // device tables (owned)
     int4* d_lines;        // (e0, e1, e2, J)
     double* d_c;          // c_e
@@ -111,13 +112,11 @@ __device__ __forceinline__ void comp_add(T& s, T& c, T x) {
 // minus H*(stride+1).  The stride is congruent to N modulo 32 so that a warp
 // of 32 consecutive points never hits the same bank twice, even when it
 // straddles two rows (N = 16, 48).
-__host__ __device__ inline int pad2d_stride(int N, int H) {
-    int w = N + 4 * H;
-    int r = ((N % 32) - (w % 32) + 32) % 32;
-    return w + r;
+__host__ __device__ constexpr int pad2d_stride(int N, int H) {
+    return N + 4 * H + (((N % 32) - ((N + 4 * H) % 32) + 32) % 32);
 }
-__host__ __device__ inline int pad2d_rows_f(int N, int H) { return N + 4 * H; }
-__host__ __device__ inline int pad2d_rows_p(int N, int H) { return N + 2 * H; }
+__host__ __device__ constexpr int pad2d_rows_f(int N, int H) { return N + 4 * H; }
+__host__ __device__ constexpr int pad2d_rows_p(int N, int H) { return N + 2 * H; }
 
 size_t fused2d_smem_bytes(int N, int H, int prec);
 int fused2d_supported(int N, int H, int prec);
@@ -125,7 +124,7 @@ int fused2d_supported(int N, int H, int prec);
 qdvm_status fused2d_eval_single(const qdvm_plan_s* p, const void* f, void* Q, int prec, void* ws,
                                 size_t ws_bytes, cudaStream_t st);
 size_t fused2d_single_workspace(const qdvm_plan_s* p, int prec);
-qdvm_status fused2d_eval_batched(const BatchDev& b, int max_N, int max_H, int n_cells, const int* cell_plan,
+qdvm_status fused2d_eval_batched(const BatchDev& b, const qdvm_tuning& tu, int n_cells, const int* cell_plan,
                                  const int64_t* cell_offset, const void* f, void* Q, double* moments, int prec,
                                  void* ws, cudaStream_t st);
 
@@ -138,7 +137,8 @@ int qdvm_num_sms();
 // ------------------------------------------------------------ generic engine
 // mode: 0 forward, 1 JVP (aux = tangent), 2 VJP (aux = cotangent)
 enum { QDVM_MODE_FWD = 0, QDVM_MODE_JVP = 1, QDVM_MODE_VJP = 2 };
-size_t engine_workspace(int mode, const BatchDev& b, int n_cells, int prec, bool single);
+// chunks: lines-per-cell split (0 = automatic)
+size_t engine_workspace(int mode, const BatchDev& b, int n_cells, int prec, bool single, int chunks);
 qdvm_status engine_run(int mode, const BatchDev& b, int n_cells, const int* cell_plan, const int64_t* cell_offset,
                        const void* f, const void* aux, void* out, double* moments, int prec, void* ws,
-                       size_t ws_bytes, bool single, cudaStream_t st);
+                       size_t ws_bytes, bool single, int chunks, cudaStream_t st);

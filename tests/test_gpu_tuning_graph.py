@@ -1,0 +1,139 @@
+"""Launch-parameter variants, the autotuner and CUDA-graph replay: every
+variant must stay within the parity bars (and bit-exact on integer data)."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "f32_kahan": 1e-5}
+TUNINGS_2D = list(itertools.product((256, 512), (0, 1, 2)))
+
+
+@pytest.fixture(scope="module")
+def q():
+    import paper_1201_3986_gb300 as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+def _batch(torch, b, Ns, prec):
+    cp = torch.tensor([Ns.index(int(n)) for n in b.Ns], dtype=torch.int32, device="cuda")
+    co = torch.tensor(b.offsets, dtype=torch.int64, device="cuda")
+    f = torch.tensor(b.f, dtype=torch.float64 if prec == "f64" else torch.float32, device="cuda")
+    return cp, co, f
+
+
+@pytest.mark.parametrize("threads,direct_j", TUNINGS_2D)
+@pytest.mark.parametrize("prec", ["f64", "f32_kahan"])
+def test_batched_2d_every_tuning(q, torch, threads, direct_j, prec):
+    Ns = (16, 20, 32, 40, 48, 64)
+    b = synth.batch_2d(18, Ns=Ns, L=8.0, seed=31)
+    plans = [q.Plan(2, n, 8, 8.0, kernel="hp") for n in Ns]
+    for p in plans:
+        p.set_tuning(threads=threads, direct_j=direct_j)
+    cp, co, f = _batch(torch, b, Ns, prec)
+    Q, _ = q.qdvm_eval_batched(plans, cp, co, f, prec)
+    Qn = Q.cpu().numpy().astype(np.float64)
+    fin = f.cpu().numpy().astype(np.float64)
+    for c in range(b.n_cells):
+        r = oracle.q(b.cell(c, fin), 8.0, 8, kernel="hp")
+        assert oracle.rel_linf(b.cell(c, Qn), r["Q"], r["scale"]) <= TOL[prec]
+
+
+@pytest.mark.parametrize("threads,direct_j", TUNINGS_2D)
+def test_single_2d_every_tuning_integer_exact(q, torch, threads, direct_j):
+    for N, Nbar in ((16, 3), (48, 8), (64, 8)):
+        f = synth.integer_field(2, N, maxval=2, seed=N + threads + direct_j)
+        plan = q.Plan(2, N, Nbar, 4.0, kernel="unit")
+        plan.set_tuning(threads=threads, direct_j=direct_j)
+        for prec in ("f64", "f32"):
+            Q = q.qdvm_eval(plan, torch.tensor(f, dtype=torch.float64 if prec == "f64" else torch.float32,
+                                               device="cuda"), prec)
+            assert np.array_equal(Q.cpu().numpy().astype(np.float64), oracle.q(f, 4.0, Nbar)["Q"])
+
+
+def test_tuning_rejects_bad_values(q):
+    p = q.Plan(2, 16, 3, 8.0)
+    with pytest.raises(q.QdvmError):
+        p.set_tuning(threads=128)
+    with pytest.raises(q.QdvmError):
+        p.set_tuning(direct_j=3)
+    assert p.tuning() == {"threads": 256, "direct_j": 2, "line_chunks": 0}
+
+
+def test_autotuner_2d_then_parity(q, torch):
+    Ns = (16, 32, 48, 64)
+    b = synth.batch_2d(600, Ns=Ns, L=8.0, seed=5)
+    plans = [q.Plan(2, n, 8, 8.0) for n in Ns]
+    cp, co, f = _batch(torch, b, Ns, "f32_kahan")
+    best = q.qdvm_tune_batched(plans, cp, co, f, "f32_kahan")
+    assert best["threads"] in (256, 512) and best["direct_j"] in (0, 1, 2)
+    assert all(p.tuning() == best for p in plans)
+    Q, _ = q.qdvm_eval_batched(plans, cp, co, f, "f32_kahan")
+    Qn = Q.cpu().numpy().astype(np.float64)
+    fin = f.cpu().numpy().astype(np.float64)
+    for c in (0, 1, 2, 3, 599):
+        r = oracle.q(b.cell(c, fin), 8.0, 8)
+        assert oracle.rel_linf(b.cell(c, Qn), r["Q"], r["scale"]) <= 1e-5
+
+
+@pytest.mark.parametrize("chunks", [1, 2, 3, 7])
+def test_engine_line_chunks_3d(q, torch, chunks):
+    b = synth.batch_3d(4, N=12, L=6.0, seed=8)
+    plan = q.Plan(3, 12, 2, 6.0, kernel="hp")
+    plan.set_tuning(line_chunks=chunks)
+    cp = torch.zeros(b.n_cells, dtype=torch.int32, device="cuda")
+    co = torch.tensor(b.offsets, dtype=torch.int64, device="cuda")
+    f = torch.tensor(b.f, dtype=torch.float32, device="cuda")
+    Q, _ = q.qdvm_eval_batched([plan], cp, co, f, "f32_kahan")
+    Qn = Q.cpu().numpy().astype(np.float64)
+    fin = f.cpu().numpy().astype(np.float64)
+    for c in range(b.n_cells):
+        r = oracle.q(b.cell(c, fin), 6.0, 2, kernel="hp")
+        assert oracle.rel_linf(b.cell(c, Qn), r["Q"], r["scale"]) <= 1e-5
+
+
+def test_autotuner_3d(q, torch):
+    b = synth.batch_3d(6, N=16, L=6.0, seed=9)
+    plan = q.Plan(3, 16, 3, 6.0, kernel="hp")
+    cp = torch.zeros(b.n_cells, dtype=torch.int32, device="cuda")
+    co = torch.tensor(b.offsets, dtype=torch.int64, device="cuda")
+    f = torch.tensor(b.f, dtype=torch.float32, device="cuda")
+    ws = torch.empty(4 * q.batched_workspace_bytes([plan], b.n_cells, "f32"), dtype=torch.uint8, device="cuda")
+    best = q.qdvm_tune_batched([plan], cp, co, f, "f32", workspace=ws)
+    assert best["line_chunks"] >= 0
+    Q, _ = q.qdvm_eval_batched([plan], cp, co, f, "f32", workspace=ws)
+    r = oracle.q(b.cell(5, f.cpu().numpy().astype(np.float64)), 6.0, 3, kernel="hp")
+    assert oracle.rel_linf(b.cell(5, Q.cpu().numpy().astype(np.float64)), r["Q"], r["scale"]) <= 1e-5
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_graph_replay_matches_direct_call(q, torch, d):
+    if d == 2:
+        Ns = (16, 32)
+        b = synth.batch_2d(10, Ns=Ns, L=8.0, seed=3)
+        plans = [q.Plan(2, n, 8, 8.0) for n in Ns]
+    else:
+        Ns = (12,)
+        b = synth.batch_3d(3, N=12, L=6.0, seed=3)
+        plans = [q.Plan(3, 12, 2, 6.0)]
+    cp, co, f = _batch(torch, b, Ns, "f32_kahan")
+    Qd, Md = q.qdvm_eval_batched(plans, cp, co, f, "f32_kahan")
+    Q = torch.full_like(f, float("nan"))
+    M = torch.full((b.n_cells, d + 2), float("nan"), dtype=torch.float64, device="cuda")
+    g = q.BatchedGraph(plans, cp, co, f, Q, M, "f32_kahan")
+    for _ in range(3):
+        Q.fill_(float("nan"))
+        g.launch()
+        torch.cuda.synchronize()
+        assert torch.equal(Q, Qd) and torch.equal(M, Md)
