@@ -95,13 +95,14 @@ extern "C" qdvm_status qdvm_eval_batched(const qdvm_plan_t* plans, int n_plans, 
     if (n_cells == 0) return QDVM_OK;
     if (!cell_plan || !cell_offset || !f || !Q) return qdvm_fail(QDVM_ERR_INVALID_ARG, "NULL device array");
     if (f == Q) return qdvm_fail(QDVM_ERR_INVALID_ARG, "f must not alias Q");
-    size_t need = 0;
-    s = qdvm_batched_workspace(plans, n_plans, n_cells, prec, &need);
-    if (s != QDVM_OK) return s;
-    if (!ws || ws_bytes < need) return qdvm_fail(QDVM_ERR_INVALID_ARG, "workspace too small for qdvm_eval_batched");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (all_fused2d(plans, n_plans, d, prec))
+    if (all_fused2d(plans, n_plans, d, prec)) {
+        // the on-chip evaluator needs the work counter and the cell schedule
+        if (!ws || ws_bytes < 256 + round256((size_t)n_cells * sizeof(int)))
+            return qdvm_fail(QDVM_ERR_INVALID_ARG, "workspace too small for qdvm_eval_batched");
         return fused2d_eval_batched(b, plans[0]->tune, n_cells, cell_plan, cell_offset, f, Q, moments, prec, ws, st);
+    }
+    // the engine checks its own layout against ws_bytes
     return engine_run(QDVM_MODE_FWD, b, n_cells, cell_plan, cell_offset, f, nullptr, Q, moments, prec, ws, ws_bytes,
                       false, plans[0]->tune.line_chunks, st);
 }
