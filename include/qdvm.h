@@ -81,11 +81,19 @@ enum { QDVM_ENGINE_AUTO = 0, QDVM_ENGINE_DIRECT = 1, QDVM_ENGINE_SCAN = 2 };
  *               read V_e straight from the cell ((2J)^2 loads, no barrier);
  *               longer windows go through the on-chip P buffer.
  *   line_chunks generic (3D) engine: chunks of lines per cell, each a work
- *               item summed afterwards in a fixed order; 0 = automatic. */
+ *               item summed afterwards in a fixed order; 0 = automatic.
+ *   loss_fft    1: the loss part sum_e c_e f V_e is evaluated as one
+ *               convolution per cell, f (K * f) with K the weighted
+ *               displacement histogram of the terms, by an on-chip 2D FFT
+ *               (mixed radix 2/3/4; cells of 16, 32, 48 or 64 points per axis
+ *               with the default truncation); the lines then only sum the
+ *               gain.  Rounding differs from the direct sums (no longer
+ *               bit-exact on integer data).  0: direct sums. */
 typedef struct {
     int threads;
     int direct_j;
     int line_chunks;
+    int loss_fft;
 } qdvm_tuning;
 
 /* ------------------------------------------------------------------ plans */
@@ -125,7 +133,7 @@ qdvm_status qdvm_plan_info(qdvm_plan_t plan, int* d, int* N, int* Ntilde, int* m
  * |e|_inf then lexicographically), J (window half-length), c (weight). */
 qdvm_status qdvm_plan_lines(qdvm_plan_t plan, int* dirs, int* J, double* c);
 
-/* Read / set a plan's launch parameters (defaults: 256, 2, 0).  A batched
+/* Read / set a plan's launch parameters (defaults: 256, 2, 0, 0).  A batched
  * call uses the parameters of plans[0].  Errors: BAD_PLAN, INVALID_ARG. */
 qdvm_status qdvm_plan_get_tuning(qdvm_plan_t plan, qdvm_tuning* t);
 qdvm_status qdvm_plan_set_tuning(qdvm_plan_t plan, const qdvm_tuning* t);

@@ -176,11 +176,12 @@ extern "C" qdvm_status qdvm_tune_batched(const qdvm_plan_t* plans, int n_plans, 
     std::vector<qdvm_tuning> cand;
     if (all_fused2d(plans, n_plans, d, prec)) {
         for (int th : {256, 512})
-            for (int dj : {0, 1, 2}) cand.push_back(qdvm_tuning{th, dj, saved.line_chunks});
+            for (int dj : {0, 1, 2}) cand.push_back(qdvm_tuning{th, dj, saved.line_chunks, 0});
+        for (int th : {256, 512}) cand.push_back(qdvm_tuning{th, saved.direct_j, saved.line_chunks, 1});
     } else {
         for (int c : {0, 1, 2, 3, 4, 6, 8}) {
             if (engine_workspace(QDVM_MODE_FWD, b, n_cells, prec, false, c) <= ws_bytes)
-                cand.push_back(qdvm_tuning{saved.threads, saved.direct_j, c});
+                cand.push_back(qdvm_tuning{saved.threads, saved.direct_j, c, saved.loss_fft});
         }
     }
     if (cand.empty()) return qdvm_fail(QDVM_ERR_INVALID_ARG, "workspace too small for every candidate");

@@ -403,6 +403,261 @@ __device__ __forceinline__ void fixed_body(const int4* __restrict__ pairs, const
     }
 }
 
+// ------------------------------------------------------------------------
+// Loss as one convolution (the paper's remark that the loss part is a plain
+// convolution): sum_e c_e V_e(i) = sum_m K(m) f(i + m) = (K * f)(i), K the
+// weighted displacement histogram of the terms (plan table, transformed).
+// An on-chip 2D FFT (Stockham, mixed radix 2/3/4, ping-pong between two
+// N x (N+1) complex buffers) gives K * f for the whole cell; the pair loop
+// then only sums the gain 2 c_e W_e W_{e^perp} -- no P buffer, no barrier.
+
+template <typename T>
+struct Cplx;
+template <>
+struct Cplx<float> {
+    using type = float2;
+};
+template <>
+struct Cplx<double> {
+    using type = double2;
+};
+
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) {
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+
+// In-register R-point DFT, forward exp(-2 pi i q k / R) or inverse.
+template <int R, bool INV, typename C>
+__device__ __forceinline__ void dft_small(C (&v)[R]) {
+    using S = decltype(v[0].x);
+    if constexpr (R == 2) {
+        const C a = v[0], b = v[1];
+        v[0].x = a.x + b.x;
+        v[0].y = a.y + b.y;
+        v[1].x = a.x - b.x;
+        v[1].y = a.y - b.y;
+    } else if constexpr (R == 3) {
+        const S h = S(0.8660254037844386467637231707529362);  // sqrt(3)/2
+        const C t1 = {v[1].x + v[2].x, v[1].y + v[2].y};
+        const C t2 = {v[1].x - v[2].x, v[1].y - v[2].y};
+        const C m = {v[0].x - S(0.5) * t1.x, v[0].y - S(0.5) * t1.y};
+        // forward: y1 = m - i h t2, y2 = m + i h t2 (inverse: signs swapped)
+        const S sx = INV ? -h * t2.y : h * t2.y;
+        const S sy = INV ? h * t2.x : -h * t2.x;
+        v[0].x += t1.x;
+        v[0].y += t1.y;
+        v[1].x = m.x + sx;
+        v[1].y = m.y + sy;
+        v[2].x = m.x - sx;
+        v[2].y = m.y - sy;
+    } else {  // R == 4
+        const C a0 = {v[0].x + v[2].x, v[0].y + v[2].y};
+        const C a1 = {v[0].x - v[2].x, v[0].y - v[2].y};
+        const C b0 = {v[1].x + v[3].x, v[1].y + v[3].y};
+        const C b1 = {v[1].x - v[3].x, v[1].y - v[3].y};
+        // forward: (-i) b1 = (b1.y, -b1.x); inverse: (+i) b1 = (-b1.y, b1.x)
+        const C rb = INV ? C{-b1.y, b1.x} : C{b1.y, -b1.x};
+        v[0] = C{a0.x + b0.x, a0.y + b0.y};
+        v[2] = C{a0.x - b0.x, a0.y - b0.y};
+        v[1] = C{a1.x + rb.x, a1.y + rb.y};
+        v[3] = C{a1.x - rb.x, a1.y - rb.y};
+    }
+}
+
+// One Stockham pass of radix R over all N lines (rows, or columns with
+// COLS), NS = product of the radices already applied.  Butterfly b works on
+// line b % N, so a warp touches consecutive lines (row stride LD = N + 1
+// complex: no bank conflicts on columns or rows).
+template <typename C, int N, int LD, int R, int NS, bool INV, bool COLS>
+__device__ __forceinline__ void fft_pass(const C* __restrict__ src, C* __restrict__ dst, const C* __restrict__ tw) {
+    constexpr int NB = N / R;
+    for (int b = threadIdx.x; b < N * NB; b += blockDim.x) {
+        const int line = b % N, j = b / N;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int e = j + r * NB;
+            v[r] = src[COLS ? e * LD + line : line * LD + e];
+        }
+        const int jm = j % NS;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            C w = tw[(jm * (N / (NS * R)) * r) % N];
+            if (INV) w.y = -w.y;
+            v[r] = cmul(v[r], w);
+        }
+        dft_small<R, INV>(v);
+        const int idxD = (j / NS) * NS * R + jm;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int e = idxD + r * NS;
+            dst[COLS ? e * LD + line : line * LD + e] = v[r];
+        }
+    }
+}
+
+template <typename C, int N, int LD, bool INV, bool COLS, int NS, int R, int... Rs>
+__device__ __forceinline__ C* fft_passes(C* a, C* b, const C* tw) {
+    fft_pass<C, N, LD, R, NS, INV, COLS>(a, b, tw);
+    __syncthreads();
+    if constexpr (sizeof...(Rs) > 0)
+        return fft_passes<C, N, LD, INV, COLS, NS * R, Rs...>(b, a, tw);
+    else
+        return b;
+}
+
+// All N line transforms of length N; returns the buffer holding the result.
+template <typename C, int N, int LD, bool INV, bool COLS>
+__device__ __forceinline__ C* fft_lines(C* a, C* b, const C* tw) {
+    if constexpr (N == 64) return fft_passes<C, N, LD, INV, COLS, 1, 4, 4, 4>(a, b, tw);
+    else if constexpr (N == 48) return fft_passes<C, N, LD, INV, COLS, 1, 3, 4, 4>(a, b, tw);
+    else if constexpr (N == 32) return fft_passes<C, N, LD, INV, COLS, 1, 2, 4, 4>(a, b, tw);
+    else return fft_passes<C, N, LD, INV, COLS, 1, 4, 4>(a, b, tw);  // N == 16
+}
+
+template <int N, int H>
+struct GeoF {
+    static constexpr int W = N + 2 * H;
+    static constexpr int RS = W + (((N % 32) - (W % 32) + 32) % 32);
+    static constexpr int LD = N + 1;
+};
+
+template <typename T, int N, int H>
+__host__ __device__ constexpr size_t fft_smem_bytes() {
+    using G = GeoF<N, H>;
+    return ((size_t)G::W * G::RS * sizeof(T) + 15) / 16 * 16 + 2 * (size_t)N * G::LD * 2 * sizeof(T);
+}
+
+template <typename T, bool KAHAN, int N, int H, int NT>
+__device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, const int pe, const T* __restrict__ fcell,
+                                             T* __restrict__ qcell, double* __restrict__ mom, unsigned char* smem,
+                                             double* red, const bool do_loss) {
+    using C = typename Cplx<T>::type;
+    using G = GeoF<N, H>;
+    constexpr int W = G::W, RS = G::RS, LD = G::LD;
+    constexpr int R = (NT / N < N) ? NT / N : N;
+    constexpr int PPT = (N + R - 1) / R;
+    constexpr int ACT = R * N;
+    constexpr int DK = R * RS;
+    constexpr bool PARTIAL = (N % R) != 0;
+    const int tid = threadIdx.x;
+    T* sF = reinterpret_cast<T*>(smem);
+    C* A = reinterpret_cast<C*>(smem + ((size_t)W * RS * sizeof(T) + 15) / 16 * 16);
+    C* B = A + N * LD;
+    const C* tw;
+    const T* kh;
+    if constexpr (sizeof(T) == 8) {
+        tw = reinterpret_cast<const C*>(P.tw);
+        kh = reinterpret_cast<const T*>(P.khat);
+    } else {
+        tw = reinterpret_cast<const C*>(P.tw_f);
+        kh = reinterpret_cast<const T*>(P.khat_f);
+    }
+
+    for (int p = tid; p < W * W; p += NT) {
+        const int py = p / W, px = p - py * W;
+        int sy = py - H, sx = px - H;
+        sy += sy < 0 ? N : 0;
+        sy -= sy >= N ? N : 0;
+        sx += sx < 0 ? N : 0;
+        sx -= sx >= N ? N : 0;
+        sF[py * RS + px] = fcell[sy * N + sx];
+    }
+    if (do_loss)
+        for (int i = tid; i < N * N; i += NT) A[(i / N) * LD + (i % N)] = C{fcell[i], T(0)};
+    __syncthreads();
+
+    const bool active = tid < ACT;
+    const int x = tid % N, y0 = tid / N;
+    const int a0 = (y0 + H) * RS + x + H;
+    const bool last_ok = !PARTIAL || (y0 + (PPT - 1) * R < N);
+    T acc[PPT], cmp[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        acc[k] = T(0);
+        cmp[k] = T(0);
+    }
+    if (do_loss) {
+        C* r = fft_lines<C, N, LD, false, false>(A, B, tw);
+        r = fft_lines<C, N, LD, false, true>(r, r == A ? B : A, tw);
+        for (int i = tid; i < N * N; i += NT) {
+            C& z = r[(i / N) * LD + (i % N)];
+            const T k = kh[i];
+            z.x *= k;
+            z.y *= k;
+        }
+        __syncthreads();
+        r = fft_lines<C, N, LD, true, true>(r, r == A ? B : A, tw);
+        r = fft_lines<C, N, LD, true, false>(r, r == A ? B : A, tw);
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (k < PPT - 1 || last_ok) {
+                    const int y = y0 + k * R;
+                    acc[k] = -sF[a0 + k * DK] * r[y * LD + x].x;  // - f (K * f): the loss
+                }
+            }
+        }
+    }
+
+    if (active) {
+        for (int pr = pb; pr < pe; ++pr) {
+            const int4 e = P.pairs[pr];
+            const T c2 = (T)(2.0 * P.pair_c[pr]);
+            const int se = e.x * RS + e.y;
+            const int sp = -e.y * RS + e.x;
+            T w[PPT], pp[PPT];
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) w[k] = pp[k] = T(0);
+            const T* b;
+            for (int j = 1; j <= e.z; ++j) {
+#define QDVM_GATHER(arr, off)                                                                \
+    b = sF + a0 + (off);                                                                     \
+    _Pragma("unroll") for (int k = 0; k < PPT; ++k) if (k < PPT - 1 || last_ok) arr[k] += b[k * DK];
+                QDVM_GATHER(w, j * se)
+                QDVM_GATHER(w, -j * se)
+                QDVM_GATHER(pp, j * sp)
+                QDVM_GATHER(pp, -j * sp)
+#undef QDVM_GATHER
+            }
+#pragma unroll
+            for (int k = 0; k < PPT; ++k)
+                if (k < PPT - 1 || last_ok) comp_add<T, KAHAN>(acc[k], cmp[k], c2 * w[k] * pp[k]);
+        }
+    }
+
+    double m[4] = {0.0, 0.0, 0.0, 0.0};
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            if (k < PPT - 1 || last_ok) {
+                const int y = y0 + k * R;
+                const T q = KAHAN ? acc[k] + cmp[k] : acc[k];
+                qcell[y * N + x] = q;
+                if (mom) {
+                    const double v0 = -P.L + y * P.h, v1 = -P.L + x * P.h, qd = (double)q;
+                    m[0] += qd;
+                    m[1] += qd * v0;
+                    m[2] += qd * v1;
+                    m[3] += qd * (v0 * v0 + v1 * v1);
+                }
+            }
+        }
+    }
+    if (mom) {
+        block_reduce_fixed<4>(m, red);
+        if (tid == 0) {
+            const double h2 = P.h * P.h;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) mom[i] = h2 * m[i];
+        }
+    }
+}
+
 // elements of the f buffer; the P buffer follows it
 __host__ __device__ inline size_t buf_f_elems(int N, int H) {
     return (size_t)pad2d_rows_f(N, H) * (size_t)pad2d_stride(N, H);
@@ -422,12 +677,17 @@ __host__ __device__ inline int ppt_pick(int NT, int need) {
 // One cell with the smallest body that covers it (no predicated-off slots).
 template <typename T, bool KAHAN, int NT>
 __device__ __forceinline__ void run_cell(const PlanDev& P, int pb, int pe, const T* f, T* q, double* mom, T* sF, T* sP,
-                                         double* red, int jd) {
+                                         double* red, int jd, int fft, bool do_loss) {
     // the common cell sizes with the default truncation floor(N/(3+sqrt 2))
-#define QDVM_FIXED(NN, HH)                                                                                  \
-    if (P.N == NN && P.Ntilde == HH) {                                                                      \
-        fixed_body<T, KAHAN, NN, HH, NT>(P.pairs, P.pair_c, pb, pe, P.h, P.L, f, q, mom, sF, sP, red, jd); \
-        return;                                                                                             \
+#define QDVM_FIXED(NN, HH)                                                                                        \
+    if (P.N == NN && P.Ntilde == HH) {                                                                            \
+        if (fft && P.khat) {                                                                                      \
+            fftloss_body<T, KAHAN, NN, HH, NT>(P, pb, pe, f, q, mom, reinterpret_cast<unsigned char*>(sF), red,  \
+                                               do_loss);                                                          \
+        } else {                                                                                                  \
+            fixed_body<T, KAHAN, NN, HH, NT>(P.pairs, P.pair_c, pb, pe, P.h, P.L, f, q, mom, sF, sP, red, jd);   \
+        }                                                                                                         \
+        return;                                                                                                   \
     }
     QDVM_FIXED(64, 14)
     QDVM_FIXED(48, 10)
@@ -455,14 +715,15 @@ __device__ __forceinline__ void run_cell(const PlanDev& P, int pb, int pe, const
 
 template <typename T, bool KAHAN, int NT>
 __global__ void __launch_bounds__(NT, 2) k_fused2d_single(PlanDev P, const T* __restrict__ f, T* __restrict__ out,
-                                                          int pairs_per_cta, size_t slot_stride, int jd) {
+                                                          int pairs_per_cta, size_t slot_stride, int jd, int fft) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32 * 4];
     T* sF = reinterpret_cast<T*>(smem_raw);
     T* sP = sF + buf_f_elems(P.N, P.Ntilde);
     const int pb = blockIdx.x * pairs_per_cta;
     const int pe = min(pb + pairs_per_cta, P.n_pairs);
-    run_cell<T, KAHAN, NT>(P, pb, pe, f, out + blockIdx.x * slot_stride, nullptr, sF, sP, red, jd);
+    run_cell<T, KAHAN, NT>(P, pb, pe, f, out + blockIdx.x * slot_stride, nullptr, sF, sP, red, jd, fft,
+                           blockIdx.x == 0);
 }
 
 // Deterministic sum of S partial results (fixed order s = 0..S-1).
@@ -480,7 +741,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused2d_batched(BatchDev B, int n_cel
                                                            const int64_t* __restrict__ cell_offset,
                                                            const int* __restrict__ order, int* counter,
                                                            const T* __restrict__ f, T* __restrict__ Q,
-                                                           double* __restrict__ moments, int jd) {
+                                                           double* __restrict__ moments, int jd, int fft) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32 * 4];
     __shared__ int s_cell;
@@ -504,21 +765,21 @@ __global__ void __launch_bounds__(NT, 2) k_fused2d_batched(BatchDev B, int n_cel
         T* sF = reinterpret_cast<T*>(smem_raw);
         T* sP = sF + buf_f_elems(P.N, P.Ntilde);
         run_cell<T, KAHAN, NT>(P, 0, P.n_pairs, f + off, Q + off, moments ? moments + (size_t)cell * 4 : nullptr, sF,
-                               sP, red, jd);
+                               sP, red, jd, fft, true);
         __syncthreads();
     }
 }
 
 template <typename T, bool KAHAN, int NT>
 qdvm_status launch_single_t(const qdvm_plan_s* p, const T* f, T* Q, T* part, int S, int ppc, size_t smem, int jd,
-                            cudaStream_t st) {
+                            int fft, cudaStream_t st) {
     cudaFuncSetAttribute(k_fused2d_single<T, KAHAN, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const PlanDev P = plan_dev(p);
     const int n = p->N * p->N;
     if (S == 1) {
-        k_fused2d_single<T, KAHAN, NT><<<1, NT, smem, st>>>(P, f, Q, ppc, 0, jd);
+        k_fused2d_single<T, KAHAN, NT><<<1, NT, smem, st>>>(P, f, Q, ppc, 0, jd, fft);
     } else {
-        k_fused2d_single<T, KAHAN, NT><<<S, NT, smem, st>>>(P, f, part, ppc, (size_t)n, jd);
+        k_fused2d_single<T, KAHAN, NT><<<S, NT, smem, st>>>(P, f, part, ppc, (size_t)n, jd, fft);
         k_reduce_partials<T, KAHAN><<<(n + 255) / 256, 256, 0, st>>>(part, S, n, Q);
     }
     QDVM_LAUNCH_CHECK("fused2d single-cell launch");
@@ -531,9 +792,9 @@ qdvm_status dispatch_single(const qdvm_plan_s* p, const void* f, void* Q, void* 
     const T* fi = static_cast<const T*>(f);
     T* qo = static_cast<T*>(Q);
     T* part = static_cast<T*>(ws);
-    const int jd = p->tune.direct_j;
-    if (p->tune.threads == 512) return launch_single_t<T, KAHAN, 512>(p, fi, qo, part, S, ppc, smem, jd, st);
-    return launch_single_t<T, KAHAN, 256>(p, fi, qo, part, S, ppc, smem, jd, st);
+    const int jd = p->tune.direct_j, fft = p->tune.loss_fft;
+    if (p->tune.threads == 512) return launch_single_t<T, KAHAN, 512>(p, fi, qo, part, S, ppc, smem, jd, fft, st);
+    return launch_single_t<T, KAHAN, 256>(p, fi, qo, part, S, ppc, smem, jd, fft, st);
 }
 
 void split_pairs(int n_pairs, int max_ctas, int* S, int* ppc) {
@@ -546,14 +807,14 @@ void split_pairs(int n_pairs, int max_ctas, int* S, int* ppc) {
 template <typename T, bool KAHAN, int NT>
 qdvm_status launch_batched_t(const BatchDev& b, int n_cells, const int* cell_plan, const int64_t* cell_offset,
                              const int* order, int* counter, const T* f, T* Q, double* moments, size_t smem, int jd,
-                             cudaStream_t st) {
+                             int fft, cudaStream_t st) {
     auto k = k_fused2d_batched<T, KAHAN, NT>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem);
     per_sm = std::max(per_sm, 1);
     const int grid = std::max(1, std::min(n_cells, per_sm * qdvm_num_sms()));
-    k<<<grid, NT, smem, st>>>(b, n_cells, cell_plan, cell_offset, order, counter, f, Q, moments, jd);
+    k<<<grid, NT, smem, st>>>(b, n_cells, cell_plan, cell_offset, order, counter, f, Q, moments, jd, fft);
     QDVM_LAUNCH_CHECK("fused2d batched launch");
     return QDVM_OK;
 }
@@ -566,16 +827,23 @@ qdvm_status dispatch_batched(const BatchDev& b, const qdvm_tuning& tu, int n_cel
     T* qo = static_cast<T*>(Q);
     if (tu.threads == 512)
         return launch_batched_t<T, KAHAN, 512>(b, n_cells, cell_plan, cell_offset, order, counter, fi, qo, moments,
-                                               smem, tu.direct_j, st);
+                                               smem, tu.direct_j, tu.loss_fft, st);
     return launch_batched_t<T, KAHAN, 256>(b, n_cells, cell_plan, cell_offset, order, counter, fi, qo, moments, smem,
-                                           tu.direct_j, st);
+                                           tu.direct_j, tu.loss_fft, st);
 }
 
 }  // namespace
 
-size_t fused2d_smem_bytes(int N, int H, int prec) {
+size_t fused2d_smem_bytes(int N, int H, int prec, int fft) {
     const size_t es = prec == QDVM_F64 ? sizeof(double) : sizeof(float);
-    return (buf_f_elems(N, H) + buf_p_elems(N, H)) * es;
+    size_t b = (buf_f_elems(N, H) + buf_p_elems(N, H)) * es;
+    if (fft) {
+        // the FFT body's layout for the compile-time cell sizes
+        const size_t W = N + 2 * H, RS = W + (((N % 32) - (W % 32) + 32) % 32), LD = N + 1;
+        const size_t fb = (W * RS * es + 15) / 16 * 16 + 2 * (size_t)N * LD * 2 * es;
+        b = std::max(b, fb);
+    }
+    return b;
 }
 
 int fused2d_supported(int N, int H, int prec) {
@@ -583,7 +851,7 @@ int fused2d_supported(int N, int H, int prec) {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return fused2d_smem_bytes(N, H, prec) + 2048 <= (size_t)optin;
+    return fused2d_smem_bytes(N, H, prec, 1) + 2048 <= (size_t)optin;
 }
 
 size_t fused2d_single_workspace(const qdvm_plan_s* p, int prec) {
@@ -601,7 +869,7 @@ qdvm_status fused2d_eval_single(const qdvm_plan_s* p, const void* f, void* Q, in
     const size_t need = fused2d_single_workspace(p, prec);
     if (need > 0 && (ws == nullptr || ws_bytes < need))
         return qdvm_fail(QDVM_ERR_INVALID_ARG, "workspace too small for qdvm_eval");
-    const size_t smem = fused2d_smem_bytes(p->N, p->Ntilde, prec);
+    const size_t smem = fused2d_smem_bytes(p->N, p->Ntilde, prec, p->tune.loss_fft);
     switch (prec) {
         case QDVM_F64: return dispatch_single<double, false>(p, f, Q, ws, S, ppc, smem, st);
         case QDVM_F32: return dispatch_single<float, false>(p, f, Q, ws, S, ppc, smem, st);
@@ -618,7 +886,8 @@ qdvm_status fused2d_eval_batched(const BatchDev& b, const qdvm_tuning& tu, int n
     qdvm_status s = schedule_launch(b, n_cells, cell_plan, order, counter, st);
     if (s != QDVM_OK) return s;
     size_t smem = 0;
-    for (int i = 0; i < b.n_plans; ++i) smem = std::max(smem, fused2d_smem_bytes(b.p[i].N, b.p[i].Ntilde, prec));
+    for (int i = 0; i < b.n_plans; ++i)
+        smem = std::max(smem, fused2d_smem_bytes(b.p[i].N, b.p[i].Ntilde, prec, tu.loss_fft));
     switch (prec) {
         case QDVM_F64:
             return dispatch_batched<double, false>(b, tu, n_cells, cell_plan, cell_offset, order, counter, f, Q,

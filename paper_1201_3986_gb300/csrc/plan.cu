@@ -250,6 +250,60 @@ __global__ void k_plane_emit(int d, int n_lines, const int4* lines, int Nt, cons
     }
 }
 
+// K(m) = sum over lines e, 0<|j|<=J_e, l in the plane list of e, of c_e
+// [j e + l = m mod N] (2D), one thread per m, lines in order: the loss
+// sum_e c_e V_e(i) is the correlation sum_m K(m) f(i + m).
+__global__ void k_loss_kernel2d(int n_lines, const int4* lines, const double* c, const int* plane_start,
+                                const char4* plane, int N, double* K) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= N * N) return;
+    const int m0 = m / N, m1 = m - (m / N) * N;
+    double acc = 0.0;
+    for (int li = 0; li < n_lines; ++li) {
+        const int4 e = lines[li];
+        int hits = 0;
+        for (int t = plane_start[li]; t < plane_start[li + 1]; ++t) {
+            const char4 l = plane[t];
+            for (int j = -e.w; j <= e.w; ++j) {
+                if (j == 0) continue;
+                int a0 = (j * e.x + l.x) % N, a1 = (j * e.y + l.y) % N;
+                a0 += a0 < 0 ? N : 0;
+                a1 += a1 < 0 ? N : 0;
+                hits += (a0 == m0 && a1 == m1) ? 1 : 0;
+            }
+        }
+        acc += c[li] * (double)hits;
+    }
+    K[m] = acc;
+}
+
+// Ktilde(xi) = sum_m K(m) cos(2 pi (m.xi mod N) / N) / N^2 (exact integer
+// phases), in FP64 and rounded to FP32.
+__global__ void k_khat2d(int N, const double* K, double* kh, float* khf) {
+    const int xi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (xi >= N * N) return;
+    const int x0 = xi / N, x1 = xi - (xi / N) * N;
+    double acc = 0.0;
+    for (int m = 0; m < N * N; ++m) {
+        const double k = K[m];
+        if (k == 0.0) continue;
+        const int t = ((m / N) * x0 + (m - (m / N) * N) * x1) % N;
+        acc += k * cospi(2.0 * t / N);
+    }
+    acc /= (double)N * (double)N;
+    kh[xi] = acc;
+    khf[xi] = (float)acc;
+}
+
+__global__ void k_twiddles(int N, double2* tw, float2* twf) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    double s, c;
+    sincospi(2.0 * t / N, &s, &c);
+    tw[t] = make_double2(c, -s);
+    twf[t] = make_float2((float)c, (float)-s);
+}
+
 // ------------------------------------------------------------ plan lifecycle
 
 static void plan_free(qdvm_plan_s* p) {
@@ -260,6 +314,10 @@ static void plan_free(qdvm_plan_s* p) {
     cudaFree(p->d_pair_c);
     cudaFree(p->d_plane_start);
     cudaFree(p->d_plane);
+    cudaFree(p->d_khat);
+    cudaFree(p->d_khat_f);
+    cudaFree(p->d_tw);
+    cudaFree(p->d_tw_f);
     p->magic = 0;
     delete p;
 }
@@ -346,6 +404,24 @@ static qdvm_status build_tables(qdvm_plan_s* p) {
                         cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(qdvm_cuda_status(e, "plane start upload"));
     k_plane_emit<<<total, 256>>>(d, total, p->d_lines, p->Ntilde, p->d_plane_start, p->d_plane);
+    if (d == 2 && p->N <= 64) {
+        const int N = p->N, n2 = N * N;
+        double* dK = nullptr;
+        if ((e = cudaMalloc(&dK, n2 * sizeof(double))) != cudaSuccess) return fail(qdvm_cuda_status(e, "K"));
+        if ((e = cudaMalloc(&p->d_khat, n2 * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_khat_f, n2 * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_tw, N * sizeof(double2))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_tw_f, N * sizeof(float2))) != cudaSuccess) {
+            cudaFree(dK);
+            return fail(qdvm_cuda_status(e, "loss kernel tables"));
+        }
+        k_loss_kernel2d<<<(n2 + 127) / 128, 128>>>(total, p->d_lines, p->d_c, p->d_plane_start, p->d_plane, N, dK);
+        k_khat2d<<<(n2 + 127) / 128, 128>>>(N, dK, p->d_khat, p->d_khat_f);
+        k_twiddles<<<(N + 63) / 64, 64>>>(N, p->d_tw, p->d_tw_f);
+        e = cudaDeviceSynchronize();
+        cudaFree(dK);
+        if (e != cudaSuccess) return fail(qdvm_cuda_status(e, "loss kernel tables"));
+    }
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(qdvm_cuda_status(e, "plan build"));
     return fail(st);
 }
@@ -381,6 +457,7 @@ extern "C" qdvm_status qdvm_plan_create_ex(qdvm_plan_t* out, int d, int N, int N
     p->tune.threads = 256;
     p->tune.direct_j = 2;
     p->tune.line_chunks = 0;
+    p->tune.loss_fft = 0;
     cudaGetDevice(&p->device);
     qdvm_status s = build_tables(p);
     if (s != QDVM_OK) {
@@ -442,6 +519,7 @@ extern "C" qdvm_status qdvm_plan_set_tuning(qdvm_plan_t p, const qdvm_tuning* t)
     if (t->threads != 256 && t->threads != 512) return qdvm_fail(QDVM_ERR_INVALID_ARG, "threads must be 256 or 512");
     if (t->direct_j < 0 || t->direct_j > 2) return qdvm_fail(QDVM_ERR_INVALID_ARG, "direct_j must be 0, 1 or 2");
     if (t->line_chunks < 0) return qdvm_fail(QDVM_ERR_INVALID_ARG, "line_chunks must be >= 0");
+    if (t->loss_fft != 0 && t->loss_fft != 1) return qdvm_fail(QDVM_ERR_INVALID_ARG, "loss_fft must be 0 or 1");
     p->tune = *t;
     return QDVM_OK;
 }

@@ -29,7 +29,15 @@ struct qdvm_plan_s {
     int4* d_pairs;        // 2D: (e0, e1, J, 0), one per pair
     double* d_pair_c;     // 2D: c_e (= c_{e^perp})
     int* d_plane_start;   // 3D: n_lines + 1 offsets into d_plane
-    char4* d_plane;       // 3D: (l0, l1, l2, 0), l in e^perp, 0 < |l|_inf <= Ntilde
+    char4* d_plane;       // (l0, l1, l2, 0), l in e^perp, 0 < |l|_inf <= Ntilde
+    // 2D, N <= 64: the loss as one convolution, loss_i = f_i (K * f)_i with
+    // K(m) = sum_e c_e #{(j, l): j e + l = m}; Ktilde(xi) = sum_m K(m)
+    // cos(2 pi m.xi / N) / N^2 (real: K is symmetric), and the N-th roots of
+    // unity exp(-2 pi i t / N) for the FFTs.
+    double* d_khat;
+    float* d_khat_f;
+    double2* d_tw;
+    float2* d_tw_f;
     // host copies
     std::vector<int4> h_lines;
     std::vector<double> h_c;
@@ -46,6 +54,10 @@ struct PlanDev {
     const double* pair_c;
     const int* plane_start;
     const char4* plane;
+    const double* khat;
+    const float* khat_f;
+    const double2* tw;
+    const float2* tw_f;
 };
 
 struct BatchDev {
@@ -68,6 +80,10 @@ inline PlanDev plan_dev(const qdvm_plan_s* p) {
     v.pair_c = p->d_pair_c;
     v.plane_start = p->d_plane_start;
     v.plane = p->d_plane;
+    v.khat = p->d_khat;
+    v.khat_f = p->d_khat_f;
+    v.tw = p->d_tw;
+    v.tw_f = p->d_tw_f;
     return v;
 }
 
@@ -118,7 +134,7 @@ __host__ __device__ constexpr int pad2d_stride(int N, int H) {
 __host__ __device__ constexpr int pad2d_rows_f(int N, int H) { return N + 4 * H; }
 __host__ __device__ constexpr int pad2d_rows_p(int N, int H) { return N + 2 * H; }
 
-size_t fused2d_smem_bytes(int N, int H, int prec);
+size_t fused2d_smem_bytes(int N, int H, int prec, int fft);
 int fused2d_supported(int N, int H, int prec);
 
 qdvm_status fused2d_eval_single(const qdvm_plan_s* p, const void* f, void* Q, int prec, void* ws,
