@@ -261,7 +261,13 @@ def run_gpu(args):
 
     # the library's autotuner picks the launch configuration on this batch;
     # each rotating buffer set is then captured once into a CUDA graph
-    tuning = q.qdvm_tune_batched(plans, cp, co, fs[0], "f32_kahan", workspace=wss)
+    if args.tuning:
+        th, dj, fft = (int(v) for v in args.tuning.split(","))
+        for p in plans:
+            p.set_tuning(threads=th, direct_j=dj, loss_fft=fft)
+        tuning = plans[0].tuning()
+    else:
+        tuning = q.qdvm_tune_batched(plans, cp, co, fs[0], "f32_kahan", workspace=wss)
     graphs = [q.BatchedGraph(plans, cp, co, fs[k], Qs[k], Ms[k], "f32_kahan", workspace=wss) for k in range(ROTATE)]
 
     for g in graphs:  # first replay of a graph uploads it; keep that out of the timed region
@@ -511,6 +517,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="batch2d", choices=["batch2d", "batch3d", "jvp3d", "vjp3d", "single3d"])
     ap.add_argument("--nbar", type=int, default=None)
+    ap.add_argument("--tuning", default=None,
+                    help="threads,direct_j,loss_fft: pin the launch configuration instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
