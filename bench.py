@@ -429,6 +429,7 @@ def run_gpu_workload(args):
         nb = args.nbar or 5
         f_np = synth.trimaxwellian_3d(32, 6.0)
         plan = q.Plan(3, 32, nb, 6.0, kernel="hp")
+        plan.set_tuning(loss_fft=args.loss_fft)
         rot = 8  # 8 x 128 KB inputs + outputs; the scratch dominates anyway
         fs = [torch.tensor(f_np, dtype=torch.float32, device=dev) for _ in range(rot)]
         outs = [torch.empty_like(fs[0]) for _ in range(rot)]
@@ -439,7 +440,8 @@ def run_gpu_workload(args):
 
         pts_per_step = 32 ** 3
         cfg = {"workload": f"3D hard spheres, one 32^3 cell on [-6,6]^3, Nbar={nb} ({plan.n_lines} lines), "
-                           "tri-axial Gaussian T=(0.5,1,2), drift (0.5,0,0), FP32", "Nbar": nb}
+                           "tri-axial Gaussian T=(0.5,1,2), drift (0.5,0,0), FP32", "Nbar": nb,
+               "tuning": plan.tuning()}
         check = lambda: (f_np, outs[0], None)
     else:
         nb = 5
@@ -452,7 +454,12 @@ def run_gpu_workload(args):
         fs = [torch.tensor(b.f, dtype=torch.float32, device=dev) for _ in range(rot)]
         ats = [torch.tensor(a_np, dtype=torch.float32, device=dev) for _ in range(rot)]
         outs = [torch.empty_like(fs[0]) for _ in range(rot)]
-        ws = torch.empty(q.batched_workspace_bytes([plan], b.n_cells, "f32"), dtype=torch.uint8, device=dev)
+        # room for both forward evaluators (line engine, FFT loss) and the derivatives
+        wsb = []
+        for fft in (0, 1):
+            plan.set_tuning(loss_fft=fft)
+            wsb.append(q.batched_workspace_bytes([plan], b.n_cells, "f32"))
+        ws = torch.empty(2 * max(wsb), dtype=torch.uint8, device=dev)
         if wl == "batch3d":
             tuning = q.qdvm_tune_batched([plan], cp, co, fs[0], "f32", workspace=ws)
 
@@ -515,6 +522,8 @@ def main():
     ap.add_argument("--impl", default="qdvm", choices=["qdvm", "reference"])
     ap.add_argument("--ref-cells", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--loss-fft", type=int, default=1, choices=[0, 1],
+                    help="single3d: loss as an FFT convolution (1) or by the line engine (0)")
     ap.add_argument("--workload", default="batch2d", choices=["batch2d", "batch3d", "jvp3d", "vjp3d", "single3d"])
     ap.add_argument("--nbar", type=int, default=None)
     ap.add_argument("--tuning", default=None,

@@ -26,6 +26,11 @@ qdvm_status build_batch(const qdvm_plan_t* plans, int n_plans, BatchDev* b, int*
     return QDVM_OK;
 }
 
+// 3D forward with the loss as an FFT convolution (tuning loss_fft = 1)
+bool use_fast3d(const BatchDev& b, const qdvm_tuning& t, int prec) {
+    return t.loss_fft && b.p[0].d == 3 && fast3d_supported(b, prec);
+}
+
 }  // namespace
 
 BatchDev single_batch(const qdvm_plan_s* p) {
@@ -46,7 +51,9 @@ extern "C" qdvm_status qdvm_eval_workspace(qdvm_plan_t p, int prec, size_t* byte
         *bytes = std::max(fused2d_single_workspace(p, prec), der);
         return QDVM_OK;
     }
-    *bytes = std::max(engine_workspace(QDVM_MODE_FWD, b, 1, prec, true, p->tune.line_chunks), der);
+    const size_t fwd = use_fast3d(b, p->tune, prec) ? fast3d_workspace(b, 1, prec, true, p->tune.line_chunks)
+                                                     : engine_workspace(QDVM_MODE_FWD, b, 1, prec, true, p->tune.line_chunks);
+    *bytes = std::max(fwd, der);
     return QDVM_OK;
 }
 
@@ -58,7 +65,10 @@ extern "C" qdvm_status qdvm_eval(qdvm_plan_t p, const void* f, void* Q, int prec
     if (f == Q) return qdvm_fail(QDVM_ERR_INVALID_ARG, "f must not alias Q");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (p->d == 2 && fused2d_supported(p->N, p->Ntilde, prec)) return fused2d_eval_single(p, f, Q, prec, ws, ws_bytes, st);
-    return engine_run(QDVM_MODE_FWD, single_batch(p), 1, nullptr, nullptr, f, nullptr, Q, nullptr, prec, ws, ws_bytes,
+    const BatchDev b = single_batch(p);
+    if (use_fast3d(b, p->tune, prec))
+        return fast3d_run(b, 1, nullptr, nullptr, f, Q, nullptr, prec, ws, ws_bytes, true, p->tune.line_chunks, st);
+    return engine_run(QDVM_MODE_FWD, b, 1, nullptr, nullptr, f, nullptr, Q, nullptr, prec, ws, ws_bytes,
                       true, p->tune.line_chunks, st);
 }
 
@@ -77,8 +87,11 @@ extern "C" qdvm_status qdvm_batched_workspace(const qdvm_plan_t* plans, int n_pl
     if (s != QDVM_OK) return s;
     const size_t der = std::max(engine_workspace(QDVM_MODE_JVP, b, n_cells, prec, false, plans[0]->tune.line_chunks),
                                 engine_workspace(QDVM_MODE_VJP, b, n_cells, prec, false, plans[0]->tune.line_chunks));
-    const size_t fwd = all_fused2d(plans, n_plans, d, prec) ? 256 + round256((size_t)std::max(n_cells, 1) * sizeof(int))
-                                                            : engine_workspace(QDVM_MODE_FWD, b, n_cells, prec, false, plans[0]->tune.line_chunks);
+    const int lc = plans[0]->tune.line_chunks;
+    size_t fwd;
+    if (all_fused2d(plans, n_plans, d, prec)) fwd = 256 + round256((size_t)std::max(n_cells, 1) * sizeof(int));
+    else if (use_fast3d(b, plans[0]->tune, prec)) fwd = fast3d_workspace(b, n_cells, prec, false, lc);
+    else fwd = engine_workspace(QDVM_MODE_FWD, b, n_cells, prec, false, lc);
     *bytes = std::max(fwd, der);
     return QDVM_OK;
 }
@@ -102,7 +115,10 @@ extern "C" qdvm_status qdvm_eval_batched(const qdvm_plan_t* plans, int n_plans, 
             return qdvm_fail(QDVM_ERR_INVALID_ARG, "workspace too small for qdvm_eval_batched");
         return fused2d_eval_batched(b, plans[0]->tune, n_cells, cell_plan, cell_offset, f, Q, moments, prec, ws, st);
     }
-    // the engine checks its own layout against ws_bytes
+    // the 3D evaluator and the engine check their own layouts against ws_bytes
+    if (use_fast3d(b, plans[0]->tune, prec))
+        return fast3d_run(b, n_cells, cell_plan, cell_offset, f, Q, moments, prec, ws, ws_bytes, false,
+                          plans[0]->tune.line_chunks, st);
     return engine_run(QDVM_MODE_FWD, b, n_cells, cell_plan, cell_offset, f, nullptr, Q, moments, prec, ws, ws_bytes,
                       false, plans[0]->tune.line_chunks, st);
 }
@@ -179,9 +195,13 @@ extern "C" qdvm_status qdvm_tune_batched(const qdvm_plan_t* plans, int n_plans, 
             for (int dj : {0, 1, 2}) cand.push_back(qdvm_tuning{th, dj, saved.line_chunks, 0});
         for (int th : {256, 512}) cand.push_back(qdvm_tuning{th, saved.direct_j, saved.line_chunks, 1});
     } else {
+        const qdvm_tuning fft{saved.threads, saved.direct_j, 0, 1};
+        const bool f3 = use_fast3d(b, fft, prec);
         for (int c : {0, 1, 2, 3, 4, 6, 8}) {
             if (engine_workspace(QDVM_MODE_FWD, b, n_cells, prec, false, c) <= ws_bytes)
-                cand.push_back(qdvm_tuning{saved.threads, saved.direct_j, c, saved.loss_fft});
+                cand.push_back(qdvm_tuning{saved.threads, saved.direct_j, c, 0});
+            if (f3 && fast3d_workspace(b, n_cells, prec, false, c) <= ws_bytes)
+                cand.push_back(qdvm_tuning{saved.threads, saved.direct_j, c, 1});
         }
     }
     if (cand.empty()) return qdvm_fail(QDVM_ERR_INVALID_ARG, "workspace too small for every candidate");

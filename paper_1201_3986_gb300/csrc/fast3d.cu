@@ -1,0 +1,341 @@
+// 3D forward evaluation with the loss as one convolution per cell.
+//
+// The loss part sum_e c_e f V_e equals f (K * f) with K the weighted
+// displacement histogram of all (k, l) terms (its transform is the plan's
+// Ktilde, factorised line by line).  A work item (cell, chunk of lines)
+// therefore only sums the gain c_e W_e P_e of its lines; the first chunk of
+// a cell also evaluates K * f with a 3D Stockham FFT (mixed radix 2/4) over
+// the CTA's global scratch.  Without V there is no P buffer and no barrier
+// per line: each thread owns z-columns of 8 points at a fixed (y, x), runs
+// the item's lines for one column at a time and keeps the sums in
+// registers.  The cell sits in shared memory with a periodic halo of Ntilde
+// along z; y and x wrap with a mask (N = 16 or 32, a power of two; the
+// halo is Ntilde < N / 2 planes on each side).
+#include <algorithm>
+
+#include "fft.cuh"
+#include "engine.cuh"
+#include "qdvm_internal.cuh"
+
+namespace {
+
+constexpr int kThreadsF3 = 512;
+
+// One Stockham pass of radix R along AXIS (0 = z, 1 = y, 2 = x) over all N^2
+// lines of an N^3 complex array in global memory.  Consecutive threads take
+// consecutive addresses: along x they share a line, along y and z they take
+// neighbouring lines.
+template <typename C, int N, int R, int NS, bool INV, int AXIS>
+__device__ __forceinline__ void fft3_pass(const C* __restrict__ src, C* __restrict__ dst, const C* __restrict__ tw) {
+    constexpr int NB = N / R, NL = N * N;
+    constexpr int ST = AXIS == 2 ? 1 : (AXIS == 1 ? N : NL);
+    for (int b = threadIdx.x; b < NL * NB; b += blockDim.x) {
+        int line, j;
+        if (AXIS == 2) {
+            line = b / NB;
+            j = b - line * NB;
+        } else {
+            line = b % NL;
+            j = b / NL;
+        }
+        const int base = AXIS == 2 ? line * N : (AXIS == 1 ? (line / N) * NL + (line % N) : line);
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[base + (j + r * NB) * ST];
+        const int jm = j % NS;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            C w = tw[(jm * (N / (NS * R)) * r) % N];
+            if (INV) w.y = -w.y;
+            v[r] = cmul(v[r], w);
+        }
+        dft_small<R, INV>(v);
+        const int idxD = (j / NS) * NS * R + jm;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[base + (idxD + r * NS) * ST] = v[r];
+    }
+}
+
+template <typename C, int N, bool INV, int AXIS, int NS, int R, int... Rs>
+__device__ __forceinline__ C* fft3_passes(C* a, C* b, const C* tw) {
+    fft3_pass<C, N, R, NS, INV, AXIS>(a, b, tw);
+    __syncthreads();
+    if constexpr (sizeof...(Rs) > 0)
+        return fft3_passes<C, N, INV, AXIS, NS * R, Rs...>(b, a, tw);
+    else
+        return b;
+}
+
+template <typename C, int N, bool INV, int AXIS>
+__device__ __forceinline__ C* fft3_axis(C* a, C* b, const C* tw) {
+    if constexpr (N == 32) return fft3_passes<C, N, INV, AXIS, 1, 2, 4, 4>(a, b, tw);
+    else return fft3_passes<C, N, INV, AXIS, 1, 4, 4>(a, b, tw);  // N == 16
+}
+
+template <typename T, bool KAHAN, int N>
+__device__ void fast3d_item(const PlanDev& P, const int lb, const int le, const bool do_loss,
+                            const T* __restrict__ fcell, T* __restrict__ fz, typename Cplx<T>::type* A,
+                            typename Cplx<T>::type* B, T* __restrict__ dst) {
+    using C = typename Cplx<T>::type;
+    constexpr int N2 = N * N, N3 = N2 * N, ZC = 8, NU = (N / ZC) * N2, M = N - 1;
+    const int NT = blockDim.x, tid = threadIdx.x, H = P.Ntilde;
+
+    for (int p = tid; p < (N + 2 * H) * N2; p += NT) {
+        const int zz = p / N2;
+        fz[p] = fcell[((zz - H + N) & M) * N2 + (p - zz * N2)];
+    }
+    if (do_loss)
+        for (int i = tid; i < N3; i += NT) A[i] = C{fcell[i], T(0)};
+    __syncthreads();
+
+    const C* conv = nullptr;
+    if (do_loss) {
+        const C* tw;
+        const T* kh;
+        if constexpr (sizeof(T) == 8) {
+            tw = reinterpret_cast<const C*>(P.tw);
+            kh = reinterpret_cast<const T*>(P.khat);
+        } else {
+            tw = reinterpret_cast<const C*>(P.tw_f);
+            kh = reinterpret_cast<const T*>(P.khat_f);
+        }
+        C* r = fft3_axis<C, N, false, 2>(A, B, tw);
+        r = fft3_axis<C, N, false, 1>(r, r == A ? B : A, tw);
+        r = fft3_axis<C, N, false, 0>(r, r == A ? B : A, tw);
+        for (int i = tid; i < N3; i += NT) {
+            const T k = kh[i];
+            r[i].x *= k;
+            r[i].y *= k;
+        }
+        __syncthreads();
+        r = fft3_axis<C, N, true, 0>(r, r == A ? B : A, tw);
+        r = fft3_axis<C, N, true, 1>(r, r == A ? B : A, tw);
+        r = fft3_axis<C, N, true, 2>(r, r == A ? B : A, tw);
+        conv = r;
+    }
+
+    for (int u = tid; u < NU; u += NT) {
+        const int zb = u / N2, rr = u - zb * N2, y = rr / N, x = rr - (rr / N) * N, z0 = zb * ZC;
+        T acc[ZC], cmp[ZC];
+#pragma unroll
+        for (int zc = 0; zc < ZC; ++zc) {
+            // the loss, - f (K * f), starts the sum
+            acc[zc] = do_loss ? -fz[(z0 + zc + H) * N2 + rr] * conv[(z0 + zc) * N2 + rr].x : T(0);
+            cmp[zc] = T(0);
+        }
+        for (int li = lb; li < le; ++li) {
+            const int4 e = P.lines[li];
+            const T c = (T)P.c[li];
+            const int ps = P.plane_start[li], pn = P.plane_start[li + 1] - ps;
+            const char4* __restrict__ pl = P.plane + ps;
+            T s[ZC], w[ZC];
+#pragma unroll
+            for (int zc = 0; zc < ZC; ++zc) s[zc] = w[zc] = T(0);
+            for (int t = 0; t < pn; ++t) {
+                const char4 l = __ldg(pl + t);
+                const T* b = fz + (z0 + l.x + H) * N2 + ((y + l.y) & M) * N + ((x + l.z) & M);
+#pragma unroll
+                for (int zc = 0; zc < ZC; ++zc) s[zc] += b[zc * N2];
+            }
+            for (int j = 1; j <= e.w; ++j) {
+                const T* bp = fz + (z0 + j * e.x + H) * N2 + ((y + j * e.y) & M) * N + ((x + j * e.z) & M);
+                const T* bm = fz + (z0 - j * e.x + H) * N2 + ((y - j * e.y) & M) * N + ((x - j * e.z) & M);
+#pragma unroll
+                for (int zc = 0; zc < ZC; ++zc) w[zc] += bp[zc * N2] + bm[zc * N2];
+            }
+#pragma unroll
+            for (int zc = 0; zc < ZC; ++zc) comp_add<T, KAHAN>(acc[zc], cmp[zc], c * w[zc] * s[zc]);
+        }
+#pragma unroll
+        for (int zc = 0; zc < ZC; ++zc) dst[(z0 + zc) * N2 + rr] = KAHAN ? acc[zc] + cmp[zc] : acc[zc];
+    }
+}
+
+template <typename T, bool KAHAN, int N>
+__global__ void __launch_bounds__(kThreadsF3) k_fast3d(BatchDev Bt, int n_cells, int Cn, const int* __restrict__ cell_plan,
+                                                       const int64_t* __restrict__ cell_offset,
+                                                       const int* __restrict__ order, int* counter,
+                                                       const T* __restrict__ f, T* __restrict__ out,
+                                                       T* __restrict__ part, size_t part_stride, char* scratch,
+                                                       size_t scr_stride) {
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item, s_cell;
+    __shared__ PlanDev s_plan;
+    const int n_items = n_cells * Cn;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int it = atomicAdd(counter, 1);
+            int cell = -1;
+            if (it < n_items) cell = order[it / Cn];
+            s_item = cell >= 0 ? it : -1;
+            s_cell = cell;
+            if (cell >= 0) {
+                const int pi = cell_plan[cell];
+#pragma unroll
+                for (int q = 0; q < QDVM_MAX_BATCH_PLANS; ++q)
+                    if (q == pi) s_plan = Bt.p[q];
+            }
+        }
+        __syncthreads();
+        const int item = s_item, cell = s_cell;
+        if (item < 0) break;
+        const PlanDev P = s_plan;
+        const int chunk = item % Cn;
+        const int lpc = (P.n_lines + Cn - 1) / Cn;
+        const int lb = min(chunk * lpc, P.n_lines), le = min(lb + lpc, P.n_lines);
+        const int64_t off = cell_offset[cell];
+        T* dst = Cn == 1 ? out + off : part + ((size_t)cell * Cn + chunk) * part_stride;
+        C* A = reinterpret_cast<C*>(scratch + (size_t)blockIdx.x * scr_stride);
+        C* B = A + N * N * N;
+        fast3d_item<T, KAHAN, N>(P, lb, le, chunk == 0, f + off, reinterpret_cast<T*>(smem_raw), A, B, dst);
+        __syncthreads();
+    }
+}
+
+__global__ void k_fast3d_single_init(int* counter, int* order, int* cell_plan, int64_t* cell_offset) {
+    *counter = 0;
+    *order = 0;
+    *cell_plan = 0;
+    *cell_offset = 0;
+}
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct F3Layout {
+    int N, C, grid;
+    size_t smem, scr_stride, part_stride, off_scr, off_part, total;
+};
+
+template <typename T, bool KAHAN, int N>
+int f3_occupancy(size_t smem) {
+    auto k = k_fast3d<T, KAHAN, N>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kThreadsF3, smem);
+    return per > 0 ? per : 1;
+}
+
+int f3_occ(int N, int prec, size_t smem) {
+    if (prec == QDVM_F64) return N == 32 ? f3_occupancy<double, false, 32>(smem) : f3_occupancy<double, false, 16>(smem);
+    if (prec == QDVM_F32_KAHAN) return N == 32 ? f3_occupancy<float, true, 32>(smem) : f3_occupancy<float, true, 16>(smem);
+    return N == 32 ? f3_occupancy<float, false, 32>(smem) : f3_occupancy<float, false, 16>(smem);
+}
+
+// 0 unless every plan is 3D with the same N in {16, 32}, has the loss
+// transform, and the haloed cell fits in shared memory.
+int f3_size(const BatchDev& b, int prec, size_t* smem) {
+    const size_t es = prec == QDVM_F64 ? sizeof(double) : sizeof(float);
+    const int N = b.p[0].N;
+    int H = 0;
+    if (N != 16 && N != 32) return 0;
+    for (int i = 0; i < b.n_plans; ++i) {
+        const PlanDev& p = b.p[i];
+        if (p.d != 3 || p.N != N || !p.khat || !p.khat_f || !p.tw || !p.tw_f) return 0;
+        H = std::max(H, p.Ntilde);
+    }
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t s = (size_t)(N + 2 * H) * N * N * es;
+    if (s + 1024 > (size_t)optin) return 0;
+    if (smem) *smem = s;
+    return N;
+}
+
+F3Layout f3_layout(const BatchDev& b, int n_cells, int prec, bool single, int chunks) {
+    F3Layout g{};
+    g.N = f3_size(b, prec, &g.smem);
+    const size_t es = prec == QDVM_F64 ? sizeof(double) : sizeof(float);
+    const size_t n3 = (size_t)g.N * g.N * g.N;
+    int maxLines = 1;
+    for (int i = 0; i < b.n_plans; ++i) maxLines = std::max(maxLines, b.p[i].n_lines);
+    const int slots = f3_occ(g.N, prec, g.smem) * qdvm_num_sms();
+    const int nc = std::max(n_cells, 1);
+    if (single)
+        g.C = std::max(1, std::min(maxLines, slots));
+    else
+        g.C = std::max(1, std::min(maxLines, (4 * slots + nc - 1) / nc));
+    if (!single && nc >= 2 * slots) g.C = 1;
+    if (chunks > 0) g.C = std::max(1, std::min(maxLines, chunks));
+    g.grid = (int)std::max(1L, std::min((long)nc * g.C, (long)slots));
+    g.scr_stride = a256(2 * n3 * 2 * es);  // two complex N^3 FFT buffers
+    g.part_stride = g.C > 1 ? n3 : 0;
+    g.off_scr = 256 + a256((size_t)nc * sizeof(int)) + 256;  // counter, order, single-cell tables
+    g.off_part = g.off_scr + (size_t)g.grid * g.scr_stride;
+    g.total = g.off_part + (g.C > 1 ? a256((size_t)nc * g.C * n3 * es) : 0);
+    return g;
+}
+
+template <typename T, bool KAHAN, int N>
+void f3_launch(const F3Layout& g, const BatchDev& b, int n_cells, const int* cp, const int64_t* co, const int* order,
+               int* counter, const void* f, void* out, char* base, cudaStream_t st) {
+    auto k = k_fast3d<T, KAHAN, N>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+    k<<<g.grid, kThreadsF3, g.smem, st>>>(b, n_cells, g.C, cp, co, order, counter, static_cast<const T*>(f),
+                                           static_cast<T*>(out), reinterpret_cast<T*>(base + g.off_part),
+                                           g.part_stride, base + g.off_scr, g.scr_stride);
+}
+
+template <typename T, bool KAHAN>
+void f3_launch_n(const F3Layout& g, const BatchDev& b, int n_cells, const int* cp, const int64_t* co,
+                 const int* order, int* counter, const void* f, void* out, char* base, cudaStream_t st) {
+    if (g.N == 32) f3_launch<T, KAHAN, 32>(g, b, n_cells, cp, co, order, counter, f, out, base, st);
+    else f3_launch<T, KAHAN, 16>(g, b, n_cells, cp, co, order, counter, f, out, base, st);
+}
+
+template <typename T, bool KAHAN>
+void f3_reduce(const F3Layout& g, const BatchDev& b, int n_cells, const int* cp, const int64_t* co, char* base,
+               void* out, cudaStream_t st) {
+    dim3 grid(8, std::max(1, std::min(n_cells, 65535)));
+    eng::k_reduce_chunks<T, KAHAN><<<grid, 256, 0, st>>>(b, n_cells, g.C, cp, co,
+                                                          reinterpret_cast<const T*>(base + g.off_part), g.part_stride,
+                                                          static_cast<T*>(out));
+}
+
+}  // namespace
+
+qdvm_status moments_batched_launch(const BatchDev& b, int n_cells, const int* cell_plan, const int64_t* cell_offset,
+                                   const void* Q, int prec, double* m, cudaStream_t st);
+
+bool fast3d_supported(const BatchDev& b, int prec) { return f3_size(b, prec, nullptr) != 0; }
+
+size_t fast3d_workspace(const BatchDev& b, int n_cells, int prec, bool single, int chunks) {
+    return f3_layout(b, single ? 1 : n_cells, prec, single, chunks).total;
+}
+
+qdvm_status fast3d_run(const BatchDev& b, int n_cells, const int* cell_plan, const int64_t* cell_offset, const void* f,
+                       void* out, double* moments, int prec, void* ws, size_t ws_bytes, bool single, int chunks,
+                       cudaStream_t st) {
+    const int nc = single ? 1 : n_cells;
+    const F3Layout g = f3_layout(b, nc, prec, single, chunks);
+    if (!g.N) return qdvm_fail(QDVM_ERR_INVALID_ARG, "the 3D FFT-loss evaluator does not support this batch");
+    if (!ws || ws_bytes < g.total) return qdvm_fail(QDVM_ERR_INVALID_ARG, "workspace too small for the 3D evaluator");
+    char* base = static_cast<char*>(ws);
+    int* counter = reinterpret_cast<int*>(base);
+    int* order = reinterpret_cast<int*>(base + 256);
+    if (single) {
+        char* tab = base + 256 + 256;
+        int* cp = reinterpret_cast<int*>(tab);
+        int64_t* co = reinterpret_cast<int64_t*>(tab + 128);
+        k_fast3d_single_init<<<1, 1, 0, st>>>(counter, order, cp, co);
+        QDVM_LAUNCH_CHECK("3D evaluator single init");
+        cell_plan = cp;
+        cell_offset = co;
+    } else {
+        qdvm_status s = schedule_launch(b, nc, cell_plan, order, counter, st);
+        if (s != QDVM_OK) return s;
+    }
+    if (prec == QDVM_F64) f3_launch_n<double, false>(g, b, nc, cell_plan, cell_offset, order, counter, f, out, base, st);
+    else if (prec == QDVM_F32_KAHAN) f3_launch_n<float, true>(g, b, nc, cell_plan, cell_offset, order, counter, f, out, base, st);
+    else f3_launch_n<float, false>(g, b, nc, cell_plan, cell_offset, order, counter, f, out, base, st);
+    QDVM_LAUNCH_CHECK("3D evaluator launch");
+    if (g.C > 1) {
+        if (prec == QDVM_F64) f3_reduce<double, false>(g, b, nc, cell_plan, cell_offset, base, out, st);
+        else if (prec == QDVM_F32_KAHAN) f3_reduce<float, true>(g, b, nc, cell_plan, cell_offset, base, out, st);
+        else f3_reduce<float, false>(g, b, nc, cell_plan, cell_offset, base, out, st);
+        QDVM_LAUNCH_CHECK("3D evaluator reduce launch");
+    }
+    if (moments) return moments_batched_launch(b, nc, cell_plan, cell_offset, out, prec, moments, st);
+    return QDVM_OK;
+}

@@ -304,6 +304,48 @@ __global__ void k_twiddles(int N, double2* tw, float2* twf) {
     twf[t] = make_float2((float)c, (float)-s);
 }
 
+// Ktilde(xi) = sum_e c_e D_e(xi) Lambda_e(xi) / N^d with
+// D_e = 2 sum_{j=1..J_e} cos(2 pi j (e.xi) / N) (the line factor) and
+// Lambda_e = sum_{l in plane list} cos(2 pi (l.xi) / N) (the e^perp factor):
+// the transform of the loss kernel K factorises line by line (the kernel
+// modes of eq. (decDVM) on the diagonal K = L).  Fixed summation order,
+// phases reduced exactly modulo N.  One thread per xi.
+__global__ void k_khat_factored(int d, int N, int n_lines, const int4* lines, const double* c,
+                                const int* plane_start, const char4* plane, double* kh, float* khf) {
+    __shared__ double ct[64];
+    for (int t = threadIdx.x; t < N; t += blockDim.x) ct[t] = cospi(2.0 * t / N);
+    __syncthreads();
+    int total = N * N;
+    if (d == 3) total *= N;
+    const int xi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (xi >= total) return;
+    int x[3] = {0, 0, 0};
+    int r = xi;
+    for (int a = d - 1; a >= 0; --a) {
+        x[a] = r % N;
+        r /= N;
+    }
+    double acc = 0.0;
+    for (int li = 0; li < n_lines; ++li) {
+        const int4 e = lines[li];
+        int ed = (e.x * x[0] + e.y * x[1] + e.z * x[2]) % N;
+        ed += ed < 0 ? N : 0;
+        double D = 0.0;
+        for (int j = 1; j <= e.w; ++j) D += ct[(j * ed) % N];
+        double lam = 0.0;
+        for (int t = plane_start[li]; t < plane_start[li + 1]; ++t) {
+            const char4 l = plane[t];
+            int ph = (l.x * x[0] + l.y * x[1] + l.z * x[2]) % N;
+            ph += ph < 0 ? N : 0;
+            lam += ct[ph];
+        }
+        acc += c[li] * 2.0 * D * lam;
+    }
+    acc /= (double)total;
+    kh[xi] = acc;
+    khf[xi] = (float)acc;
+}
+
 // ------------------------------------------------------------ plan lifecycle
 
 static void plan_free(qdvm_plan_s* p) {
@@ -404,6 +446,18 @@ static qdvm_status build_tables(qdvm_plan_s* p) {
                         cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(qdvm_cuda_status(e, "plane start upload"));
     k_plane_emit<<<total, 256>>>(d, total, p->d_lines, p->Ntilde, p->d_plane_start, p->d_plane);
+    if (d == 3 && p->N <= 32) {
+        const int N = p->N, n3 = N * N * N;
+        if ((e = cudaMalloc(&p->d_khat, n3 * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_khat_f, n3 * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_tw, N * sizeof(double2))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_tw_f, N * sizeof(float2))) != cudaSuccess)
+            return fail(qdvm_cuda_status(e, "3D loss kernel tables"));
+        k_khat_factored<<<(n3 + 127) / 128, 128>>>(3, N, total, p->d_lines, p->d_c, p->d_plane_start, p->d_plane,
+                                                   p->d_khat, p->d_khat_f);
+        k_twiddles<<<(N + 63) / 64, 64>>>(N, p->d_tw, p->d_tw_f);
+        if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(qdvm_cuda_status(e, "3D loss kernel tables"));
+    }
     if (d == 2 && p->N <= 64) {
         const int N = p->N, n2 = N * N;
         double* dK = nullptr;

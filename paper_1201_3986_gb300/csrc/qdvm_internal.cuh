@@ -30,10 +30,10 @@ struct qdvm_plan_s {
     double* d_pair_c;     // 2D: c_e (= c_{e^perp})
     int* d_plane_start;   // 3D: n_lines + 1 offsets into d_plane
     char4* d_plane;       // (l0, l1, l2, 0), l in e^perp, 0 < |l|_inf <= Ntilde
-    // 2D, N <= 64: the loss as one convolution, loss_i = f_i (K * f)_i with
-    // K(m) = sum_e c_e #{(j, l): j e + l = m}; Ktilde(xi) = sum_m K(m)
-    // cos(2 pi m.xi / N) / N^2 (real: K is symmetric), and the N-th roots of
-    // unity exp(-2 pi i t / N) for the FFTs.
+    // 2D with N <= 64 and 3D with N <= 32: the loss as one convolution,
+    // loss_i = f_i (K * f)_i with K(m) = sum_e c_e #{(j, l): j e + l = m};
+    // Ktilde(xi) = sum_m K(m) cos(2 pi m.xi / N) / N^d (real: K is
+    // symmetric), and the N-th roots of unity exp(-2 pi i t / N) for the FFTs.
     double* d_khat;
     float* d_khat_f;
     double2* d_tw;
@@ -158,3 +158,12 @@ size_t engine_workspace(int mode, const BatchDev& b, int n_cells, int prec, bool
 qdvm_status engine_run(int mode, const BatchDev& b, int n_cells, const int* cell_plan, const int64_t* cell_offset,
                        const void* f, const void* aux, void* out, double* moments, int prec, void* ws,
                        size_t ws_bytes, bool single, int chunks, cudaStream_t st);
+
+// ------------------------------------------------------------ 3D FFT-loss evaluator
+// Forward 3D batches whose plans share N in {16, 32}: the loss as one FFT
+// convolution per cell, the gain per line with register accumulation.
+bool fast3d_supported(const BatchDev& b, int prec);
+size_t fast3d_workspace(const BatchDev& b, int n_cells, int prec, bool single, int chunks);
+qdvm_status fast3d_run(const BatchDev& b, int n_cells, const int* cell_plan, const int64_t* cell_offset, const void* f,
+                       void* out, double* moments, int prec, void* ws, size_t ws_bytes, bool single, int chunks,
+                       cudaStream_t st);

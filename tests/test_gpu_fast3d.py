@@ -1,0 +1,161 @@
+"""GPU parity of the 3D evaluator that takes the loss as one FFT convolution
+per cell (tuning loss_fft = 1; plans sharing N in {16, 32}) against the CPU
+oracle, plus the fall-back to the line engine where it does not apply."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "f32_kahan": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def q():
+    import paper_1201_3986_gb300 as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+def _dt(torch, prec):
+    return torch.float64 if prec == "f64" else torch.float32
+
+
+def _sample_idx(N, n, seed):
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(N ** 3, size=n, replace=False)
+    extra = [0, N - 1, N * N - 1, N ** 3 - 1, (N // 2) * (N * N + N + 1)]
+    return np.unique(np.concatenate([idx, extra])).astype(np.int64)
+
+
+def _run_batch(q, torch, b, plans, prec, chunks=0):
+    for p in plans:
+        p.set_tuning(loss_fft=1, line_chunks=chunks)
+    cp = torch.zeros(b.n_cells, dtype=torch.int32, device="cuda")
+    co = torch.tensor(b.offsets, dtype=torch.int64, device="cuda")
+    f = torch.tensor(b.f, dtype=_dt(torch, prec), device="cuda")
+    Q, mom = q.qdvm_eval_batched(plans, cp, co, f, prec)
+    return Q.cpu().numpy().astype(np.float64), mom.cpu().numpy(), f.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("chunks", [0, 1, 3])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32_kahan"])
+@pytest.mark.parametrize("kernel", ["unit", "hp"])
+def test_batched_N16_every_cell(q, torch, chunks, prec, kernel):
+    b = synth.batch_3d(5, N=16, L=6.0, seed=12)
+    Qn, mom, fin = _run_batch(q, torch, b, [q.Plan(3, 16, 3, 6.0, kernel=kernel)], prec, chunks)
+    for c in range(b.n_cells):
+        r = oracle.q(b.cell(c, fin), 6.0, 3, kernel=kernel)
+        assert oracle.rel_linf(b.cell(c, Qn), r["Q"], r["scale"]) <= TOL[prec]
+        # mass: the loss convolution and the gain sums cancel to rounding
+        h3 = (12.0 / 16) ** 3
+        assert abs(mom[c, 0]) <= (1e-13 if prec == "f64" else 1e-6) * h3 * r["scale"].sum()
+
+
+@pytest.mark.parametrize("Nt,Nbar", [(2, 2), (5, 4), (7, 7)])
+def test_batched_N16_other_truncations(q, torch, Nt, Nbar):
+    """The halo follows the plan's Ntilde (any 2 Ntilde < N)."""
+    b = synth.batch_3d(3, N=16, L=6.0, seed=Nt)
+    for prec in ("f64", "f32_kahan"):
+        Qn, _, fin = _run_batch(q, torch, b, [q.Plan(3, 16, Nbar, 6.0, kernel="hp", Ntilde=Nt)], prec)
+        for c in range(b.n_cells):
+            r = oracle.q(b.cell(c, fin), 6.0, Nbar, kernel="hp", Ntilde=Nt)
+            assert oracle.rel_linf(b.cell(c, Qn), r["Q"], r["scale"]) <= TOL[prec]
+
+
+@pytest.mark.parametrize("Nbar", [3, 5, 7])
+@pytest.mark.parametrize("prec", ["f32", "f32_kahan"])
+def test_batched_N32_sampled(q, torch, Nbar, prec):
+    """32^3 cells, hard spheres, Ntilde = 7: sampled points of every cell."""
+    b = synth.batch_3d(4, N=32, L=6.0, seed=Nbar)
+    Qn, mom, fin = _run_batch(q, torch, b, [q.Plan(3, 32, Nbar, 6.0, kernel="hp")], prec)
+    assert np.all(np.isfinite(Qn))
+    for c in range(b.n_cells):
+        idx = _sample_idx(32, 40, 10 * Nbar + c)
+        r = oracle.q_points(b.cell(c, fin), 6.0, Nbar, idx, kernel="hp")
+        err = np.max(np.abs(b.cell(c, Qn).ravel()[idx] - r["Q"])) / np.max(r["scale"])
+        assert err <= 1e-5, f"cell {c}: {err:.3e}"
+
+
+def test_single_cell_trimaxwellian_N32(q, torch):
+    f = synth.trimaxwellian_3d(32, 6.0).astype(np.float32).astype(np.float64)
+    plan = q.Plan(3, 32, 5, 6.0, kernel="hp")
+    plan.set_tuning(loss_fft=1)
+    Q = q.qdvm_eval(plan, torch.tensor(f, dtype=torch.float32, device="cuda"), "f32_kahan").cpu().numpy()
+    idx = _sample_idx(32, 120, 3)
+    r = oracle.q_points(f, 6.0, 5, idx, kernel="hp")
+    assert np.max(np.abs(Q.astype(np.float64).ravel()[idx] - r["Q"])) / np.max(r["scale"]) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32_kahan"])
+def test_single_cell_N16_full(q, torch, prec):
+    f = synth.mixture(3, 16, 6.0, np.random.default_rng(21))
+    f = f if prec == "f64" else f.astype(np.float32).astype(np.float64)
+    plan = q.Plan(3, 16, 3, 6.0, kernel="hp")
+    plan.set_tuning(loss_fft=1)
+    Q = q.qdvm_eval(plan, torch.tensor(f, dtype=_dt(torch, prec), device="cuda"), prec).cpu().numpy()
+    r = oracle.q(f, 6.0, 3, kernel="hp")
+    assert oracle.rel_linf(Q.astype(np.float64), r["Q"], r["scale"]) <= TOL[prec]
+
+
+def test_fallbacks_fp64_N32_and_mixed_sizes(q, torch):
+    """FP64 32^3 does not fit on chip and a batch mixing 12^3 and 16^3 has no
+    common N: both run the line engine with loss_fft = 1 set."""
+    b = synth.batch_3d(2, N=32, L=6.0, seed=2)
+    Qn, _, fin = _run_batch(q, torch, b, [q.Plan(3, 32, 3, 6.0, kernel="hp")], "f64")
+    idx = _sample_idx(32, 40, 9)
+    r = oracle.q_points(b.cell(1, fin), 6.0, 3, idx, kernel="hp")
+    assert np.max(np.abs(b.cell(1, Qn).ravel()[idx] - r["Q"])) / np.max(r["scale"]) <= 1e-12
+
+    b1 = synth.batch_3d(2, N=12, L=6.0, seed=4)
+    b2 = synth.batch_3d(2, N=16, L=6.0, seed=5)
+    bb = synth.Batch(3, 6.0, np.concatenate([b1.Ns, b2.Ns]), np.concatenate([b1.f, b2.f]))
+    plans = [q.Plan(3, 12, 2, 6.0), q.Plan(3, 16, 3, 6.0)]
+    for p in plans:
+        p.set_tuning(loss_fft=1)
+    cp = torch.tensor([0, 0, 1, 1], dtype=torch.int32, device="cuda")
+    co = torch.tensor(bb.offsets, dtype=torch.int64, device="cuda")
+    f = torch.tensor(bb.f, dtype=torch.float32, device="cuda")
+    Q, _ = q.qdvm_eval_batched(plans, cp, co, f, "f32_kahan")
+    Qn = Q.cpu().numpy().astype(np.float64)
+    fin = f.cpu().numpy().astype(np.float64)
+    for c in range(4):
+        r = oracle.q(bb.cell(c, fin), 6.0, 2 if c < 2 else 3)
+        assert oracle.rel_linf(bb.cell(c, Qn), r["Q"], r["scale"]) <= 1e-5
+
+
+def test_autotuner_considers_fft_loss_and_graph_replay(q, torch):
+    b = synth.batch_3d(40, N=16, L=6.0, seed=17)
+    plan = q.Plan(3, 16, 3, 6.0, kernel="hp")
+    cp = torch.zeros(b.n_cells, dtype=torch.int32, device="cuda")
+    co = torch.tensor(b.offsets, dtype=torch.int64, device="cuda")
+    f = torch.tensor(b.f, dtype=torch.float32, device="cuda")
+    plan.set_tuning(loss_fft=1)
+    ws_fft = q.batched_workspace_bytes([plan], b.n_cells, "f32_kahan")
+    plan.set_tuning(loss_fft=0)
+    ws_eng = q.batched_workspace_bytes([plan], b.n_cells, "f32_kahan")
+    ws = torch.empty(8 * max(ws_fft, ws_eng), dtype=torch.uint8, device="cuda")
+    best = q.qdvm_tune_batched([plan], cp, co, f, "f32_kahan", workspace=ws)
+    assert best["loss_fft"] in (0, 1) and plan.tuning() == best
+    plan.set_tuning(loss_fft=1, line_chunks=2)
+    Qd, Md = q.qdvm_eval_batched([plan], cp, co, f, "f32_kahan")
+    Q = torch.full_like(f, float("nan"))
+    M = torch.full((b.n_cells, 5), float("nan"), dtype=torch.float64, device="cuda")
+    g = q.BatchedGraph([plan], cp, co, f, Q, M, "f32_kahan")
+    for _ in range(2):
+        Q.fill_(float("nan"))
+        g.launch()
+        torch.cuda.synchronize()
+        assert torch.equal(Q, Qd) and torch.equal(M, Md)
+    Qn = Qd.cpu().numpy().astype(np.float64)
+    fin = f.cpu().numpy().astype(np.float64)
+    for c in (0, 39):
+        r = oracle.q(b.cell(c, fin), 6.0, 3, kernel="hp")
+        assert oracle.rel_linf(b.cell(c, Qn), r["Q"], r["scale"]) <= 1e-5
