@@ -128,6 +128,15 @@ qdvm_status qdvm_plan_destroy(qdvm_plan_t plan);
 qdvm_status qdvm_plan_info(qdvm_plan_t plan, int* d, int* N, int* Ntilde, int* m, int* n_lines,
                            int64_t* n_terms);
 
+/* Row decomposition of the 3D plane polygons (3D plans with N = 16 or 32
+ * and Ntilde <= 7; the offset sets {l in e^perp, 0 < |l|_inf <= Ntilde} of
+ * eq. (decDVM), alpha'_p, written as rows along an in-plane lattice
+ * vector): the number of line classes
+ * sharing that vector and the total number of rows.  Both are 0 for other
+ * plans, whose 3D evaluation sums the polygons point by point.  Any pointer
+ * may be NULL. */
+qdvm_status qdvm_plan_row_info(qdvm_plan_t plan, int* n_classes, int* n_rows);
+
 /* Copy the line table to HOST arrays of n_lines entries: dirs (3 ints per
  * line, unused components 0, first non-zero component positive, ordered by
  * |e|_inf then lexicographically), J (window half-length), c (weight). */

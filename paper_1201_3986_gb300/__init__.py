@@ -63,6 +63,7 @@ _sig("qdvm_plan_create_ex", [_P(_vp), _i, _i, _i, _i, ctypes.c_double, _i, _i])
 _sig("qdvm_plan_destroy", [_vp])
 _sig("qdvm_plan_info", [_vp, _P(_i), _P(_i), _P(_i), _P(_i), _P(_i), _P(ctypes.c_int64)])
 _sig("qdvm_plan_lines", [_vp, _P(_i), _P(_i), _P(ctypes.c_double)])
+_sig("qdvm_plan_row_info", [_vp, _P(_i), _P(_i)])
 _sig("qdvm_eval_workspace", [_vp, _i, _P(_sz)])
 _sig("qdvm_eval", [_vp, _vp, _vp, _i, _vp, _sz, _vp])
 _sig("qdvm_eval_batched", [_P(_vp), _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _sz, _vp])
@@ -153,6 +154,12 @@ class Plan:
         _check(_lib.qdvm_plan_lines(self.handle, dirs.ctypes.data_as(_P(_i)), J.ctypes.data_as(_P(_i)),
                                     c.ctypes.data_as(_P(ctypes.c_double))), "qdvm_plan_lines")
         return dirs[:, :self.d], J, c
+
+    def row_info(self):
+        """(line classes, rows) of the 3D row decomposition; (0, 0) without."""
+        nc, nr = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.qdvm_plan_row_info(self.handle, ctypes.byref(nc), ctypes.byref(nr)), "qdvm_plan_row_info")
+        return nc.value, nr.value
 
     def eval_workspace(self, prec) -> int:
         b = ctypes.c_size_t()

@@ -193,6 +193,226 @@ __global__ void __launch_bounds__(kThreadsF3) k_fast3d(BatchDev Bt, int n_cells,
     }
 }
 
+// ---------------------------------------------------------------- row form
+// Gain via the row tables of the plan (plan_rows.cu).  For each line class
+// the cell is re-indexed in the class coordinates q = (alpha, beta, gamma),
+// point = M q mod N, and stored as g[(beta N + gamma) SA + alpha] with the
+// first SA - N alpha values repeated after alpha = N - 1, so that a run of up
+// to QDVM_ROW_MAX + 7 points starting at any alpha < N is contiguous.  SA is
+// odd: the 32 lanes of a warp, which differ in gamma (and, for N = 16, in
+// beta), hit 32 distinct banks.
+template <int N>
+__host__ __device__ constexpr int rows_sa() {
+    return (N + QDVM_ROW_MAX + 6) | 1;
+}
+
+// P[k] += sum_{t<LEN} b[k + t], k = 0..7, as one run of LEN + 7 loads and a
+// sliding window.
+template <int LEN, typename T>
+__device__ __forceinline__ void row_run(const T* __restrict__ b, T (&P)[8]) {
+    T v[LEN + 7];
+#pragma unroll
+    for (int t = 0; t < LEN + 7; ++t) v[t] = b[t];
+    T s = v[0];
+#pragma unroll
+    for (int t = 1; t < LEN; ++t) s += v[t];
+    P[0] += s;
+#pragma unroll
+    for (int k = 1; k < 8; ++k) {
+        s += v[LEN - 1 + k] - v[k - 1];
+        P[k] += s;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void row_dispatch(int len, const T* b, T (&P)[8]) {
+    switch (len) {
+        case 1: row_run<1>(b, P); break;
+        case 2: row_run<2>(b, P); break;
+        case 3: row_run<3>(b, P); break;
+        case 4: row_run<4>(b, P); break;
+        case 5: row_run<5>(b, P); break;
+        case 6: row_run<6>(b, P); break;
+        case 7: row_run<7>(b, P); break;
+        case 8: row_run<8>(b, P); break;
+        case 9: row_run<9>(b, P); break;
+        case 10: row_run<10>(b, P); break;
+        case 11: row_run<11>(b, P); break;
+        case 12: row_run<12>(b, P); break;
+        case 13: row_run<13>(b, P); break;
+        case 14: row_run<14>(b, P); break;
+        default: row_run<15>(b, P); break;
+    }
+}
+
+// conv = K * f for the cell (3D FFT over the CTA's scratch A, B).
+template <typename T, int N>
+__device__ const typename Cplx<T>::type* loss_conv(const PlanDev& P, const T* __restrict__ fcell,
+                                                   typename Cplx<T>::type* A, typename Cplx<T>::type* B) {
+    using C = typename Cplx<T>::type;
+    constexpr int N3 = N * N * N;
+    const int NT = blockDim.x, tid = threadIdx.x;
+    for (int i = tid; i < N3; i += NT) A[i] = C{fcell[i], T(0)};
+    __syncthreads();
+    const C* tw;
+    const T* kh;
+    if constexpr (sizeof(T) == 8) {
+        tw = reinterpret_cast<const C*>(P.tw);
+        kh = reinterpret_cast<const T*>(P.khat);
+    } else {
+        tw = reinterpret_cast<const C*>(P.tw_f);
+        kh = reinterpret_cast<const T*>(P.khat_f);
+    }
+    C* r = fft3_axis<C, N, false, 2>(A, B, tw);
+    r = fft3_axis<C, N, false, 1>(r, r == A ? B : A, tw);
+    r = fft3_axis<C, N, false, 0>(r, r == A ? B : A, tw);
+    for (int i = tid; i < N3; i += NT) {
+        const T k = kh[i];
+        r[i].x *= k;
+        r[i].y *= k;
+    }
+    __syncthreads();
+    r = fft3_axis<C, N, true, 0>(r, r == A ? B : A, tw);
+    r = fft3_axis<C, N, true, 1>(r, r == A ? B : A, tw);
+    r = fft3_axis<C, N, true, 2>(r, r == A ? B : A, tw);
+    return r;
+}
+
+template <typename T, bool KAHAN, int N>
+__device__ void rows3d_item(const PlanDev& P, const int lb, const int le, const bool do_loss,
+                            const T* __restrict__ fcell, T* __restrict__ g, typename Cplx<T>::type* A,
+                            typename Cplx<T>::type* B, T* __restrict__ comp, T* __restrict__ dst) {
+    constexpr int N2 = N * N, N3 = N2 * N, M = N - 1, SA = rows_sa<N>(), NU = (N / 8) * N2;
+    const int NT = blockDim.x, tid = threadIdx.x;
+
+    // the loss, - f (K * f), or zero starts the sum
+    if (do_loss) {
+        const auto* conv = loss_conv<T, N>(P, fcell, A, B);
+        for (int i = tid; i < N3; i += NT) dst[i] = -fcell[i] * conv[i].x;
+    } else {
+        for (int i = tid; i < N3; i += NT) dst[i] = T(0);
+    }
+    if (KAHAN)
+        for (int i = tid; i < N3; i += NT) comp[i] = T(0);
+    __syncthreads();
+
+    for (int k = 0; k < P.n_rclass; ++k) {
+        const int* cd = P.rclass + k * QDVM_RCLASS_INTS;
+        const int ls = max(__ldg(cd + 18), lb), lend = min(__ldg(cd + 19), le);
+        if (ls >= lend) continue;
+        int Mm[9], Mi[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            Mm[t] = __ldg(cd + t);
+            Mi[t] = __ldg(cd + 9 + t);
+        }
+        // re-index the cell: q = M^-1 p (mod N); neighbouring p (last axis)
+        // map to neighbouring gamma when w3 is the last axis
+        for (int p = tid; p < N3; p += NT) {
+            const int p0 = p / N2, p1 = (p / N) & M, p2 = p & M;
+            const int al = (Mi[0] * p0 + Mi[1] * p1 + Mi[2] * p2) & M;
+            const int be = (Mi[3] * p0 + Mi[4] * p1 + Mi[5] * p2) & M;
+            const int ga = (Mi[6] * p0 + Mi[7] * p1 + Mi[8] * p2) & M;
+            const T v = fcell[p];
+            T* d = g + (be * N + ga) * SA + al;
+            d[0] = v;
+            if (al < SA - N) d[N] = v;
+        }
+        __syncthreads();
+        for (int u = tid; u < NU; u += NT) {
+            const int ga = u & M, be = (u / N) & M, a0 = (u / N2) * 8;
+            T acc[8], cmp[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) acc[t] = cmp[t] = T(0);
+            for (int li = ls; li < lend; ++li) {
+                const int4 e = __ldg(P.rline + li);
+                const T c = (T)__ldg(P.rc + li);
+                const int rs = __ldg(P.rrow_start + li), re = __ldg(P.rrow_start + li + 1);
+                T Pv[8], W[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) Pv[t] = W[t] = T(0);
+                for (int r = rs; r < re; ++r) {
+                    const uchar4 w = __ldg(P.rrow + r);
+                    const T* b = g + (((be + w.y) & M) * N + ((ga + w.z) & M)) * SA + ((a0 + w.x) & M);
+                    row_dispatch(w.w, b, Pv);
+                }
+                for (int j = 1; j <= e.w; ++j) {
+                    const T* bp = g + (((be + j * e.y) & M) * N + ((ga + j * e.z) & M)) * SA + ((a0 + j * e.x) & M);
+                    const T* bm = g + (((be - j * e.y) & M) * N + ((ga - j * e.z) & M)) * SA + ((a0 - j * e.x) & M);
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) W[t] += bp[t] + bm[t];
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t) comp_add<T, KAHAN>(acc[t], cmp[t], c * W[t] * Pv[t]);
+            }
+            // add the class sums at the points' cell indices p = M q (mod N)
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int al = a0 + t;
+                const int o0 = (Mm[0] * al + Mm[1] * be + Mm[2] * ga) & M;
+                const int o1 = (Mm[3] * al + Mm[4] * be + Mm[5] * ga) & M;
+                const int o2 = (Mm[6] * al + Mm[7] * be + Mm[8] * ga) & M;
+                const int o = o0 * N2 + o1 * N + o2;
+                if (KAHAN) {
+                    T s = dst[o], cc = comp[o];
+                    comp_add<T, true>(s, cc, acc[t] + cmp[t]);
+                    dst[o] = s;
+                    comp[o] = cc;
+                } else {
+                    dst[o] += acc[t];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (KAHAN) {
+        for (int i = tid; i < N3; i += NT) dst[i] = dst[i] + comp[i];
+    }
+}
+
+template <typename T, bool KAHAN, int N>
+__global__ void __launch_bounds__(kThreadsF3) k_rows3d(BatchDev Bt, int n_cells, int Cn, const int* __restrict__ cell_plan,
+                                                       const int64_t* __restrict__ cell_offset,
+                                                       const int* __restrict__ order, int* counter,
+                                                       const T* __restrict__ f, T* __restrict__ out,
+                                                       T* __restrict__ part, size_t part_stride, char* scratch,
+                                                       size_t scr_stride) {
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item, s_cell;
+    __shared__ PlanDev s_plan;
+    const int n_items = n_cells * Cn;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int it = atomicAdd(counter, 1);
+            int cell = -1;
+            if (it < n_items) cell = order[it / Cn];
+            s_item = cell >= 0 ? it : -1;
+            s_cell = cell;
+            if (cell >= 0) {
+                const int pi = cell_plan[cell];
+#pragma unroll
+                for (int q = 0; q < QDVM_MAX_BATCH_PLANS; ++q)
+                    if (q == pi) s_plan = Bt.p[q];
+            }
+        }
+        __syncthreads();
+        const int item = s_item, cell = s_cell;
+        if (item < 0) break;
+        const PlanDev P = s_plan;
+        const int chunk = item % Cn;
+        const int lpc = (P.n_lines + Cn - 1) / Cn;
+        const int lb = min(chunk * lpc, P.n_lines), le = min(lb + lpc, P.n_lines);
+        const int64_t off = cell_offset[cell];
+        T* dst = Cn == 1 ? out + off : part + ((size_t)cell * Cn + chunk) * part_stride;
+        C* A = reinterpret_cast<C*>(scratch + (size_t)blockIdx.x * scr_stride);
+        C* B = A + N * N * N;
+        T* comp = reinterpret_cast<T*>(B + N * N * N);
+        rows3d_item<T, KAHAN, N>(P, lb, le, chunk == 0, f + off, reinterpret_cast<T*>(smem_raw), A, B, comp, dst);
+        __syncthreads();
+    }
+}
+
 __global__ void k_fast3d_single_init(int* counter, int* order, int* cell_plan, int64_t* cell_offset) {
     *counter = 0;
     *order = 0;
@@ -204,53 +424,69 @@ size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct F3Layout {
     int N, C, grid;
+    bool rows;
     size_t smem, scr_stride, part_stride, off_scr, off_part, total;
 };
 
-template <typename T, bool KAHAN, int N>
+template <typename T, bool KAHAN, int N, bool ROWS>
 int f3_occupancy(size_t smem) {
-    auto k = k_fast3d<T, KAHAN, N>;
+    auto k = ROWS ? k_rows3d<T, KAHAN, N> : k_fast3d<T, KAHAN, N>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kThreadsF3, smem);
     return per > 0 ? per : 1;
 }
 
-int f3_occ(int N, int prec, size_t smem) {
-    if (prec == QDVM_F64) return N == 32 ? f3_occupancy<double, false, 32>(smem) : f3_occupancy<double, false, 16>(smem);
-    if (prec == QDVM_F32_KAHAN) return N == 32 ? f3_occupancy<float, true, 32>(smem) : f3_occupancy<float, true, 16>(smem);
-    return N == 32 ? f3_occupancy<float, false, 32>(smem) : f3_occupancy<float, false, 16>(smem);
+template <bool ROWS>
+int f3_occ_r(int N, int prec, size_t smem) {
+    if (prec == QDVM_F64)
+        return N == 32 ? f3_occupancy<double, false, 32, ROWS>(smem) : f3_occupancy<double, false, 16, ROWS>(smem);
+    if (prec == QDVM_F32_KAHAN)
+        return N == 32 ? f3_occupancy<float, true, 32, ROWS>(smem) : f3_occupancy<float, true, 16, ROWS>(smem);
+    return N == 32 ? f3_occupancy<float, false, 32, ROWS>(smem) : f3_occupancy<float, false, 16, ROWS>(smem);
+}
+
+int f3_occ(int N, int prec, size_t smem, bool rows) {
+    return rows ? f3_occ_r<true>(N, prec, smem) : f3_occ_r<false>(N, prec, smem);
 }
 
 // 0 unless every plan is 3D with the same N in {16, 32}, has the loss
-// transform, and the haloed cell fits in shared memory.
-int f3_size(const BatchDev& b, int prec, size_t* smem) {
+// transform, and the re-indexed cell (row form, when every plan has row
+// tables) or the haloed cell (point-by-point plane sums) fits in shared
+// memory.
+int f3_size(const BatchDev& b, int prec, size_t* smem, bool* rows) {
     const size_t es = prec == QDVM_F64 ? sizeof(double) : sizeof(float);
     const int N = b.p[0].N;
     int H = 0;
+    bool r = true;
     if (N != 16 && N != 32) return 0;
     for (int i = 0; i < b.n_plans; ++i) {
         const PlanDev& p = b.p[i];
         if (p.d != 3 || p.N != N || !p.khat || !p.khat_f || !p.tw || !p.tw_f) return 0;
         H = std::max(H, p.Ntilde);
+        r = r && p.n_rclass > 0;
     }
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t s = (size_t)(N + 2 * H) * N * N * es;
+    const size_t sa = (size_t)(N == 32 ? rows_sa<32>() : rows_sa<16>());
+    const size_t s_rows = (size_t)N * N * sa * es, s_dir = (size_t)(N + 2 * H) * N * N * es;
+    r = r && s_rows + 1024 <= (size_t)optin;
+    const size_t s = r ? s_rows : s_dir;
     if (s + 1024 > (size_t)optin) return 0;
     if (smem) *smem = s;
+    if (rows) *rows = r;
     return N;
 }
 
 F3Layout f3_layout(const BatchDev& b, int n_cells, int prec, bool single, int chunks) {
     F3Layout g{};
-    g.N = f3_size(b, prec, &g.smem);
+    g.N = f3_size(b, prec, &g.smem, &g.rows);
     const size_t es = prec == QDVM_F64 ? sizeof(double) : sizeof(float);
     const size_t n3 = (size_t)g.N * g.N * g.N;
     int maxLines = 1;
     for (int i = 0; i < b.n_plans; ++i) maxLines = std::max(maxLines, b.p[i].n_lines);
-    const int slots = f3_occ(g.N, prec, g.smem) * qdvm_num_sms();
+    const int slots = g.N ? f3_occ(g.N, prec, g.smem, g.rows) * qdvm_num_sms() : 1;
     const int nc = std::max(n_cells, 1);
     if (single)
         g.C = std::max(1, std::min(maxLines, slots));
@@ -259,7 +495,7 @@ F3Layout f3_layout(const BatchDev& b, int n_cells, int prec, bool single, int ch
     if (!single && nc >= 2 * slots) g.C = 1;
     if (chunks > 0) g.C = std::max(1, std::min(maxLines, chunks));
     g.grid = (int)std::max(1L, std::min((long)nc * g.C, (long)slots));
-    g.scr_stride = a256(2 * n3 * 2 * es);  // two complex N^3 FFT buffers
+    g.scr_stride = a256(2 * n3 * 2 * es + (g.rows ? n3 * es : 0));  // two complex N^3 FFT buffers (+ compensation)
     g.part_stride = g.C > 1 ? n3 : 0;
     g.off_scr = 256 + a256((size_t)nc * sizeof(int)) + 256;  // counter, order, single-cell tables
     g.off_part = g.off_scr + (size_t)g.grid * g.scr_stride;
@@ -270,7 +506,7 @@ F3Layout f3_layout(const BatchDev& b, int n_cells, int prec, bool single, int ch
 template <typename T, bool KAHAN, int N>
 void f3_launch(const F3Layout& g, const BatchDev& b, int n_cells, const int* cp, const int64_t* co, const int* order,
                int* counter, const void* f, void* out, char* base, cudaStream_t st) {
-    auto k = k_fast3d<T, KAHAN, N>;
+    auto k = g.rows ? k_rows3d<T, KAHAN, N> : k_fast3d<T, KAHAN, N>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
     k<<<g.grid, kThreadsF3, g.smem, st>>>(b, n_cells, g.C, cp, co, order, counter, static_cast<const T*>(f),
                                            static_cast<T*>(out), reinterpret_cast<T*>(base + g.off_part),
@@ -298,7 +534,7 @@ void f3_reduce(const F3Layout& g, const BatchDev& b, int n_cells, const int* cp,
 qdvm_status moments_batched_launch(const BatchDev& b, int n_cells, const int* cell_plan, const int64_t* cell_offset,
                                    const void* Q, int prec, double* m, cudaStream_t st);
 
-bool fast3d_supported(const BatchDev& b, int prec) { return f3_size(b, prec, nullptr) != 0; }
+bool fast3d_supported(const BatchDev& b, int prec) { return f3_size(b, prec, nullptr, nullptr) != 0; }
 
 size_t fast3d_workspace(const BatchDev& b, int n_cells, int prec, bool single, int chunks) {
     return f3_layout(b, single ? 1 : n_cells, prec, single, chunks).total;

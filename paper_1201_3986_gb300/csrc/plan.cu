@@ -360,6 +360,11 @@ static void plan_free(qdvm_plan_s* p) {
     cudaFree(p->d_khat_f);
     cudaFree(p->d_tw);
     cudaFree(p->d_tw_f);
+    cudaFree(p->d_rclass);
+    cudaFree(p->d_rline);
+    cudaFree(p->d_rc);
+    cudaFree(p->d_rrow_start);
+    cudaFree(p->d_rrow);
     p->magic = 0;
     delete p;
 }
@@ -457,6 +462,8 @@ static qdvm_status build_tables(qdvm_plan_s* p) {
                                                    p->d_khat, p->d_khat_f);
         k_twiddles<<<(N + 63) / 64, 64>>>(N, p->d_tw, p->d_tw_f);
         if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(qdvm_cuda_status(e, "3D loss kernel tables"));
+        const qdvm_status rs = build_row_tables(p);
+        if (rs != QDVM_OK) return fail(rs);
     }
     if (d == 2 && p->N <= 64) {
         const int N = p->N, n2 = N * N;
@@ -542,6 +549,13 @@ extern "C" qdvm_status qdvm_plan_info(qdvm_plan_t p, int* d, int* N, int* Ntilde
     if (m) *m = p->m;
     if (n_lines) *n_lines = p->n_lines;
     if (n_terms) *n_terms = p->n_terms;
+    return QDVM_OK;
+}
+
+extern "C" qdvm_status qdvm_plan_row_info(qdvm_plan_t p, int* n_classes, int* n_rows) {
+    if (!qdvm_plan_ok(p)) return qdvm_fail(QDVM_ERR_BAD_PLAN, "bad plan handle");
+    if (n_classes) *n_classes = p->n_rclass;
+    if (n_rows) *n_rows = p->n_rclass ? p->n_rrow : 0;
     return QDVM_OK;
 }
 

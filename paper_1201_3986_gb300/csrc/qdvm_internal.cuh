@@ -10,6 +10,8 @@
 #include "qdvm.h"
 
 #define QDVM_PLAN_MAGIC 0x51445650u  // "QDVP"
+#define QDVM_RCLASS_INTS 20           // ints per row class: M, M^-1, first line, end line
+#define QDVM_ROW_MAX 15               // longest polygon row (2 Ntilde + 1 with Ntilde <= 7)
 
 // Plan object behind the opaque qdvm_plan_t.
 struct qdvm_plan_s {
@@ -38,6 +40,16 @@ struct qdvm_plan_s {
     float* d_khat_f;
     double2* d_tw;
     float2* d_tw_f;
+    // 3D, N in {16, 32}, Ntilde <= 7: the plane polygons as rows along an
+    // in-plane lattice vector u, lines grouped into classes of a common u
+    // (plan_rows.cu).  Lines are listed class by class.
+    int n_rclass;          // 0: no row tables
+    int n_rrow;
+    int* d_rclass;         // per class: M (3x3, columns u, w2, w3), M^-1, first and end line
+    int4* d_rline;         // per line: e in class coordinates (mod N), J
+    double* d_rc;          // c_e
+    int* d_rrow_start;     // n_lines + 1 offsets into d_rrow
+    uchar4* d_rrow;        // per row: start (alpha, beta, gamma) mod N, length
     // host copies
     std::vector<int4> h_lines;
     std::vector<double> h_c;
@@ -58,6 +70,12 @@ struct PlanDev {
     const float* khat_f;
     const double2* tw;
     const float2* tw_f;
+    int n_rclass;
+    const int* rclass;
+    const int4* rline;
+    const double* rc;
+    const int* rrow_start;
+    const uchar4* rrow;
 };
 
 struct BatchDev {
@@ -84,6 +102,12 @@ inline PlanDev plan_dev(const qdvm_plan_s* p) {
     v.khat_f = p->d_khat_f;
     v.tw = p->d_tw;
     v.tw_f = p->d_tw_f;
+    v.n_rclass = p->n_rclass;
+    v.rclass = p->d_rclass;
+    v.rline = p->d_rline;
+    v.rc = p->d_rc;
+    v.rrow_start = p->d_rrow_start;
+    v.rrow = p->d_rrow;
     return v;
 }
 
@@ -163,6 +187,7 @@ qdvm_status engine_run(int mode, const BatchDev& b, int n_cells, const int* cell
 // Forward 3D batches whose plans share N in {16, 32}: the loss as one FFT
 // convolution per cell, the gain per line with register accumulation.
 bool fast3d_supported(const BatchDev& b, int prec);
+qdvm_status build_row_tables(qdvm_plan_s* p);
 size_t fast3d_workspace(const BatchDev& b, int n_cells, int prec, bool single, int chunks);
 qdvm_status fast3d_run(const BatchDev& b, int n_cells, const int* cell_plan, const int64_t* cell_offset, const void* f,
                        void* out, double* moments, int prec, void* ws, size_t ws_bytes, bool single, int chunks,

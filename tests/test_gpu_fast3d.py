@@ -159,3 +159,40 @@ def test_autotuner_considers_fft_loss_and_graph_replay(q, torch):
     for c in (0, 39):
         r = oracle.q(b.cell(c, fin), 6.0, 3, kernel="hp")
         assert oracle.rel_linf(b.cell(c, Qn), r["Q"], r["scale"]) <= 1e-5
+
+
+@pytest.mark.parametrize("N,Nbar,Nt", [(16, 3, None), (16, 7, 7), (32, 3, None), (32, 5, None), (32, 7, None)])
+def test_row_tables_present(q, N, Nbar, Nt):
+    """3D plans with N in {16, 32} and Ntilde <= 7 carry the row form of the
+    plane polygons; the rows cover every polygon point (sum of row lengths =
+    sum of plane sizes is checked through parity elsewhere)."""
+    p = q.Plan(3, N, Nbar, 6.0, kernel="hp", Ntilde=Nt)
+    nc, nr = p.row_info()
+    assert 1 <= nc <= p.n_lines and nr >= p.n_lines
+    assert q.Plan(2, 32, 8, 6.0).row_info() == (0, 0)
+    assert q.Plan(3, 12, 2, 6.0).row_info() == (0, 0)
+    assert q.Plan(3, 32, 3, 6.0, Ntilde=9).row_info() == (0, 0)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f32_kahan"])
+def test_point_sum_form_N32_wide_truncation(q, torch, prec):
+    """Ntilde = 9 > 7 has no row tables: the FFT-loss evaluator sums the plane
+    polygons point by point."""
+    f = synth.trimaxwellian_3d(32, 6.0).astype(np.float32).astype(np.float64)
+    plan = q.Plan(3, 32, 3, 6.0, kernel="hp", Ntilde=9)
+    plan.set_tuning(loss_fft=1)
+    Q = q.qdvm_eval(plan, torch.tensor(f, dtype=torch.float32, device="cuda"), prec).cpu().numpy()
+    idx = _sample_idx(32, 64, 7)
+    r = oracle.q_points(f, 6.0, 3, idx, kernel="hp", Ntilde=9)
+    assert np.max(np.abs(Q.astype(np.float64).ravel()[idx] - r["Q"])) / np.max(r["scale"]) <= 1e-5
+
+
+def test_integer_data_row_form_close(q, torch):
+    """Integer data: the gain sums are exact integers in the row form, the FFT
+    loss is within rounding of the integer loss."""
+    f = synth.integer_field(3, 16, maxval=2, seed=3)
+    plan = q.Plan(3, 16, 3, 4.0, kernel="unit")
+    plan.set_tuning(loss_fft=1)
+    Q = q.qdvm_eval(plan, torch.tensor(f, dtype=torch.float64, device="cuda"), "f64").cpu().numpy()
+    r = oracle.q(f, 4.0, 3)
+    assert np.max(np.abs(Q - r["Q"])) <= 1e-9 * np.max(r["scale"])
