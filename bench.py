@@ -445,7 +445,7 @@ def run_gpu_workload(args):
         check = lambda: (f_np, outs[0], None)
     else:
         nb = 5
-        b = synth.batch_3d(256, N=32, L=6.0, seed=1)
+        b = synth.batch_3d(args.cells, N=32, L=6.0, seed=1)
         a_np = synth.gaussian(b.f.shape, seed=2)
         plan = q.Plan(3, 32, nb, 6.0, kernel="hp")
         cp = torch.zeros(b.n_cells, dtype=torch.int32, device=dev)
@@ -460,8 +460,14 @@ def run_gpu_workload(args):
             plan.set_tuning(loss_fft=fft)
             wsb.append(q.batched_workspace_bytes([plan], b.n_cells, "f32"))
         ws = torch.empty(2 * max(wsb), dtype=torch.uint8, device=dev)
+        plan.set_tuning(loss_fft=args.loss_fft)
         if wl == "batch3d":
-            tuning = q.qdvm_tune_batched([plan], cp, co, fs[0], "f32", workspace=ws)
+            if args.tuning:
+                th, dj, fft, ch = (int(v) for v in args.tuning.split(","))
+                plan.set_tuning(threads=th, direct_j=dj, loss_fft=fft, line_chunks=ch)
+            else:
+                plan.set_tuning(loss_fft=0)
+                q.qdvm_tune_batched([plan], cp, co, fs[0], "f32", workspace=ws)
 
             def step(k):
                 q.qdvm_eval_batched([plan], cp, co, fs[k % rot], "f32", out=outs[k % rot], moments=False,
@@ -473,7 +479,7 @@ def run_gpu_workload(args):
             def step(k):
                 q.qdvm_vjp_batched([plan], cp, co, fs[k % rot], ats[k % rot], "f32", out=outs[k % rot], workspace=ws)
         pts_per_step = b.total
-        cfg = {"workload": f"{wl}: 256 cells of 32^3 on [-6,6]^3, Nbar=5 (577 lines), hard spheres, two-Maxwellian "
+        cfg = {"workload": f"{wl}: {b.n_cells} cells of 32^3 on [-6,6]^3, Nbar=5 (577 lines), hard spheres, two-Maxwellian "
                            "mixtures (seed 1), Gaussian tangents/cotangents (seed 2), FP32", "Nbar": nb,
                "tuning": plan.tuning()}
         check = lambda: (b.cell(0, b.f.astype(np.float32).astype(np.float64)), outs[0][:32 ** 3].view(32, 32, 32),
@@ -523,11 +529,13 @@ def main():
     ap.add_argument("--ref-cells", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--loss-fft", type=int, default=1, choices=[0, 1],
-                    help="single3d: loss as an FFT convolution (1) or by the line engine (0)")
+                    help="single3d, jvp3d: loss as an FFT convolution with row-form gain (1) or the line engine (0)")
     ap.add_argument("--workload", default="batch2d", choices=["batch2d", "batch3d", "jvp3d", "vjp3d", "single3d"])
     ap.add_argument("--nbar", type=int, default=None)
+    ap.add_argument("--cells", type=int, default=256, help="batch3d / jvp3d / vjp3d: number of 32^3 cells")
     ap.add_argument("--tuning", default=None,
-                    help="threads,direct_j,loss_fft: pin the launch configuration instead of autotuning")
+                    help="pin the launch configuration instead of autotuning: batch2d threads,direct_j,loss_fft; "
+                         "batch3d threads,direct_j,loss_fft,line_chunks")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -27,8 +27,14 @@ qdvm_status build_batch(const qdvm_plan_t* plans, int n_plans, BatchDev* b, int*
 }
 
 // 3D forward with the loss as an FFT convolution (tuning loss_fft = 1)
-bool use_fast3d(const BatchDev& b, const qdvm_tuning& t, int prec) {
-    return t.loss_fft && b.p[0].d == 3 && fast3d_supported(b, prec);
+bool use_fast3d(int mode, const BatchDev& b, const qdvm_tuning& t, int prec) {
+    return t.loss_fft && b.p[0].d == 3 && fast3d_supported(mode, b, prec);
+}
+
+// workspace of one mode: the 3D FFT-loss evaluator or the line engine
+size_t mode_workspace(int mode, const BatchDev& b, int n_cells, int prec, bool single, const qdvm_tuning& t) {
+    return use_fast3d(mode, b, t, prec) ? fast3d_workspace(mode, b, n_cells, prec, single, t.line_chunks)
+                                        : engine_workspace(mode, b, n_cells, prec, single, t.line_chunks);
 }
 
 }  // namespace
@@ -45,15 +51,13 @@ extern "C" qdvm_status qdvm_eval_workspace(qdvm_plan_t p, int prec, size_t* byte
     if (!qdvm_plan_ok(p)) return qdvm_fail(QDVM_ERR_BAD_PLAN, "bad plan handle");
     if (!prec_ok(prec) || !bytes) return qdvm_fail(QDVM_ERR_INVALID_ARG, "bad precision or NULL bytes");
     const BatchDev b = single_batch(p);
-    const size_t der = std::max(engine_workspace(QDVM_MODE_JVP, b, 1, prec, true, p->tune.line_chunks),
-                                engine_workspace(QDVM_MODE_VJP, b, 1, prec, true, p->tune.line_chunks));
+    const size_t der = std::max(mode_workspace(QDVM_MODE_JVP, b, 1, prec, true, p->tune),
+                                mode_workspace(QDVM_MODE_VJP, b, 1, prec, true, p->tune));
     if (p->d == 2 && fused2d_supported(p->N, p->Ntilde, prec)) {
         *bytes = std::max(fused2d_single_workspace(p, prec), der);
         return QDVM_OK;
     }
-    const size_t fwd = use_fast3d(b, p->tune, prec) ? fast3d_workspace(b, 1, prec, true, p->tune.line_chunks)
-                                                     : engine_workspace(QDVM_MODE_FWD, b, 1, prec, true, p->tune.line_chunks);
-    *bytes = std::max(fwd, der);
+    *bytes = std::max(mode_workspace(QDVM_MODE_FWD, b, 1, prec, true, p->tune), der);
     return QDVM_OK;
 }
 
@@ -66,8 +70,9 @@ extern "C" qdvm_status qdvm_eval(qdvm_plan_t p, const void* f, void* Q, int prec
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (p->d == 2 && fused2d_supported(p->N, p->Ntilde, prec)) return fused2d_eval_single(p, f, Q, prec, ws, ws_bytes, st);
     const BatchDev b = single_batch(p);
-    if (use_fast3d(b, p->tune, prec))
-        return fast3d_run(b, 1, nullptr, nullptr, f, Q, nullptr, prec, ws, ws_bytes, true, p->tune.line_chunks, st);
+    if (use_fast3d(QDVM_MODE_FWD, b, p->tune, prec))
+        return fast3d_run(QDVM_MODE_FWD, b, 1, nullptr, nullptr, f, nullptr, Q, nullptr, prec, ws, ws_bytes, true,
+                          p->tune.line_chunks, st);
     return engine_run(QDVM_MODE_FWD, b, 1, nullptr, nullptr, f, nullptr, Q, nullptr, prec, ws, ws_bytes,
                       true, p->tune.line_chunks, st);
 }
@@ -85,13 +90,11 @@ extern "C" qdvm_status qdvm_batched_workspace(const qdvm_plan_t* plans, int n_pl
     int d = 0;
     qdvm_status s = build_batch(plans, n_plans, &b, &d);
     if (s != QDVM_OK) return s;
-    const size_t der = std::max(engine_workspace(QDVM_MODE_JVP, b, n_cells, prec, false, plans[0]->tune.line_chunks),
-                                engine_workspace(QDVM_MODE_VJP, b, n_cells, prec, false, plans[0]->tune.line_chunks));
-    const int lc = plans[0]->tune.line_chunks;
-    size_t fwd;
-    if (all_fused2d(plans, n_plans, d, prec)) fwd = 256 + round256((size_t)std::max(n_cells, 1) * sizeof(int));
-    else if (use_fast3d(b, plans[0]->tune, prec)) fwd = fast3d_workspace(b, n_cells, prec, false, lc);
-    else fwd = engine_workspace(QDVM_MODE_FWD, b, n_cells, prec, false, lc);
+    const qdvm_tuning& tu = plans[0]->tune;
+    const size_t der = std::max(mode_workspace(QDVM_MODE_JVP, b, n_cells, prec, false, tu),
+                                mode_workspace(QDVM_MODE_VJP, b, n_cells, prec, false, tu));
+    const size_t fwd = all_fused2d(plans, n_plans, d, prec) ? 256 + round256((size_t)std::max(n_cells, 1) * sizeof(int))
+                                                            : mode_workspace(QDVM_MODE_FWD, b, n_cells, prec, false, tu);
     *bytes = std::max(fwd, der);
     return QDVM_OK;
 }
@@ -116,9 +119,9 @@ extern "C" qdvm_status qdvm_eval_batched(const qdvm_plan_t* plans, int n_plans, 
         return fused2d_eval_batched(b, plans[0]->tune, n_cells, cell_plan, cell_offset, f, Q, moments, prec, ws, st);
     }
     // the 3D evaluator and the engine check their own layouts against ws_bytes
-    if (use_fast3d(b, plans[0]->tune, prec))
-        return fast3d_run(b, n_cells, cell_plan, cell_offset, f, Q, moments, prec, ws, ws_bytes, false,
-                          plans[0]->tune.line_chunks, st);
+    if (use_fast3d(QDVM_MODE_FWD, b, plans[0]->tune, prec))
+        return fast3d_run(QDVM_MODE_FWD, b, n_cells, cell_plan, cell_offset, f, nullptr, Q, moments, prec, ws, ws_bytes,
+                          false, plans[0]->tune.line_chunks, st);
     return engine_run(QDVM_MODE_FWD, b, n_cells, cell_plan, cell_offset, f, nullptr, Q, moments, prec, ws, ws_bytes,
                       false, plans[0]->tune.line_chunks, st);
 }
@@ -135,7 +138,11 @@ static qdvm_status derivative_single(int mode, qdvm_plan_t p, const void* f, con
     if (!prec_ok(prec)) return qdvm_fail(QDVM_ERR_INVALID_ARG, "bad precision");
     if (!f || !a || !out) return qdvm_fail(QDVM_ERR_INVALID_ARG, "NULL device array");
     if (out == f || out == a) return qdvm_fail(QDVM_ERR_INVALID_ARG, "the output must not alias an input");
-    return engine_run(mode, single_batch(p), 1, nullptr, nullptr, f, a, out, nullptr, prec, ws, ws_bytes, true,
+    const BatchDev b = single_batch(p);
+    if (use_fast3d(mode, b, p->tune, prec))
+        return fast3d_run(mode, b, 1, nullptr, nullptr, f, a, out, nullptr, prec, ws, ws_bytes, true, p->tune.line_chunks,
+                          static_cast<cudaStream_t>(stream));
+    return engine_run(mode, b, 1, nullptr, nullptr, f, a, out, nullptr, prec, ws, ws_bytes, true,
                       p->tune.line_chunks, static_cast<cudaStream_t>(stream));
 }
 
@@ -151,6 +158,9 @@ static qdvm_status derivative_batched(int mode, const qdvm_plan_t* plans, int n_
     if (n_cells == 0) return QDVM_OK;
     if (!cell_plan || !cell_offset || !f || !a || !out) return qdvm_fail(QDVM_ERR_INVALID_ARG, "NULL device array");
     if (out == f || out == a) return qdvm_fail(QDVM_ERR_INVALID_ARG, "the output must not alias an input");
+    if (use_fast3d(mode, b, plans[0]->tune, prec))
+        return fast3d_run(mode, b, n_cells, cell_plan, cell_offset, f, a, out, nullptr, prec, ws, ws_bytes, false,
+                          plans[0]->tune.line_chunks, static_cast<cudaStream_t>(stream));
     return engine_run(mode, b, n_cells, cell_plan, cell_offset, f, a, out, nullptr, prec, ws, ws_bytes, false,
                       plans[0]->tune.line_chunks, static_cast<cudaStream_t>(stream));
 }
@@ -196,11 +206,11 @@ extern "C" qdvm_status qdvm_tune_batched(const qdvm_plan_t* plans, int n_plans, 
         for (int th : {256, 512}) cand.push_back(qdvm_tuning{th, saved.direct_j, saved.line_chunks, 1});
     } else {
         const qdvm_tuning fft{saved.threads, saved.direct_j, 0, 1};
-        const bool f3 = use_fast3d(b, fft, prec);
+        const bool f3 = use_fast3d(QDVM_MODE_FWD, b, fft, prec);
         for (int c : {0, 1, 2, 3, 4, 6, 8}) {
             if (engine_workspace(QDVM_MODE_FWD, b, n_cells, prec, false, c) <= ws_bytes)
                 cand.push_back(qdvm_tuning{saved.threads, saved.direct_j, c, 0});
-            if (f3 && fast3d_workspace(b, n_cells, prec, false, c) <= ws_bytes)
+            if (f3 && fast3d_workspace(QDVM_MODE_FWD, b, n_cells, prec, false, c) <= ws_bytes)
                 cand.push_back(qdvm_tuning{saved.threads, saved.direct_j, c, 1});
         }
     }

@@ -155,9 +155,9 @@ template <typename T, bool KAHAN, int N>
 __global__ void __launch_bounds__(kThreadsF3) k_fast3d(BatchDev Bt, int n_cells, int Cn, const int* __restrict__ cell_plan,
                                                        const int64_t* __restrict__ cell_offset,
                                                        const int* __restrict__ order, int* counter,
-                                                       const T* __restrict__ f, T* __restrict__ out,
-                                                       T* __restrict__ part, size_t part_stride, char* scratch,
-                                                       size_t scr_stride) {
+                                                       const T* __restrict__ f, const T* __restrict__ /*aux*/,
+                                                       T* __restrict__ out, T* __restrict__ part, size_t part_stride,
+                                                       char* scratch, size_t scr_stride) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item, s_cell;
@@ -206,54 +206,15 @@ __host__ __device__ constexpr int rows_sa() {
     return (N + QDVM_ROW_MAX + 6) | 1;
 }
 
-// P[k] += sum_{t<LEN} b[k + t], k = 0..7, as one run of LEN + 7 loads and a
-// sliding window.
-template <int LEN, typename T>
-__device__ __forceinline__ void row_run(const T* __restrict__ b, T (&P)[8]) {
-    T v[LEN + 7];
-#pragma unroll
-    for (int t = 0; t < LEN + 7; ++t) v[t] = b[t];
-    T s = v[0];
-#pragma unroll
-    for (int t = 1; t < LEN; ++t) s += v[t];
-    P[0] += s;
-#pragma unroll
-    for (int k = 1; k < 8; ++k) {
-        s += v[LEN - 1 + k] - v[k - 1];
-        P[k] += s;
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ void row_dispatch(int len, const T* b, T (&P)[8]) {
-    switch (len) {
-        case 1: row_run<1>(b, P); break;
-        case 2: row_run<2>(b, P); break;
-        case 3: row_run<3>(b, P); break;
-        case 4: row_run<4>(b, P); break;
-        case 5: row_run<5>(b, P); break;
-        case 6: row_run<6>(b, P); break;
-        case 7: row_run<7>(b, P); break;
-        case 8: row_run<8>(b, P); break;
-        case 9: row_run<9>(b, P); break;
-        case 10: row_run<10>(b, P); break;
-        case 11: row_run<11>(b, P); break;
-        case 12: row_run<12>(b, P); break;
-        case 13: row_run<13>(b, P); break;
-        case 14: row_run<14>(b, P); break;
-        default: row_run<15>(b, P); break;
-    }
-}
-
-// conv = K * f for the cell (3D FFT over the CTA's scratch A, B).
+// The loss convolution of one or two real fields at once: with A = x1 + i x2
+// on entry, the FFT times the real Ktilde, transformed back, holds K * x1 in
+// the real and K * x2 in the imaginary part (3D FFT over the CTA's scratch A,
+// B; the caller fills A and synchronises).
 template <typename T, int N>
-__device__ const typename Cplx<T>::type* loss_conv(const PlanDev& P, const T* __restrict__ fcell,
-                                                   typename Cplx<T>::type* A, typename Cplx<T>::type* B) {
+__device__ const typename Cplx<T>::type* loss_conv(const PlanDev& P, typename Cplx<T>::type* A,
+                                                   typename Cplx<T>::type* B) {
     using C = typename Cplx<T>::type;
     constexpr int N3 = N * N * N;
-    const int NT = blockDim.x, tid = threadIdx.x;
-    for (int i = tid; i < N3; i += NT) A[i] = C{fcell[i], T(0)};
-    __syncthreads();
     const C* tw;
     const T* kh;
     if constexpr (sizeof(T) == 8) {
@@ -266,7 +227,7 @@ __device__ const typename Cplx<T>::type* loss_conv(const PlanDev& P, const T* __
     C* r = fft3_axis<C, N, false, 2>(A, B, tw);
     r = fft3_axis<C, N, false, 1>(r, r == A ? B : A, tw);
     r = fft3_axis<C, N, false, 0>(r, r == A ? B : A, tw);
-    for (int i = tid; i < N3; i += NT) {
+    for (int i = threadIdx.x; i < N3; i += blockDim.x) {
         const T k = kh[i];
         r[i].x *= k;
         r[i].y *= k;
@@ -278,17 +239,192 @@ __device__ const typename Cplx<T>::type* loss_conv(const PlanDev& P, const T* __
     return r;
 }
 
-template <typename T, bool KAHAN, int N>
+// Window stride of the global class-coordinate copy: alpha runs of 8 from
+// any alpha < N.
+template <int N>
+__host__ __device__ constexpr int rows_sw() {
+    return N + 7;
+}
+
+// The cell src in class coordinates q = M^-1 p (mod N), in shared memory:
+// g[(beta N + gamma) SA + alpha].  Neighbouring p (last axis) map to
+// neighbouring gamma when w3 is the last axis.
+template <typename T, int N>
+__device__ __forceinline__ void relayout_smem(const int (&Mi)[9], const T* __restrict__ src, T* __restrict__ g) {
+    constexpr int N2 = N * N, N3 = N2 * N, M = N - 1, SA = rows_sa<N>();
+    for (int p = threadIdx.x; p < N3; p += blockDim.x) {
+        const int p0 = p / N2, p1 = (p / N) & M, p2 = p & M;
+        const int al = (Mi[0] * p0 + Mi[1] * p1 + Mi[2] * p2) & M;
+        const int be = (Mi[3] * p0 + Mi[4] * p1 + Mi[5] * p2) & M;
+        const int ga = (Mi[6] * p0 + Mi[7] * p1 + Mi[8] * p2) & M;
+        const T v = src[p];
+        T* d = g + (be * N + ga) * SA + al;
+        d[0] = v;
+        if (al < SA - N) d[N] = v;
+    }
+}
+
+// The same in the CTA's global scratch for line-window taps, gamma fastest
+// (a warp's 32 gammas share cache lines): gw[(beta SW + alpha) N + gamma],
+// alpha < 7 repeated after N - 1.  Read back with plain loads after a CTA
+// barrier.
+template <typename T, int N>
+__device__ __forceinline__ void relayout_glob(const int (&Mi)[9], const T* __restrict__ src, T* gw) {
+    constexpr int N2 = N * N, N3 = N2 * N, M = N - 1, SW = rows_sw<N>();
+    for (int p = threadIdx.x; p < N3; p += blockDim.x) {
+        const int p0 = p / N2, p1 = (p / N) & M, p2 = p & M;
+        const int al = (Mi[0] * p0 + Mi[1] * p1 + Mi[2] * p2) & M;
+        const int be = (Mi[3] * p0 + Mi[4] * p1 + Mi[5] * p2) & M;
+        const int ga = (Mi[6] * p0 + Mi[7] * p1 + Mi[8] * p2) & M;
+        const T v = src[p];
+        T* d = gw + (be * SW + al) * N + ga;
+        d[0] = v;
+        if (al < SW - N) d[N2] = v;
+    }
+}
+
+// Pairwise sum of v[LO, HI).
+template <int LO, int HI, typename T, int K>
+__device__ __forceinline__ T tree_sum(const T (&v)[K]) {
+    if constexpr (HI - LO == 1) return v[LO];
+    else return tree_sum<LO, (LO + HI) / 2>(v) + tree_sum<(LO + HI) / 2, HI>(v);
+}
+
+// One row of length LEN for the 8 points a0 .. a0 + 7: LEN + 7 loads; the
+// first window is added to P0 and the window increments to D (the window at
+// point k is P0 + D[0] + ... + D[k-1]).
+template <int LEN, typename T>
+__device__ __forceinline__ void row_run(const T* __restrict__ b, T& P0, T (&D)[7]) {
+    T v[LEN + 7];
+#pragma unroll
+    for (int t = 0; t < LEN + 7; ++t) v[t] = b[t];
+    P0 += tree_sum<0, LEN>(v);
+#pragma unroll
+    for (int k = 1; k < 8; ++k) D[k - 1] += v[LEN - 1 + k] - v[k - 1];
+}
+
+template <typename T>
+__device__ __forceinline__ void row_dispatch(int len, const T* b, T& P0, T (&D)[7]) {
+    switch (len) {
+        case 1: row_run<1>(b, P0, D); break;
+        case 2: row_run<2>(b, P0, D); break;
+        case 3: row_run<3>(b, P0, D); break;
+        case 4: row_run<4>(b, P0, D); break;
+        case 5: row_run<5>(b, P0, D); break;
+        case 6: row_run<6>(b, P0, D); break;
+        case 7: row_run<7>(b, P0, D); break;
+        case 8: row_run<8>(b, P0, D); break;
+        case 9: row_run<9>(b, P0, D); break;
+        case 10: row_run<10>(b, P0, D); break;
+        case 11: row_run<11>(b, P0, D); break;
+        case 12: row_run<12>(b, P0, D); break;
+        case 13: row_run<13>(b, P0, D); break;
+        case 14: row_run<14>(b, P0, D); break;
+        default: row_run<15>(b, P0, D); break;
+    }
+}
+
+// Sums over the lines [ls, lend) of one class for the thread's units of 8
+// consecutive alpha points and adds them at the points' cell indices
+// p = M q (mod N).  Plane sums come from the rows of g; line windows from g
+// (WG false) or from the global copy gw (WG true).
+template <typename T, bool KAHAN, int N, bool WG>
+__device__ void class_units(const PlanDev& P, const int (&Mm)[9], int ls, int lend, const T* __restrict__ g,
+                            const T* gw, T* __restrict__ dst, T* __restrict__ comp) {
+    constexpr int N2 = N * N, M = N - 1, SA = rows_sa<N>(), SW = rows_sw<N>(), NU = (N / 8) * N2;
+    for (int u = threadIdx.x; u < NU; u += blockDim.x) {
+        const int ga = u & M, be = (u / N) & M, a0 = (u / N2) * 8;
+        T acc[8], cmp[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) acc[t] = cmp[t] = T(0);
+        int4 e = __ldg(P.rline + ls);
+        double cd = __ldg(P.rc + ls);
+        int rs = __ldg(P.rrow_start + ls);
+        for (int li = ls; li < lend; ++li) {
+            const int re = __ldg(P.rrow_start + li + 1);
+            // next line's descriptor in flight while this line is summed
+            const int ln = min(li + 1, lend - 1);
+            const int4 e_n = __ldg(P.rline + ln);
+            const double c_n = __ldg(P.rc + ln);
+            T P0 = T(0), D[7], W[8];
+#pragma unroll
+            for (int t = 0; t < 7; ++t) D[t] = T(0);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) W[t] = T(0);
+            uchar4 w = __ldg(P.rrow + rs);
+            for (int r = rs; r < re; ++r) {
+                const uchar4 w_n = __ldg(P.rrow + min(r + 1, re - 1));
+                const T* b = g + (((be + w.y) & M) * N + ((ga + w.z) & M)) * SA + ((a0 + w.x) & M);
+                row_dispatch(w.w, b, P0, D);
+                w = w_n;
+            }
+            for (int j = 1; j <= e.w; ++j) {
+                if (WG) {
+                    const T* bp = gw + (((be + j * e.y) & M) * SW + ((a0 + j * e.x) & M)) * N + ((ga + j * e.z) & M);
+                    const T* bm = gw + (((be - j * e.y) & M) * SW + ((a0 - j * e.x) & M)) * N + ((ga - j * e.z) & M);
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) W[t] += bp[t * N] + bm[t * N];
+                } else {
+                    const T* bp = g + (((be + j * e.y) & M) * N + ((ga + j * e.z) & M)) * SA + ((a0 + j * e.x) & M);
+                    const T* bm = g + (((be - j * e.y) & M) * N + ((ga - j * e.z) & M)) * SA + ((a0 - j * e.x) & M);
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) W[t] += bp[t] + bm[t];
+                }
+            }
+            const T c = (T)cd;
+            T Pk = P0;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                if (t > 0) Pk += D[t - 1];
+                comp_add<T, KAHAN>(acc[t], cmp[t], c * W[t] * Pk);
+            }
+            e = e_n;
+            cd = c_n;
+            rs = re;
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int al = a0 + t;
+            const int o0 = (Mm[0] * al + Mm[1] * be + Mm[2] * ga) & M;
+            const int o1 = (Mm[3] * al + Mm[4] * be + Mm[5] * ga) & M;
+            const int o2 = (Mm[6] * al + Mm[7] * be + Mm[8] * ga) & M;
+            const int o = o0 * N2 + o1 * N + o2;
+            if (KAHAN) {
+                T s = dst[o], cc = comp[o];
+                comp_add<T, true>(s, cc, acc[t] + cmp[t]);
+                dst[o] = s;
+                comp[o] = cc;
+            } else {
+                dst[o] += acc[t];
+            }
+        }
+    }
+}
+
+enum { F3_FWD = 0, F3_JVP = 1 };
+
+// One work item: the loss part (first chunk) or zero, then for every class
+// with lines in [lb, le) the class sums.  Forward: sum c W_e(f) P_e(f).
+// JVP with tangent d: loss -d (K * f) - f (K * d), gain
+// sum c [W_e(d) P_e(f) + W_e(f) P_e(d)] as two passes (plane rows of f with
+// windows of d, then rows of d with windows of f).
+template <typename T, bool KAHAN, int N, int MODE>
 __device__ void rows3d_item(const PlanDev& P, const int lb, const int le, const bool do_loss,
-                            const T* __restrict__ fcell, T* __restrict__ g, typename Cplx<T>::type* A,
-                            typename Cplx<T>::type* B, T* __restrict__ comp, T* __restrict__ dst) {
-    constexpr int N2 = N * N, N3 = N2 * N, M = N - 1, SA = rows_sa<N>(), NU = (N / 8) * N2;
+                            const T* __restrict__ fcell, const T* __restrict__ acell, T* __restrict__ g,
+                            typename Cplx<T>::type* A, typename Cplx<T>::type* B, T* __restrict__ comp, T* gw,
+                            T* __restrict__ dst) {
+    using C = typename Cplx<T>::type;
+    constexpr int N3 = N * N * N;
     const int NT = blockDim.x, tid = threadIdx.x;
 
-    // the loss, - f (K * f), or zero starts the sum
     if (do_loss) {
-        const auto* conv = loss_conv<T, N>(P, fcell, A, B);
-        for (int i = tid; i < N3; i += NT) dst[i] = -fcell[i] * conv[i].x;
+        for (int i = tid; i < N3; i += NT) A[i] = C{fcell[i], MODE == F3_JVP ? acell[i] : T(0)};
+        __syncthreads();
+        const C* conv = loss_conv<T, N>(P, A, B);
+        for (int i = tid; i < N3; i += NT) {
+            const C k = conv[i];
+            dst[i] = MODE == F3_JVP ? -acell[i] * k.x - fcell[i] * k.y : -fcell[i] * k.x;
+        }
     } else {
         for (int i = tid; i < N3; i += NT) dst[i] = T(0);
     }
@@ -296,88 +432,41 @@ __device__ void rows3d_item(const PlanDev& P, const int lb, const int le, const 
         for (int i = tid; i < N3; i += NT) comp[i] = T(0);
     __syncthreads();
 
-    for (int k = 0; k < P.n_rclass; ++k) {
-        const int* cd = P.rclass + k * QDVM_RCLASS_INTS;
-        const int ls = max(__ldg(cd + 18), lb), lend = min(__ldg(cd + 19), le);
-        if (ls >= lend) continue;
-        int Mm[9], Mi[9];
+    constexpr int passes = MODE == F3_JVP ? 2 : 1;
+    for (int pass = 0; pass < passes; ++pass) {
+        const T* rsrc = pass ? acell : fcell;
+        const T* wsrc = pass ? fcell : acell;
+        for (int k = 0; k < P.n_rclass; ++k) {
+            const int* cdp = P.rclass + k * QDVM_RCLASS_INTS;
+            const int ls = max(__ldg(cdp + 18), lb), lend = min(__ldg(cdp + 19), le);
+            if (ls >= lend) continue;
+            int Mm[9], Mi[9];
 #pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            Mm[t] = __ldg(cd + t);
-            Mi[t] = __ldg(cd + 9 + t);
-        }
-        // re-index the cell: q = M^-1 p (mod N); neighbouring p (last axis)
-        // map to neighbouring gamma when w3 is the last axis
-        for (int p = tid; p < N3; p += NT) {
-            const int p0 = p / N2, p1 = (p / N) & M, p2 = p & M;
-            const int al = (Mi[0] * p0 + Mi[1] * p1 + Mi[2] * p2) & M;
-            const int be = (Mi[3] * p0 + Mi[4] * p1 + Mi[5] * p2) & M;
-            const int ga = (Mi[6] * p0 + Mi[7] * p1 + Mi[8] * p2) & M;
-            const T v = fcell[p];
-            T* d = g + (be * N + ga) * SA + al;
-            d[0] = v;
-            if (al < SA - N) d[N] = v;
-        }
-        __syncthreads();
-        for (int u = tid; u < NU; u += NT) {
-            const int ga = u & M, be = (u / N) & M, a0 = (u / N2) * 8;
-            T acc[8], cmp[8];
-#pragma unroll
-            for (int t = 0; t < 8; ++t) acc[t] = cmp[t] = T(0);
-            for (int li = ls; li < lend; ++li) {
-                const int4 e = __ldg(P.rline + li);
-                const T c = (T)__ldg(P.rc + li);
-                const int rs = __ldg(P.rrow_start + li), re = __ldg(P.rrow_start + li + 1);
-                T Pv[8], W[8];
-#pragma unroll
-                for (int t = 0; t < 8; ++t) Pv[t] = W[t] = T(0);
-                for (int r = rs; r < re; ++r) {
-                    const uchar4 w = __ldg(P.rrow + r);
-                    const T* b = g + (((be + w.y) & M) * N + ((ga + w.z) & M)) * SA + ((a0 + w.x) & M);
-                    row_dispatch(w.w, b, Pv);
-                }
-                for (int j = 1; j <= e.w; ++j) {
-                    const T* bp = g + (((be + j * e.y) & M) * N + ((ga + j * e.z) & M)) * SA + ((a0 + j * e.x) & M);
-                    const T* bm = g + (((be - j * e.y) & M) * N + ((ga - j * e.z) & M)) * SA + ((a0 - j * e.x) & M);
-#pragma unroll
-                    for (int t = 0; t < 8; ++t) W[t] += bp[t] + bm[t];
-                }
-#pragma unroll
-                for (int t = 0; t < 8; ++t) comp_add<T, KAHAN>(acc[t], cmp[t], c * W[t] * Pv[t]);
+            for (int t = 0; t < 9; ++t) {
+                Mm[t] = __ldg(cdp + t);
+                Mi[t] = __ldg(cdp + 9 + t);
             }
-            // add the class sums at the points' cell indices p = M q (mod N)
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int al = a0 + t;
-                const int o0 = (Mm[0] * al + Mm[1] * be + Mm[2] * ga) & M;
-                const int o1 = (Mm[3] * al + Mm[4] * be + Mm[5] * ga) & M;
-                const int o2 = (Mm[6] * al + Mm[7] * be + Mm[8] * ga) & M;
-                const int o = o0 * N2 + o1 * N + o2;
-                if (KAHAN) {
-                    T s = dst[o], cc = comp[o];
-                    comp_add<T, true>(s, cc, acc[t] + cmp[t]);
-                    dst[o] = s;
-                    comp[o] = cc;
-                } else {
-                    dst[o] += acc[t];
-                }
-            }
+            relayout_smem<T, N>(Mi, rsrc, g);
+            if (MODE == F3_JVP) relayout_glob<T, N>(Mi, wsrc, gw);
+            __syncthreads();
+            class_units<T, KAHAN, N, MODE == F3_JVP>(P, Mm, ls, lend, g, gw, dst, comp);
+            __syncthreads();
         }
-        __syncthreads();
     }
     if (KAHAN) {
         for (int i = tid; i < N3; i += NT) dst[i] = dst[i] + comp[i];
     }
 }
 
-template <typename T, bool KAHAN, int N>
+template <typename T, bool KAHAN, int N, int MODE>
 __global__ void __launch_bounds__(kThreadsF3) k_rows3d(BatchDev Bt, int n_cells, int Cn, const int* __restrict__ cell_plan,
                                                        const int64_t* __restrict__ cell_offset,
                                                        const int* __restrict__ order, int* counter,
-                                                       const T* __restrict__ f, T* __restrict__ out,
-                                                       T* __restrict__ part, size_t part_stride, char* scratch,
-                                                       size_t scr_stride) {
+                                                       const T* __restrict__ f, const T* __restrict__ aux,
+                                                       T* __restrict__ out, T* __restrict__ part, size_t part_stride,
+                                                       char* scratch, size_t scr_stride) {
     using C = typename Cplx<T>::type;
+    constexpr int N3 = N * N * N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item, s_cell;
     __shared__ PlanDev s_plan;
@@ -405,10 +494,14 @@ __global__ void __launch_bounds__(kThreadsF3) k_rows3d(BatchDev Bt, int n_cells,
         const int lb = min(chunk * lpc, P.n_lines), le = min(lb + lpc, P.n_lines);
         const int64_t off = cell_offset[cell];
         T* dst = Cn == 1 ? out + off : part + ((size_t)cell * Cn + chunk) * part_stride;
+        // scratch: FFT buffers A, B (complex N^3 each), compensation (N^3),
+        // window copy (JVP)
         C* A = reinterpret_cast<C*>(scratch + (size_t)blockIdx.x * scr_stride);
-        C* B = A + N * N * N;
-        T* comp = reinterpret_cast<T*>(B + N * N * N);
-        rows3d_item<T, KAHAN, N>(P, lb, le, chunk == 0, f + off, reinterpret_cast<T*>(smem_raw), A, B, comp, dst);
+        C* B = A + N3;
+        T* comp = reinterpret_cast<T*>(B + N3);
+        T* gw = comp + N3;
+        rows3d_item<T, KAHAN, N, MODE>(P, lb, le, chunk == 0, f + off, aux ? aux + off : nullptr,
+                                       reinterpret_cast<T*>(smem_raw), A, B, comp, gw, dst);
         __syncthreads();
     }
 }
@@ -423,38 +516,47 @@ __global__ void k_fast3d_single_init(int* counter, int* order, int* cell_plan, i
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct F3Layout {
-    int N, C, grid;
+    int N, C, grid, mode;
     bool rows;
     size_t smem, scr_stride, part_stride, off_scr, off_part, total;
 };
 
-template <typename T, bool KAHAN, int N, bool ROWS>
-int f3_occupancy(size_t smem) {
-    auto k = ROWS ? k_rows3d<T, KAHAN, N> : k_fast3d<T, KAHAN, N>;
+template <typename T>
+using F3Kernel = void (*)(BatchDev, int, int, const int*, const int64_t*, const int*, int*, const T*, const T*, T*, T*,
+                          size_t, char*, size_t);
+
+// the kernel for a layout: point-by-point plane sums (forward only) or the
+// row form, forward or JVP
+template <typename T, bool KAHAN, int N>
+F3Kernel<T> f3_kernel(bool rows, int mode) {
+    if (!rows) return k_fast3d<T, KAHAN, N>;
+    return mode == F3_JVP ? k_rows3d<T, KAHAN, N, F3_JVP> : k_rows3d<T, KAHAN, N, F3_FWD>;
+}
+
+template <typename T, bool KAHAN>
+F3Kernel<T> f3_kernel_n(int N, bool rows, int mode) {
+    return N == 32 ? f3_kernel<T, KAHAN, 32>(rows, mode) : f3_kernel<T, KAHAN, 16>(rows, mode);
+}
+
+template <typename T>
+int f3_occupancy(F3Kernel<T> k, size_t smem) {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kThreadsF3, smem);
     return per > 0 ? per : 1;
 }
 
-template <bool ROWS>
-int f3_occ_r(int N, int prec, size_t smem) {
-    if (prec == QDVM_F64)
-        return N == 32 ? f3_occupancy<double, false, 32, ROWS>(smem) : f3_occupancy<double, false, 16, ROWS>(smem);
-    if (prec == QDVM_F32_KAHAN)
-        return N == 32 ? f3_occupancy<float, true, 32, ROWS>(smem) : f3_occupancy<float, true, 16, ROWS>(smem);
-    return N == 32 ? f3_occupancy<float, false, 32, ROWS>(smem) : f3_occupancy<float, false, 16, ROWS>(smem);
-}
-
-int f3_occ(int N, int prec, size_t smem, bool rows) {
-    return rows ? f3_occ_r<true>(N, prec, smem) : f3_occ_r<false>(N, prec, smem);
+int f3_occ(int N, int prec, size_t smem, bool rows, int mode) {
+    if (prec == QDVM_F64) return f3_occupancy<double>(f3_kernel_n<double, false>(N, rows, mode), smem);
+    if (prec == QDVM_F32_KAHAN) return f3_occupancy<float>(f3_kernel_n<float, true>(N, rows, mode), smem);
+    return f3_occupancy<float>(f3_kernel_n<float, false>(N, rows, mode), smem);
 }
 
 // 0 unless every plan is 3D with the same N in {16, 32}, has the loss
 // transform, and the re-indexed cell (row form, when every plan has row
-// tables) or the haloed cell (point-by-point plane sums) fits in shared
-// memory.
-int f3_size(const BatchDev& b, int prec, size_t* smem, bool* rows) {
+// tables) or the haloed cell (point-by-point plane sums, forward only) fits
+// in shared memory.
+int f3_size(const BatchDev& b, int prec, int mode, size_t* smem, bool* rows) {
     const size_t es = prec == QDVM_F64 ? sizeof(double) : sizeof(float);
     const int N = b.p[0].N;
     int H = 0;
@@ -472,6 +574,7 @@ int f3_size(const BatchDev& b, int prec, size_t* smem, bool* rows) {
     const size_t sa = (size_t)(N == 32 ? rows_sa<32>() : rows_sa<16>());
     const size_t s_rows = (size_t)N * N * sa * es, s_dir = (size_t)(N + 2 * H) * N * N * es;
     r = r && s_rows + 1024 <= (size_t)optin;
+    if (mode != F3_FWD && !r) return 0;
     const size_t s = r ? s_rows : s_dir;
     if (s + 1024 > (size_t)optin) return 0;
     if (smem) *smem = s;
@@ -479,14 +582,15 @@ int f3_size(const BatchDev& b, int prec, size_t* smem, bool* rows) {
     return N;
 }
 
-F3Layout f3_layout(const BatchDev& b, int n_cells, int prec, bool single, int chunks) {
+F3Layout f3_layout(const BatchDev& b, int mode, int n_cells, int prec, bool single, int chunks) {
     F3Layout g{};
-    g.N = f3_size(b, prec, &g.smem, &g.rows);
+    g.mode = mode;
+    g.N = f3_size(b, prec, mode, &g.smem, &g.rows);
     const size_t es = prec == QDVM_F64 ? sizeof(double) : sizeof(float);
     const size_t n3 = (size_t)g.N * g.N * g.N;
     int maxLines = 1;
     for (int i = 0; i < b.n_plans; ++i) maxLines = std::max(maxLines, b.p[i].n_lines);
-    const int slots = g.N ? f3_occ(g.N, prec, g.smem, g.rows) * qdvm_num_sms() : 1;
+    const int slots = g.N ? f3_occ(g.N, prec, g.smem, g.rows, mode) * qdvm_num_sms() : 1;
     const int nc = std::max(n_cells, 1);
     if (single)
         g.C = std::max(1, std::min(maxLines, slots));
@@ -495,7 +599,10 @@ F3Layout f3_layout(const BatchDev& b, int n_cells, int prec, bool single, int ch
     if (!single && nc >= 2 * slots) g.C = 1;
     if (chunks > 0) g.C = std::max(1, std::min(maxLines, chunks));
     g.grid = (int)std::max(1L, std::min((long)nc * g.C, (long)slots));
-    g.scr_stride = a256(2 * n3 * 2 * es + (g.rows ? n3 * es : 0));  // two complex N^3 FFT buffers (+ compensation)
+    // two complex N^3 FFT buffers, the compensation field (row form) and the
+    // window copy in class coordinates (JVP)
+    const size_t sw = (size_t)g.N * (g.N == 32 ? rows_sw<32>() : rows_sw<16>()) * g.N;
+    g.scr_stride = a256(2 * n3 * 2 * es + (g.rows ? n3 * es : 0) + (mode == F3_JVP ? sw * es : 0));
     g.part_stride = g.C > 1 ? n3 : 0;
     g.off_scr = 256 + a256((size_t)nc * sizeof(int)) + 256;  // counter, order, single-cell tables
     g.off_part = g.off_scr + (size_t)g.grid * g.scr_stride;
@@ -503,21 +610,15 @@ F3Layout f3_layout(const BatchDev& b, int n_cells, int prec, bool single, int ch
     return g;
 }
 
-template <typename T, bool KAHAN, int N>
+template <typename T, bool KAHAN>
 void f3_launch(const F3Layout& g, const BatchDev& b, int n_cells, const int* cp, const int64_t* co, const int* order,
-               int* counter, const void* f, void* out, char* base, cudaStream_t st) {
-    auto k = g.rows ? k_rows3d<T, KAHAN, N> : k_fast3d<T, KAHAN, N>;
+               int* counter, const void* f, const void* aux, void* out, char* base, cudaStream_t st) {
+    const F3Kernel<T> k = f3_kernel_n<T, KAHAN>(g.N, g.rows, g.mode);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
     k<<<g.grid, kThreadsF3, g.smem, st>>>(b, n_cells, g.C, cp, co, order, counter, static_cast<const T*>(f),
-                                           static_cast<T*>(out), reinterpret_cast<T*>(base + g.off_part),
-                                           g.part_stride, base + g.off_scr, g.scr_stride);
-}
-
-template <typename T, bool KAHAN>
-void f3_launch_n(const F3Layout& g, const BatchDev& b, int n_cells, const int* cp, const int64_t* co,
-                 const int* order, int* counter, const void* f, void* out, char* base, cudaStream_t st) {
-    if (g.N == 32) f3_launch<T, KAHAN, 32>(g, b, n_cells, cp, co, order, counter, f, out, base, st);
-    else f3_launch<T, KAHAN, 16>(g, b, n_cells, cp, co, order, counter, f, out, base, st);
+                                           static_cast<const T*>(aux), static_cast<T*>(out),
+                                           reinterpret_cast<T*>(base + g.off_part), g.part_stride, base + g.off_scr,
+                                           g.scr_stride);
 }
 
 template <typename T, bool KAHAN>
@@ -529,22 +630,30 @@ void f3_reduce(const F3Layout& g, const BatchDev& b, int n_cells, const int* cp,
                                                           static_cast<T*>(out));
 }
 
+int f3_mode(int qdvm_mode) { return qdvm_mode == QDVM_MODE_JVP ? F3_JVP : F3_FWD; }
+
 }  // namespace
 
 qdvm_status moments_batched_launch(const BatchDev& b, int n_cells, const int* cell_plan, const int64_t* cell_offset,
                                    const void* Q, int prec, double* m, cudaStream_t st);
 
-bool fast3d_supported(const BatchDev& b, int prec) { return f3_size(b, prec, nullptr, nullptr) != 0; }
-
-size_t fast3d_workspace(const BatchDev& b, int n_cells, int prec, bool single, int chunks) {
-    return f3_layout(b, single ? 1 : n_cells, prec, single, chunks).total;
+bool fast3d_supported(int mode, const BatchDev& b, int prec) {
+    if (mode != QDVM_MODE_FWD && mode != QDVM_MODE_JVP) return false;
+    return f3_size(b, prec, f3_mode(mode), nullptr, nullptr) != 0;
 }
 
-qdvm_status fast3d_run(const BatchDev& b, int n_cells, const int* cell_plan, const int64_t* cell_offset, const void* f,
-                       void* out, double* moments, int prec, void* ws, size_t ws_bytes, bool single, int chunks,
-                       cudaStream_t st) {
+size_t fast3d_workspace(int mode, const BatchDev& b, int n_cells, int prec, bool single, int chunks) {
+    return f3_layout(b, f3_mode(mode), single ? 1 : n_cells, prec, single, chunks).total;
+}
+
+qdvm_status fast3d_run(int mode, const BatchDev& b, int n_cells, const int* cell_plan, const int64_t* cell_offset,
+                       const void* f, const void* aux, void* out, double* moments, int prec, void* ws,
+                       size_t ws_bytes, bool single, int chunks, cudaStream_t st) {
     const int nc = single ? 1 : n_cells;
-    const F3Layout g = f3_layout(b, nc, prec, single, chunks);
+    if (mode != QDVM_MODE_FWD && mode != QDVM_MODE_JVP)
+        return qdvm_fail(QDVM_ERR_UNSUPPORTED, "the 3D FFT-loss evaluator covers the forward map and the JVP");
+    if (mode == QDVM_MODE_JVP && !aux) return qdvm_fail(QDVM_ERR_INVALID_ARG, "JVP without a tangent");
+    const F3Layout g = f3_layout(b, f3_mode(mode), nc, prec, single, chunks);
     if (!g.N) return qdvm_fail(QDVM_ERR_INVALID_ARG, "the 3D FFT-loss evaluator does not support this batch");
     if (!ws || ws_bytes < g.total) return qdvm_fail(QDVM_ERR_INVALID_ARG, "workspace too small for the 3D evaluator");
     char* base = static_cast<char*>(ws);
@@ -562,9 +671,9 @@ qdvm_status fast3d_run(const BatchDev& b, int n_cells, const int* cell_plan, con
         qdvm_status s = schedule_launch(b, nc, cell_plan, order, counter, st);
         if (s != QDVM_OK) return s;
     }
-    if (prec == QDVM_F64) f3_launch_n<double, false>(g, b, nc, cell_plan, cell_offset, order, counter, f, out, base, st);
-    else if (prec == QDVM_F32_KAHAN) f3_launch_n<float, true>(g, b, nc, cell_plan, cell_offset, order, counter, f, out, base, st);
-    else f3_launch_n<float, false>(g, b, nc, cell_plan, cell_offset, order, counter, f, out, base, st);
+    if (prec == QDVM_F64) f3_launch<double, false>(g, b, nc, cell_plan, cell_offset, order, counter, f, aux, out, base, st);
+    else if (prec == QDVM_F32_KAHAN) f3_launch<float, true>(g, b, nc, cell_plan, cell_offset, order, counter, f, aux, out, base, st);
+    else f3_launch<float, false>(g, b, nc, cell_plan, cell_offset, order, counter, f, aux, out, base, st);
     QDVM_LAUNCH_CHECK("3D evaluator launch");
     if (g.C > 1) {
         if (prec == QDVM_F64) f3_reduce<double, false>(g, b, nc, cell_plan, cell_offset, base, out, st);

@@ -184,11 +184,13 @@ qdvm_status engine_run(int mode, const BatchDev& b, int n_cells, const int* cell
                        size_t ws_bytes, bool single, int chunks, cudaStream_t st);
 
 // ------------------------------------------------------------ 3D FFT-loss evaluator
-// Forward 3D batches whose plans share N in {16, 32}: the loss as one FFT
-// convolution per cell, the gain per line with register accumulation.
-bool fast3d_supported(const BatchDev& b, int prec);
+// 3D batches whose plans share N in {16, 32}: the loss as one FFT
+// convolution per cell, the gain per line with register accumulation (row
+// form of the plane sums where the plans carry row tables).  mode: forward
+// or JVP (aux = tangent; row form only).
+bool fast3d_supported(int mode, const BatchDev& b, int prec);
 qdvm_status build_row_tables(qdvm_plan_s* p);
-size_t fast3d_workspace(const BatchDev& b, int n_cells, int prec, bool single, int chunks);
-qdvm_status fast3d_run(const BatchDev& b, int n_cells, const int* cell_plan, const int64_t* cell_offset, const void* f,
-                       void* out, double* moments, int prec, void* ws, size_t ws_bytes, bool single, int chunks,
-                       cudaStream_t st);
+size_t fast3d_workspace(int mode, const BatchDev& b, int n_cells, int prec, bool single, int chunks);
+qdvm_status fast3d_run(int mode, const BatchDev& b, int n_cells, const int* cell_plan, const int64_t* cell_offset,
+                       const void* f, const void* aux, void* out, double* moments, int prec, void* ws,
+                       size_t ws_bytes, bool single, int chunks, cudaStream_t st);

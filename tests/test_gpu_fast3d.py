@@ -196,3 +196,59 @@ def test_integer_data_row_form_close(q, torch):
     Q = q.qdvm_eval(plan, torch.tensor(f, dtype=torch.float64, device="cuda"), "f64").cpu().numpy()
     r = oracle.q(f, 4.0, 3)
     assert np.max(np.abs(Q - r["Q"])) <= 1e-9 * np.max(r["scale"])
+
+
+def _jvp_batch(q, torch, b, a, plan, prec, chunks):
+    plan.set_tuning(loss_fft=1, line_chunks=chunks)
+    cp = torch.zeros(b.n_cells, dtype=torch.int32, device="cuda")
+    co = torch.tensor(b.offsets, dtype=torch.int64, device="cuda")
+    f = torch.tensor(b.f, dtype=_dt(torch, prec), device="cuda")
+    d = torch.tensor(a, dtype=_dt(torch, prec), device="cuda")
+    J = q.qdvm_jvp_batched([plan], cp, co, f, d, prec)
+    return (J.cpu().numpy().astype(np.float64), f.cpu().numpy().astype(np.float64),
+            d.cpu().numpy().astype(np.float64))
+
+
+@pytest.mark.parametrize("chunks", [0, 1, 3])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32_kahan"])
+@pytest.mark.parametrize("kernel", ["unit", "hp"])
+def test_jvp_row_form_N16_every_cell(q, torch, chunks, prec, kernel):
+    """JVP with the loss -d (K * f) - f (K * d) from one complex FFT and the
+    gain in two row-form passes (rows of f with windows of d, then rows of d
+    with windows of f)."""
+    b = synth.batch_3d(3, N=16, L=6.0, seed=30)
+    a = synth.gaussian(b.f.shape, seed=31)
+    J, fin, din = _jvp_batch(q, torch, b, a, q.Plan(3, 16, 3, 6.0, kernel=kernel), prec, chunks)
+    for c in range(b.n_cells):
+        r, sc = oracle.jvp_points(b.cell(c, fin), b.cell(c, din), 6.0, 3, kernel=kernel)
+        assert np.max(np.abs(b.cell(c, J) - r)) / np.max(sc) <= TOL[prec]
+
+
+@pytest.mark.parametrize("Nbar", [3, 5])
+def test_jvp_row_form_N32_sampled(q, torch, Nbar):
+    b = synth.batch_3d(3, N=32, L=6.0, seed=40 + Nbar)
+    a = synth.gaussian(b.f.shape, seed=Nbar)
+    for prec in ("f32", "f32_kahan"):
+        J, fin, din = _jvp_batch(q, torch, b, a, q.Plan(3, 32, Nbar, 6.0, kernel="hp"), prec, 0)
+        for c in range(b.n_cells):
+            idx = _sample_idx(32, 40, c + Nbar)
+            r, sc = oracle.jvp_points(b.cell(c, fin), b.cell(c, din), 6.0, Nbar, idx, kernel="hp")
+            assert np.max(np.abs(b.cell(c, J).ravel()[idx] - r)) / np.max(sc) <= 1e-5
+
+
+def test_jvp_row_form_single_cell_and_transpose(q, torch):
+    """Single-cell JVP through the row form against the oracle, and
+    <g, J d> = <J^T g, d> with the VJP (line engine)."""
+    rs = np.random.default_rng(8)
+    f = synth.mixture(3, 16, 6.0, rs)
+    d = rs.standard_normal((16,) * 3)
+    g = rs.standard_normal((16,) * 3)
+    plan = q.Plan(3, 16, 3, 6.0, kernel="hp")
+    plan.set_tuning(loss_fft=1)
+    tf = lambda x: torch.tensor(x, dtype=torch.float64, device="cuda")
+    J = q.qdvm_jvp(plan, tf(f), tf(d), "f64").cpu().numpy()
+    G = q.qdvm_vjp(plan, tf(f), tf(g), "f64").cpu().numpy()
+    r, sc = oracle.jvp_points(f, d, 6.0, 3, kernel="hp")
+    assert np.max(np.abs(J - r)) / np.max(sc) <= 1e-12
+    lhs, rhs = float(np.sum(g * J)), float(np.sum(G * d))
+    assert abs(lhs - rhs) <= 1e-11 * (np.sum(np.abs(g)) * np.max(sc))
