@@ -196,11 +196,11 @@ __global__ void __launch_bounds__(kThreadsF3) k_fast3d(BatchDev Bt, int n_cells,
 // ---------------------------------------------------------------- row form
 // Gain via the row tables of the plan (plan_rows.cu).  For each line class
 // the cell is re-indexed in the class coordinates q = (alpha, beta, gamma),
-// point = M q mod N, and stored as g[(beta N + gamma) SA + alpha] with the
-// first SA - N alpha values repeated after alpha = N - 1, so that a run of up
-// to QDVM_ROW_MAX + 7 points starting at any alpha < N is contiguous.  SA is
-// odd: the 32 lanes of a warp, which differ in gamma (and, for N = 16, in
-// beta), hit 32 distinct banks.
+// point = M q mod N, and stored as g[(beta N + gamma) SA + a] for every
+// a < SA with a = alpha (mod N), so that a run of up to QDVM_ROW_MAX + 7
+// points starting at any alpha < N is contiguous.  SA is odd: the 32 lanes
+// of a warp, which differ in gamma (and, for N = 16, in beta), hit 32
+// distinct banks.
 template <int N>
 __host__ __device__ constexpr int rows_sa() {
     return (N + QDVM_ROW_MAX + 6) | 1;
@@ -258,9 +258,8 @@ __device__ __forceinline__ void relayout_smem(const int (&Mi)[9], const T* __res
         const int be = (Mi[3] * p0 + Mi[4] * p1 + Mi[5] * p2) & M;
         const int ga = (Mi[6] * p0 + Mi[7] * p1 + Mi[8] * p2) & M;
         const T v = src[p];
-        T* d = g + (be * N + ga) * SA + al;
-        d[0] = v;
-        if (al < SA - N) d[N] = v;
+        T* d = g + (be * N + ga) * SA;
+        for (int a = al; a < SA; a += N) d[a] = v;  // alpha and its repeats below SA
     }
 }
 
@@ -401,7 +400,176 @@ __device__ void class_units(const PlanDev& P, const int (&Mm)[9], int ls, int le
     }
 }
 
-enum { F3_FWD = 0, F3_JVP = 1 };
+// VJP with cotangent gc (the transpose of the JVP; Omega_e and Pi_e are
+// symmetric on the torus): loss part -[g (K * f) + K * (g f)], gain part
+// sum_e c [Omega_e(g P_e(f)) + Pi_e(g W_e(f))].  Both gain terms apply a
+// stencil to a per-line product, so each line materialises its product over
+// the cell.  Pass A: rows of f in shared memory, X = g P_e(f) to the global
+// window copy, then the windows Omega_e(X).  Pass B: windows of f from the
+// global window copy, Y = g W_e(f) into shared memory, then the rows Pi_e(Y).
+// Class sums go to a compact class-coordinate field acc[(beta N + gamma) N +
+// alpha] (8 consecutive alpha per unit: two 16-byte accesses) and are added
+// at the cell indices once per class.
+template <typename T, int N>
+__device__ __forceinline__ void relayout_compact(const int (&Mi)[9], const T* __restrict__ src, T* dstc) {
+    constexpr int N2 = N * N, N3 = N2 * N, M = N - 1;
+    for (int p = threadIdx.x; p < N3; p += blockDim.x) {
+        const int p0 = p / N2, p1 = (p / N) & M, p2 = p & M;
+        const int al = (Mi[0] * p0 + Mi[1] * p1 + Mi[2] * p2) & M;
+        const int be = (Mi[3] * p0 + Mi[4] * p1 + Mi[5] * p2) & M;
+        const int ga = (Mi[6] * p0 + Mi[7] * p1 + Mi[8] * p2) & M;
+        dstc[(be * N + ga) * N + al] = src[p];
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void load8(const T* p, T (&v)[8]) {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v[t] = p[t];
+}
+
+template <typename T, bool KAHAN>
+__device__ __forceinline__ void acc8(T* acc, T* cmp, const T (&x)[8], T c) {
+    T a[8];
+    load8(acc, a);
+    if (KAHAN) {
+        T k[8];
+        load8(cmp, k);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) comp_add<T, true>(a[t], k[t], c * x[t]);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) cmp[t] = k[t];
+    } else {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) a[t] += c * x[t];
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) acc[t] = a[t];
+}
+
+template <typename T, bool KAHAN, int N>
+__device__ void vjp_class(const PlanDev& P, const int (&Mm)[9], const int (&Mi)[9], int ls, int lend,
+                          const T* __restrict__ fcell, const T* __restrict__ gcell, T* __restrict__ g, T* gwf, T* X,
+                          T* gC, T* accC, T* cmpC, T* __restrict__ dst, T* __restrict__ comp) {
+    constexpr int N2 = N * N, N3 = N2 * N, M = N - 1, SA = rows_sa<N>(), SW = rows_sw<N>(), NU = (N / 8) * N2;
+    const int NT = blockDim.x, tid = threadIdx.x;
+    relayout_smem<T, N>(Mi, fcell, g);
+    relayout_glob<T, N>(Mi, fcell, gwf);
+    relayout_compact<T, N>(Mi, gcell, gC);
+    for (int i = tid; i < N3; i += NT) {
+        accC[i] = T(0);
+        if (KAHAN) cmpC[i] = T(0);
+    }
+    __syncthreads();
+    // pass A: X = g P_e(f), then Omega_e(X)
+    for (int li = ls; li < lend; ++li) {
+        const int rs = __ldg(P.rrow_start + li), re = __ldg(P.rrow_start + li + 1);
+        for (int u = tid; u < NU; u += NT) {
+            const int ga = u & M, be = (u / N) & M, a0 = (u / N2) * 8;
+            T P0 = T(0), D[7], gv[8];
+#pragma unroll
+            for (int t = 0; t < 7; ++t) D[t] = T(0);
+            for (int r = rs; r < re; ++r) {
+                const uchar4 w = __ldg(P.rrow + r);
+                const T* b = g + (((be + w.y) & M) * N + ((ga + w.z) & M)) * SA + ((a0 + w.x) & M);
+                row_dispatch(w.w, b, P0, D);
+            }
+            load8(gC + (be * N + ga) * N + a0, gv);
+            T Pk = P0;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                if (t > 0) Pk += D[t - 1];
+                T* xp = X + (be * SW + a0 + t) * N + ga;
+                const T x = gv[t] * Pk;
+                xp[0] = x;
+                if (a0 + t < SW - N) xp[N2] = x;
+            }
+        }
+        __syncthreads();
+        const int4 e = __ldg(P.rline + li);
+        const T c = (T)__ldg(P.rc + li);
+        for (int u = tid; u < NU; u += NT) {
+            const int ga = u & M, be = (u / N) & M, a0 = (u / N2) * 8;
+            T W[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) W[t] = T(0);
+            for (int j = 1; j <= e.w; ++j) {
+                const T* bp = X + (((be + j * e.y) & M) * SW + ((a0 + j * e.x) & M)) * N + ((ga + j * e.z) & M);
+                const T* bm = X + (((be - j * e.y) & M) * SW + ((a0 - j * e.x) & M)) * N + ((ga - j * e.z) & M);
+#pragma unroll
+                for (int t = 0; t < 8; ++t) W[t] += bp[t * N] + bm[t * N];
+            }
+            const int ci = (be * N + ga) * N + a0;
+            acc8<T, KAHAN>(accC + ci, cmpC + ci, W, c);
+        }
+        __syncthreads();
+    }
+    // pass B: Y = g W_e(f) into shared memory, then Pi_e(Y)
+    for (int li = ls; li < lend; ++li) {
+        const int4 e = __ldg(P.rline + li);
+        const T c = (T)__ldg(P.rc + li);
+        for (int u = tid; u < NU; u += NT) {
+            const int ga = u & M, be = (u / N) & M, a0 = (u / N2) * 8;
+            T W[8], gv[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) W[t] = T(0);
+            for (int j = 1; j <= e.w; ++j) {
+                const T* bp = gwf + (((be + j * e.y) & M) * SW + ((a0 + j * e.x) & M)) * N + ((ga + j * e.z) & M);
+                const T* bm = gwf + (((be - j * e.y) & M) * SW + ((a0 - j * e.x) & M)) * N + ((ga - j * e.z) & M);
+#pragma unroll
+                for (int t = 0; t < 8; ++t) W[t] += bp[t * N] + bm[t * N];
+            }
+            load8(gC + (be * N + ga) * N + a0, gv);
+            T* yp = g + (be * N + ga) * SA;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const T y = gv[t] * W[t];
+                for (int a = a0 + t; a < SA; a += N) yp[a] = y;
+            }
+        }
+        __syncthreads();
+        const int rs = __ldg(P.rrow_start + li), re = __ldg(P.rrow_start + li + 1);
+        for (int u = tid; u < NU; u += NT) {
+            const int ga = u & M, be = (u / N) & M, a0 = (u / N2) * 8;
+            T P0 = T(0), D[7], Pv[8];
+#pragma unroll
+            for (int t = 0; t < 7; ++t) D[t] = T(0);
+            for (int r = rs; r < re; ++r) {
+                const uchar4 w = __ldg(P.rrow + r);
+                const T* b = g + (((be + w.y) & M) * N + ((ga + w.z) & M)) * SA + ((a0 + w.x) & M);
+                row_dispatch(w.w, b, P0, D);
+            }
+            Pv[0] = P0;
+#pragma unroll
+            for (int t = 1; t < 8; ++t) Pv[t] = Pv[t - 1] + D[t - 1];
+            const int ci = (be * N + ga) * N + a0;
+            acc8<T, KAHAN>(accC + ci, cmpC + ci, Pv, c);
+        }
+        __syncthreads();
+    }
+    // class sums to the cell indices p = M q (mod N)
+    for (int u = tid; u < NU; u += NT) {
+        const int ga = u & M, be = (u / N) & M, a0 = (u / N2) * 8;
+        const int ci = (be * N + ga) * N + a0;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int al = a0 + t;
+            const int o = ((Mm[0] * al + Mm[1] * be + Mm[2] * ga) & M) * N2 +
+                          ((Mm[3] * al + Mm[4] * be + Mm[5] * ga) & M) * N + ((Mm[6] * al + Mm[7] * be + Mm[8] * ga) & M);
+            if (KAHAN) {
+                T s = dst[o], cc = comp[o];
+                comp_add<T, true>(s, cc, accC[ci + t] + cmpC[ci + t]);
+                dst[o] = s;
+                comp[o] = cc;
+            } else {
+                dst[o] += accC[ci + t];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+enum { F3_FWD = 0, F3_JVP = 1, F3_VJP = 2 };
 
 // One work item: the loss part (first chunk) or zero, then for every class
 // with lines in [lb, le) the class sums.  Forward: sum c W_e(f) P_e(f).
@@ -414,16 +582,22 @@ __device__ void rows3d_item(const PlanDev& P, const int lb, const int le, const 
                             typename Cplx<T>::type* A, typename Cplx<T>::type* B, T* __restrict__ comp, T* gw,
                             T* __restrict__ dst) {
     using C = typename Cplx<T>::type;
-    constexpr int N3 = N * N * N;
+    constexpr int N3 = N * N * N, NW = N * rows_sw<N>() * N;
     const int NT = blockDim.x, tid = threadIdx.x;
 
     if (do_loss) {
-        for (int i = tid; i < N3; i += NT) A[i] = C{fcell[i], MODE == F3_JVP ? acell[i] : T(0)};
+        // forward: K * f; JVP: K * f and K * d; VJP: K * f and K * (g f)
+        for (int i = tid; i < N3; i += NT) {
+            const T im = MODE == F3_JVP ? acell[i] : (MODE == F3_VJP ? acell[i] * fcell[i] : T(0));
+            A[i] = C{fcell[i], im};
+        }
         __syncthreads();
         const C* conv = loss_conv<T, N>(P, A, B);
         for (int i = tid; i < N3; i += NT) {
             const C k = conv[i];
-            dst[i] = MODE == F3_JVP ? -acell[i] * k.x - fcell[i] * k.y : -fcell[i] * k.x;
+            if (MODE == F3_JVP) dst[i] = -acell[i] * k.x - fcell[i] * k.y;
+            else if (MODE == F3_VJP) dst[i] = -(acell[i] * k.x + k.y);
+            else dst[i] = -fcell[i] * k.x;
         }
     } else {
         for (int i = tid; i < N3; i += NT) dst[i] = T(0);
@@ -432,7 +606,27 @@ __device__ void rows3d_item(const PlanDev& P, const int lb, const int le, const 
         for (int i = tid; i < N3; i += NT) comp[i] = T(0);
     __syncthreads();
 
-    constexpr int passes = MODE == F3_JVP ? 2 : 1;
+    if (MODE == F3_VJP) {
+        // scratch after the window copy gw: X (window layout), g, acc and
+        // its compensation in compact class coordinates
+        T* X = gw + NW;
+        T* gC = X + NW;
+        T* accC = gC + N3;
+        T* cmpC = accC + N3;
+        for (int k = 0; k < P.n_rclass; ++k) {
+            const int* cdp = P.rclass + k * QDVM_RCLASS_INTS;
+            const int ls = max(__ldg(cdp + 18), lb), lend = min(__ldg(cdp + 19), le);
+            if (ls >= lend) continue;
+            int Mm[9], Mi[9];
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                Mm[t] = __ldg(cdp + t);
+                Mi[t] = __ldg(cdp + 9 + t);
+            }
+            vjp_class<T, KAHAN, N>(P, Mm, Mi, ls, lend, fcell, acell, g, gw, X, gC, accC, cmpC, dst, comp);
+        }
+    }
+    constexpr int passes = MODE == F3_JVP ? 2 : (MODE == F3_FWD ? 1 : 0);
     for (int pass = 0; pass < passes; ++pass) {
         const T* rsrc = pass ? acell : fcell;
         const T* wsrc = pass ? fcell : acell;
@@ -459,7 +653,7 @@ __device__ void rows3d_item(const PlanDev& P, const int lb, const int le, const 
 }
 
 template <typename T, bool KAHAN, int N, int MODE>
-__global__ void __launch_bounds__(kThreadsF3) k_rows3d(BatchDev Bt, int n_cells, int Cn, const int* __restrict__ cell_plan,
+__global__ void __launch_bounds__(kThreadsF3, 1) k_rows3d(BatchDev Bt, int n_cells, int Cn, const int* __restrict__ cell_plan,
                                                        const int64_t* __restrict__ cell_offset,
                                                        const int* __restrict__ order, int* counter,
                                                        const T* __restrict__ f, const T* __restrict__ aux,
@@ -530,6 +724,7 @@ using F3Kernel = void (*)(BatchDev, int, int, const int*, const int64_t*, const 
 template <typename T, bool KAHAN, int N>
 F3Kernel<T> f3_kernel(bool rows, int mode) {
     if (!rows) return k_fast3d<T, KAHAN, N>;
+    if (mode == F3_VJP) return k_rows3d<T, KAHAN, N, F3_VJP>;
     return mode == F3_JVP ? k_rows3d<T, KAHAN, N, F3_JVP> : k_rows3d<T, KAHAN, N, F3_FWD>;
 }
 
@@ -599,10 +794,14 @@ F3Layout f3_layout(const BatchDev& b, int mode, int n_cells, int prec, bool sing
     if (!single && nc >= 2 * slots) g.C = 1;
     if (chunks > 0) g.C = std::max(1, std::min(maxLines, chunks));
     g.grid = (int)std::max(1L, std::min((long)nc * g.C, (long)slots));
-    // two complex N^3 FFT buffers, the compensation field (row form) and the
-    // window copy in class coordinates (JVP)
+    // two complex N^3 FFT buffers, the compensation field (row form), the
+    // window copy in class coordinates (JVP, VJP) and for the VJP the product
+    // X in window layout plus g, acc, compensation in compact layout
     const size_t sw = (size_t)g.N * (g.N == 32 ? rows_sw<32>() : rows_sw<16>()) * g.N;
-    g.scr_stride = a256(2 * n3 * 2 * es + (g.rows ? n3 * es : 0) + (mode == F3_JVP ? sw * es : 0));
+    size_t fields = 2 * n3 * 2 + (g.rows ? n3 : 0);
+    if (mode == F3_JVP) fields += sw;
+    if (mode == F3_VJP) fields += 2 * sw + 3 * n3;
+    g.scr_stride = a256(fields * es);
     g.part_stride = g.C > 1 ? n3 : 0;
     g.off_scr = 256 + a256((size_t)nc * sizeof(int)) + 256;  // counter, order, single-cell tables
     g.off_part = g.off_scr + (size_t)g.grid * g.scr_stride;
@@ -630,7 +829,9 @@ void f3_reduce(const F3Layout& g, const BatchDev& b, int n_cells, const int* cp,
                                                           static_cast<T*>(out));
 }
 
-int f3_mode(int qdvm_mode) { return qdvm_mode == QDVM_MODE_JVP ? F3_JVP : F3_FWD; }
+int f3_mode(int qdvm_mode) {
+    return qdvm_mode == QDVM_MODE_JVP ? F3_JVP : (qdvm_mode == QDVM_MODE_VJP ? F3_VJP : F3_FWD);
+}
 
 }  // namespace
 
@@ -638,7 +839,7 @@ qdvm_status moments_batched_launch(const BatchDev& b, int n_cells, const int* ce
                                    const void* Q, int prec, double* m, cudaStream_t st);
 
 bool fast3d_supported(int mode, const BatchDev& b, int prec) {
-    if (mode != QDVM_MODE_FWD && mode != QDVM_MODE_JVP) return false;
+    if (mode != QDVM_MODE_FWD && mode != QDVM_MODE_JVP && mode != QDVM_MODE_VJP) return false;
     return f3_size(b, prec, f3_mode(mode), nullptr, nullptr) != 0;
 }
 
@@ -650,9 +851,9 @@ qdvm_status fast3d_run(int mode, const BatchDev& b, int n_cells, const int* cell
                        const void* f, const void* aux, void* out, double* moments, int prec, void* ws,
                        size_t ws_bytes, bool single, int chunks, cudaStream_t st) {
     const int nc = single ? 1 : n_cells;
-    if (mode != QDVM_MODE_FWD && mode != QDVM_MODE_JVP)
-        return qdvm_fail(QDVM_ERR_UNSUPPORTED, "the 3D FFT-loss evaluator covers the forward map and the JVP");
-    if (mode == QDVM_MODE_JVP && !aux) return qdvm_fail(QDVM_ERR_INVALID_ARG, "JVP without a tangent");
+    if (mode != QDVM_MODE_FWD && mode != QDVM_MODE_JVP && mode != QDVM_MODE_VJP)
+        return qdvm_fail(QDVM_ERR_UNSUPPORTED, "unknown mode for the 3D FFT-loss evaluator");
+    if (mode != QDVM_MODE_FWD && !aux) return qdvm_fail(QDVM_ERR_INVALID_ARG, "JVP / VJP without a tangent or cotangent");
     const F3Layout g = f3_layout(b, f3_mode(mode), nc, prec, single, chunks);
     if (!g.N) return qdvm_fail(QDVM_ERR_INVALID_ARG, "the 3D FFT-loss evaluator does not support this batch");
     if (!ws || ws_bytes < g.total) return qdvm_fail(QDVM_ERR_INVALID_ARG, "workspace too small for the 3D evaluator");

@@ -186,8 +186,9 @@ qdvm_status engine_run(int mode, const BatchDev& b, int n_cells, const int* cell
 // ------------------------------------------------------------ 3D FFT-loss evaluator
 // 3D batches whose plans share N in {16, 32}: the loss as one FFT
 // convolution per cell, the gain per line with register accumulation (row
-// form of the plane sums where the plans carry row tables).  mode: forward
-// or JVP (aux = tangent; row form only).
+// form of the plane sums where the plans carry row tables).  mode: forward,
+// JVP (aux = tangent) or VJP (aux = cotangent); the derivatives need the row
+// form.
 bool fast3d_supported(int mode, const BatchDev& b, int prec);
 qdvm_status build_row_tables(qdvm_plan_s* p);
 size_t fast3d_workspace(int mode, const BatchDev& b, int n_cells, int prec, bool single, int chunks);

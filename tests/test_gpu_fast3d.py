@@ -252,3 +252,60 @@ def test_jvp_row_form_single_cell_and_transpose(q, torch):
     assert np.max(np.abs(J - r)) / np.max(sc) <= 1e-12
     lhs, rhs = float(np.sum(g * J)), float(np.sum(G * d))
     assert abs(lhs - rhs) <= 1e-11 * (np.sum(np.abs(g)) * np.max(sc))
+
+
+def _vjp_batch(q, torch, b, a, plan, prec, chunks):
+    plan.set_tuning(loss_fft=1, line_chunks=chunks)
+    cp = torch.zeros(b.n_cells, dtype=torch.int32, device="cuda")
+    co = torch.tensor(b.offsets, dtype=torch.int64, device="cuda")
+    f = torch.tensor(b.f, dtype=_dt(torch, prec), device="cuda")
+    g = torch.tensor(a, dtype=_dt(torch, prec), device="cuda")
+    G = q.qdvm_vjp_batched([plan], cp, co, f, g, prec)
+    return (G.cpu().numpy().astype(np.float64), f.cpu().numpy().astype(np.float64),
+            g.cpu().numpy().astype(np.float64))
+
+
+@pytest.mark.parametrize("chunks", [0, 1, 3])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32_kahan"])
+@pytest.mark.parametrize("kernel", ["unit", "hp"])
+def test_vjp_row_form_N16_every_cell(q, torch, chunks, prec, kernel):
+    """VJP: loss -[g (K * f) + K * (g f)] from one complex FFT; gain
+    Omega_e(g P_e f) + Pi_e(g W_e f) with the per-line products materialised
+    (windows of X = g P in global scratch, rows of Y = g W in shared memory)."""
+    b = synth.batch_3d(3, N=16, L=6.0, seed=50)
+    a = synth.gaussian(b.f.shape, seed=51)
+    G, fin, gin = _vjp_batch(q, torch, b, a, q.Plan(3, 16, 3, 6.0, kernel=kernel), prec, chunks)
+    for c in range(b.n_cells):
+        r, sc = oracle.vjp(b.cell(c, fin), b.cell(c, gin), 6.0, 3, kernel=kernel, with_scale=True)
+        assert np.max(np.abs(b.cell(c, G) - r)) / np.max(sc) <= TOL[prec]
+
+
+@pytest.mark.parametrize("Nbar", [3, 5])
+def test_vjp_row_form_N32_sampled(q, torch, Nbar):
+    b = synth.batch_3d(2, N=32, L=6.0, seed=60 + Nbar)
+    a = synth.gaussian(b.f.shape, seed=Nbar + 1)
+    for prec in ("f32", "f32_kahan"):
+        G, fin, gin = _vjp_batch(q, torch, b, a, q.Plan(3, 32, Nbar, 6.0, kernel="hp"), prec, 0)
+        for c in range(b.n_cells):
+            idx = _sample_idx(32, 32, c + 3 * Nbar)
+            r, sc = oracle.vjp_points(b.cell(c, fin), b.cell(c, gin), 6.0, Nbar, idx, kernel="hp")
+            assert np.max(np.abs(b.cell(c, G).ravel()[idx] - r)) / np.max(sc) <= 1e-5
+
+
+@pytest.mark.parametrize("Nt,Nbar", [(7, 7), (5, 4)])
+def test_jvp_vjp_transpose_row_form_N16(q, torch, Nt, Nbar):
+    """<g, J d> = <J^T g, d> with both derivatives in row form, FP64, long
+    rows (Ntilde = 7 gives rows of 15 points)."""
+    rs = np.random.default_rng(Nt)
+    f = synth.mixture(3, 16, 6.0, rs)
+    d = rs.standard_normal((16,) * 3)
+    g = rs.standard_normal((16,) * 3)
+    plan = q.Plan(3, 16, Nbar, 6.0, kernel="hp", Ntilde=Nt)
+    plan.set_tuning(loss_fft=1)
+    tf = lambda x: torch.tensor(x, dtype=torch.float64, device="cuda")
+    J = q.qdvm_jvp(plan, tf(f), tf(d), "f64").cpu().numpy()
+    G = q.qdvm_vjp(plan, tf(f), tf(g), "f64").cpu().numpy()
+    r, sc = oracle.vjp(f, g, 6.0, Nbar, kernel="hp", Ntilde=Nt, with_scale=True)
+    assert np.max(np.abs(G - r)) / np.max(sc) <= 1e-12
+    lhs, rhs = float(np.sum(g * J)), float(np.sum(G * d))
+    assert abs(lhs - rhs) <= 1e-11 * np.sum(np.abs(g)) * np.max(sc)
