@@ -407,9 +407,9 @@ __device__ void class_units(const PlanDev& P, const int (&Mm)[9], int ls, int le
 // the cell.  Pass A: rows of f in shared memory, X = g P_e(f) to the global
 // window copy, then the windows Omega_e(X).  Pass B: windows of f from the
 // global window copy, Y = g W_e(f) into shared memory, then the rows Pi_e(Y).
-// Class sums go to a compact class-coordinate field acc[(beta N + gamma) N +
-// alpha] (8 consecutive alpha per unit: two 16-byte accesses) and are added
-// at the cell indices once per class.
+// Class sums go to a compact class-coordinate field acc[(beta N + alpha) N +
+// gamma] (gamma fastest: a warp's accesses are coalesced) and are added at
+// the cell indices once per class.
 template <typename T, int N>
 __device__ __forceinline__ void relayout_compact(const int (&Mi)[9], const T* __restrict__ src, T* dstc) {
     constexpr int N2 = N * N, N3 = N2 * N, M = N - 1;
@@ -418,33 +418,34 @@ __device__ __forceinline__ void relayout_compact(const int (&Mi)[9], const T* __
         const int al = (Mi[0] * p0 + Mi[1] * p1 + Mi[2] * p2) & M;
         const int be = (Mi[3] * p0 + Mi[4] * p1 + Mi[5] * p2) & M;
         const int ga = (Mi[6] * p0 + Mi[7] * p1 + Mi[8] * p2) & M;
-        dstc[(be * N + ga) * N + al] = src[p];
+        dstc[(be * N + al) * N + ga] = src[p];
     }
 }
 
-template <typename T>
+// 8 values of a compact field at alpha = a0 .. a0 + 7 (stride N)
+template <int N, typename T>
 __device__ __forceinline__ void load8(const T* p, T (&v)[8]) {
 #pragma unroll
-    for (int t = 0; t < 8; ++t) v[t] = p[t];
+    for (int t = 0; t < 8; ++t) v[t] = p[t * N];
 }
 
-template <typename T, bool KAHAN>
+template <int N, typename T, bool KAHAN>
 __device__ __forceinline__ void acc8(T* acc, T* cmp, const T (&x)[8], T c) {
     T a[8];
-    load8(acc, a);
+    load8<N>(acc, a);
     if (KAHAN) {
         T k[8];
-        load8(cmp, k);
+        load8<N>(cmp, k);
 #pragma unroll
         for (int t = 0; t < 8; ++t) comp_add<T, true>(a[t], k[t], c * x[t]);
 #pragma unroll
-        for (int t = 0; t < 8; ++t) cmp[t] = k[t];
+        for (int t = 0; t < 8; ++t) cmp[t * N] = k[t];
     } else {
 #pragma unroll
         for (int t = 0; t < 8; ++t) a[t] += c * x[t];
     }
 #pragma unroll
-    for (int t = 0; t < 8; ++t) acc[t] = a[t];
+    for (int t = 0; t < 8; ++t) acc[t * N] = a[t];
 }
 
 template <typename T, bool KAHAN, int N>
@@ -474,7 +475,7 @@ __device__ void vjp_class(const PlanDev& P, const int (&Mm)[9], const int (&Mi)[
                 const T* b = g + (((be + w.y) & M) * N + ((ga + w.z) & M)) * SA + ((a0 + w.x) & M);
                 row_dispatch(w.w, b, P0, D);
             }
-            load8(gC + (be * N + ga) * N + a0, gv);
+            load8<N>(gC + (be * N + a0) * N + ga, gv);
             T Pk = P0;
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
@@ -499,8 +500,8 @@ __device__ void vjp_class(const PlanDev& P, const int (&Mm)[9], const int (&Mi)[
 #pragma unroll
                 for (int t = 0; t < 8; ++t) W[t] += bp[t * N] + bm[t * N];
             }
-            const int ci = (be * N + ga) * N + a0;
-            acc8<T, KAHAN>(accC + ci, cmpC + ci, W, c);
+            const int ci = (be * N + a0) * N + ga;
+            acc8<N, T, KAHAN>(accC + ci, cmpC + ci, W, c);
         }
         __syncthreads();
     }
@@ -519,7 +520,7 @@ __device__ void vjp_class(const PlanDev& P, const int (&Mm)[9], const int (&Mi)[
 #pragma unroll
                 for (int t = 0; t < 8; ++t) W[t] += bp[t * N] + bm[t * N];
             }
-            load8(gC + (be * N + ga) * N + a0, gv);
+            load8<N>(gC + (be * N + a0) * N + ga, gv);
             T* yp = g + (be * N + ga) * SA;
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
@@ -542,15 +543,15 @@ __device__ void vjp_class(const PlanDev& P, const int (&Mm)[9], const int (&Mi)[
             Pv[0] = P0;
 #pragma unroll
             for (int t = 1; t < 8; ++t) Pv[t] = Pv[t - 1] + D[t - 1];
-            const int ci = (be * N + ga) * N + a0;
-            acc8<T, KAHAN>(accC + ci, cmpC + ci, Pv, c);
+            const int ci = (be * N + a0) * N + ga;
+            acc8<N, T, KAHAN>(accC + ci, cmpC + ci, Pv, c);
         }
         __syncthreads();
     }
     // class sums to the cell indices p = M q (mod N)
     for (int u = tid; u < NU; u += NT) {
         const int ga = u & M, be = (u / N) & M, a0 = (u / N2) * 8;
-        const int ci = (be * N + ga) * N + a0;
+        const int ci = (be * N + a0) * N + ga;
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
             const int al = a0 + t;
@@ -558,11 +559,11 @@ __device__ void vjp_class(const PlanDev& P, const int (&Mm)[9], const int (&Mi)[
                           ((Mm[3] * al + Mm[4] * be + Mm[5] * ga) & M) * N + ((Mm[6] * al + Mm[7] * be + Mm[8] * ga) & M);
             if (KAHAN) {
                 T s = dst[o], cc = comp[o];
-                comp_add<T, true>(s, cc, accC[ci + t] + cmpC[ci + t]);
+                comp_add<T, true>(s, cc, accC[ci + t * N] + cmpC[ci + t * N]);
                 dst[o] = s;
                 comp[o] = cc;
             } else {
-                dst[o] += accC[ci + t];
+                dst[o] += accC[ci + t * N];
             }
         }
     }
