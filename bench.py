@@ -71,7 +71,8 @@ def dist_env():
 
 
 PROFILE = os.path.join(ROOT, "profiles", "k_fused2d_batched__batch2d_4096cells.md")
-KERNEL_SOURCES = ["paper_1201_3986_gb300/csrc/fused2d.cu", "paper_1201_3986_gb300/csrc/qdvm_internal.cuh"]
+KERNEL_SOURCES = ["paper_1201_3986_gb300/csrc/fused2d.cu", "paper_1201_3986_gb300/csrc/fft.cuh",
+                  "paper_1201_3986_gb300/csrc/qdvm_internal.cuh"]
 
 
 def kernel_source_hash() -> str:

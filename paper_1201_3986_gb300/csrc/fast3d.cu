@@ -1,4 +1,5 @@
-// 3D forward evaluation with the loss as one convolution per cell.
+// 3D evaluation (forward, JVP, VJP) with the loss as one convolution per
+// cell (eq. (decD): the loss terms of all lines form one convolution).
 //
 // The loss part sum_e c_e f V_e equals f (K * f) with K the weighted
 // displacement histogram of all (k, l) terms (its transform is the plan's

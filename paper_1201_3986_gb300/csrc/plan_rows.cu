@@ -1,6 +1,6 @@
 // Host side of the plan: the 3D plane polygons e^perp ∩ [-Ntilde, Ntilde]^3
-// as rows along an in-plane lattice vector, with the lines grouped by that
-// vector.
+// (the offsets l of the plane sums P_e, alpha'_p in eq. (decDVM)) as rows
+// along an in-plane lattice vector, with the lines grouped by that vector.
 //
 // For a line e pick a primitive u in e^perp and a v with u x v = ±e, so that
 // (u, v) is a basis of the plane lattice e^perp ∩ Z^3.  Every polygon point
