@@ -20,7 +20,10 @@
 
 namespace {
 
-constexpr int kThreadsF3 = 512;
+// Threads per CTA: the cell occupies most of the shared memory (one CTA
+// per SM), so 32^3 cells run 1024 threads (32 warps to hide latency, 64
+// registers each); 16^3 cells have 512 units of 8 points.
+__host__ __device__ constexpr int f3_threads(int N) { return N >= 32 ? 1024 : 512; }
 
 // One Stockham pass of radix R along AXIS (0 = z, 1 = y, 2 = x) over all N^2
 // lines of an N^3 complex array in global memory.  Consecutive threads take
@@ -153,7 +156,7 @@ __device__ void fast3d_item(const PlanDev& P, const int lb, const int le, const 
 }
 
 template <typename T, bool KAHAN, int N>
-__global__ void __launch_bounds__(kThreadsF3) k_fast3d(BatchDev Bt, int n_cells, int Cn, const int* __restrict__ cell_plan,
+__global__ void __launch_bounds__(f3_threads(N), 1) k_fast3d(BatchDev Bt, int n_cells, int Cn, const int* __restrict__ cell_plan,
                                                        const int64_t* __restrict__ cell_offset,
                                                        const int* __restrict__ order, int* counter,
                                                        const T* __restrict__ f, const T* __restrict__ /*aux*/,
@@ -290,37 +293,68 @@ __device__ __forceinline__ T tree_sum(const T (&v)[K]) {
     else return tree_sum<LO, (LO + HI) / 2>(v) + tree_sum<(LO + HI) / 2, HI>(v);
 }
 
+// Start of a row run in the class-coordinate cell: row offsets (dalpha,
+// dbeta, dgamma) from the unit at (a0, be, ga).
+template <int N, typename T>
+__device__ __forceinline__ const T* row_base(const T* g, int be, int ga, int a0, uchar4 w) {
+    constexpr int M = N - 1, SA = rows_sa<N>();
+    return g + (((be + w.y) & M) * N + ((ga + w.z) & M)) * SA + ((a0 + w.x) & M);
+}
+
 // One row of length LEN for the 8 points a0 .. a0 + 7: LEN + 7 loads; the
 // first window is added to P0 and the window increments to D (the window at
-// point k is P0 + D[0] + ... + D[k-1]).
-template <int LEN, typename T>
-__device__ __forceinline__ void row_run(const T* __restrict__ b, T& P0, T (&D)[7]) {
+// point k is P0 + D[0] + ... + D[k-1]).  The next row's start is computed
+// while the loads are in flight and returned.
+template <int LEN, int N, typename T>
+__device__ __forceinline__ const T* row_run(const T* __restrict__ b, T& P0, T (&D)[7], const T* g, int be, int ga,
+                                            int a0, uchar4 wn) {
     T v[LEN + 7];
 #pragma unroll
     for (int t = 0; t < LEN + 7; ++t) v[t] = b[t];
+    const T* bn = row_base<N>(g, be, ga, a0, wn);
     P0 += tree_sum<0, LEN>(v);
 #pragma unroll
     for (int k = 1; k < 8; ++k) D[k - 1] += v[LEN - 1 + k] - v[k - 1];
+    return bn;
 }
 
-template <typename T>
-__device__ __forceinline__ void row_dispatch(int len, const T* b, T& P0, T (&D)[7]) {
+template <int N, typename T>
+__device__ __forceinline__ const T* row_dispatch(int len, const T* b, T& P0, T (&D)[7], const T* g, int be, int ga,
+                                                 int a0, uchar4 wn) {
     switch (len) {
-        case 1: row_run<1>(b, P0, D); break;
-        case 2: row_run<2>(b, P0, D); break;
-        case 3: row_run<3>(b, P0, D); break;
-        case 4: row_run<4>(b, P0, D); break;
-        case 5: row_run<5>(b, P0, D); break;
-        case 6: row_run<6>(b, P0, D); break;
-        case 7: row_run<7>(b, P0, D); break;
-        case 8: row_run<8>(b, P0, D); break;
-        case 9: row_run<9>(b, P0, D); break;
-        case 10: row_run<10>(b, P0, D); break;
-        case 11: row_run<11>(b, P0, D); break;
-        case 12: row_run<12>(b, P0, D); break;
-        case 13: row_run<13>(b, P0, D); break;
-        case 14: row_run<14>(b, P0, D); break;
-        default: row_run<15>(b, P0, D); break;
+        case 1: return row_run<1, N>(b, P0, D, g, be, ga, a0, wn);
+        case 2: return row_run<2, N>(b, P0, D, g, be, ga, a0, wn);
+        case 3: return row_run<3, N>(b, P0, D, g, be, ga, a0, wn);
+        case 4: return row_run<4, N>(b, P0, D, g, be, ga, a0, wn);
+        case 5: return row_run<5, N>(b, P0, D, g, be, ga, a0, wn);
+        case 6: return row_run<6, N>(b, P0, D, g, be, ga, a0, wn);
+        case 7: return row_run<7, N>(b, P0, D, g, be, ga, a0, wn);
+        case 8: return row_run<8, N>(b, P0, D, g, be, ga, a0, wn);
+        case 9: return row_run<9, N>(b, P0, D, g, be, ga, a0, wn);
+        case 10: return row_run<10, N>(b, P0, D, g, be, ga, a0, wn);
+        case 11: return row_run<11, N>(b, P0, D, g, be, ga, a0, wn);
+        case 12: return row_run<12, N>(b, P0, D, g, be, ga, a0, wn);
+        case 13: return row_run<13, N>(b, P0, D, g, be, ga, a0, wn);
+        case 14: return row_run<14, N>(b, P0, D, g, be, ga, a0, wn);
+        default: return row_run<15, N>(b, P0, D, g, be, ga, a0, wn);
+    }
+}
+
+// Plane sums of one line, rows [rs, re), for the unit (a0, be, ga):
+// P0 and D as in row_run.  Row descriptors are fetched two rows ahead and
+// row starts one row ahead.
+template <int N, typename T>
+__device__ __forceinline__ void plane_rows(const uchar4* __restrict__ rows, int rs, int re, const T* g, int be,
+                                           int ga, int a0, T& P0, T (&D)[7]) {
+    if (rs >= re) return;
+    uchar4 w0 = __ldg(rows + rs);
+    uchar4 w1 = __ldg(rows + min(rs + 1, re - 1));
+    const T* b = row_base<N>(g, be, ga, a0, w0);
+    for (int r = rs; r < re; ++r) {
+        const uchar4 w2 = __ldg(rows + min(r + 2, re - 1));
+        b = row_dispatch<N>(w0.w, b, P0, D, g, be, ga, a0, w1);
+        w0 = w1;
+        w1 = w2;
     }
 }
 
@@ -351,13 +385,7 @@ __device__ void class_units(const PlanDev& P, const int (&Mm)[9], int ls, int le
             for (int t = 0; t < 7; ++t) D[t] = T(0);
 #pragma unroll
             for (int t = 0; t < 8; ++t) W[t] = T(0);
-            uchar4 w = __ldg(P.rrow + rs);
-            for (int r = rs; r < re; ++r) {
-                const uchar4 w_n = __ldg(P.rrow + min(r + 1, re - 1));
-                const T* b = g + (((be + w.y) & M) * N + ((ga + w.z) & M)) * SA + ((a0 + w.x) & M);
-                row_dispatch(w.w, b, P0, D);
-                w = w_n;
-            }
+            plane_rows<N>(P.rrow, rs, re, g, be, ga, a0, P0, D);
             for (int j = 1; j <= e.w; ++j) {
                 if (WG) {
                     const T* bp = gw + (((be + j * e.y) & M) * SW + ((a0 + j * e.x) & M)) * N + ((ga + j * e.z) & M);
@@ -471,11 +499,7 @@ __device__ void vjp_class(const PlanDev& P, const int (&Mm)[9], const int (&Mi)[
             T P0 = T(0), D[7], gv[8];
 #pragma unroll
             for (int t = 0; t < 7; ++t) D[t] = T(0);
-            for (int r = rs; r < re; ++r) {
-                const uchar4 w = __ldg(P.rrow + r);
-                const T* b = g + (((be + w.y) & M) * N + ((ga + w.z) & M)) * SA + ((a0 + w.x) & M);
-                row_dispatch(w.w, b, P0, D);
-            }
+            plane_rows<N>(P.rrow, rs, re, g, be, ga, a0, P0, D);
             load8<N>(gC + (be * N + a0) * N + ga, gv);
             T Pk = P0;
 #pragma unroll
@@ -536,11 +560,7 @@ __device__ void vjp_class(const PlanDev& P, const int (&Mm)[9], const int (&Mi)[
             T P0 = T(0), D[7], Pv[8];
 #pragma unroll
             for (int t = 0; t < 7; ++t) D[t] = T(0);
-            for (int r = rs; r < re; ++r) {
-                const uchar4 w = __ldg(P.rrow + r);
-                const T* b = g + (((be + w.y) & M) * N + ((ga + w.z) & M)) * SA + ((a0 + w.x) & M);
-                row_dispatch(w.w, b, P0, D);
-            }
+            plane_rows<N>(P.rrow, rs, re, g, be, ga, a0, P0, D);
             Pv[0] = P0;
 #pragma unroll
             for (int t = 1; t < 8; ++t) Pv[t] = Pv[t - 1] + D[t - 1];
@@ -655,7 +675,7 @@ __device__ void rows3d_item(const PlanDev& P, const int lb, const int le, const 
 }
 
 template <typename T, bool KAHAN, int N, int MODE>
-__global__ void __launch_bounds__(kThreadsF3, 1) k_rows3d(BatchDev Bt, int n_cells, int Cn, const int* __restrict__ cell_plan,
+__global__ void __launch_bounds__(f3_threads(N), 1) k_rows3d(BatchDev Bt, int n_cells, int Cn, const int* __restrict__ cell_plan,
                                                        const int64_t* __restrict__ cell_offset,
                                                        const int* __restrict__ order, int* counter,
                                                        const T* __restrict__ f, const T* __restrict__ aux,
@@ -736,17 +756,18 @@ F3Kernel<T> f3_kernel_n(int N, bool rows, int mode) {
 }
 
 template <typename T>
-int f3_occupancy(F3Kernel<T> k, size_t smem) {
+int f3_occupancy(F3Kernel<T> k, int threads, size_t smem) {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kThreadsF3, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, threads, smem);
     return per > 0 ? per : 1;
 }
 
 int f3_occ(int N, int prec, size_t smem, bool rows, int mode) {
-    if (prec == QDVM_F64) return f3_occupancy<double>(f3_kernel_n<double, false>(N, rows, mode), smem);
-    if (prec == QDVM_F32_KAHAN) return f3_occupancy<float>(f3_kernel_n<float, true>(N, rows, mode), smem);
-    return f3_occupancy<float>(f3_kernel_n<float, false>(N, rows, mode), smem);
+    const int nt = f3_threads(N);
+    if (prec == QDVM_F64) return f3_occupancy<double>(f3_kernel_n<double, false>(N, rows, mode), nt, smem);
+    if (prec == QDVM_F32_KAHAN) return f3_occupancy<float>(f3_kernel_n<float, true>(N, rows, mode), nt, smem);
+    return f3_occupancy<float>(f3_kernel_n<float, false>(N, rows, mode), nt, smem);
 }
 
 // 0 unless every plan is 3D with the same N in {16, 32}, has the loss
@@ -816,7 +837,7 @@ void f3_launch(const F3Layout& g, const BatchDev& b, int n_cells, const int* cp,
                int* counter, const void* f, const void* aux, void* out, char* base, cudaStream_t st) {
     const F3Kernel<T> k = f3_kernel_n<T, KAHAN>(g.N, g.rows, g.mode);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
-    k<<<g.grid, kThreadsF3, g.smem, st>>>(b, n_cells, g.C, cp, co, order, counter, static_cast<const T*>(f),
+    k<<<g.grid, f3_threads(g.N), g.smem, st>>>(b, n_cells, g.C, cp, co, order, counter, static_cast<const T*>(f),
                                            static_cast<const T*>(aux), static_cast<T*>(out),
                                            reinterpret_cast<T*>(base + g.off_part), g.part_stride, base + g.off_scr,
                                            g.scr_stride);
