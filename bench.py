@@ -410,6 +410,83 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_rk2_workload(args):
+    """Time stepping: the 4096-cell batched 2D workload advanced by
+    args.rk2_steps second-order TVD Runge-Kutta steps (two Q evaluations
+    each) per CUDA-graph launch, on 6 rotating batch copies (> L2).  The
+    value counts Q evaluations per second, like the default workload."""
+    import torch
+
+    import oracle
+    import paper_1201_3986_gb300 as q
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    K = args.rk2_steps
+    dt = 0.002
+    b = synth.batch_2d(N_CELLS, Ns=NS, L=L, seed=0)
+    plans = [q.Plan(2, n, NBAR, L, kernel="unit") for n in NS]
+    idx = {n: i for i, n in enumerate(NS)}
+    cp = torch.tensor([idx[int(n)] for n in b.Ns], dtype=torch.int32, device=dev)
+    co = torch.tensor(b.offsets, dtype=torch.int64, device=dev)
+    f_host = torch.from_numpy(b.f.astype(np.float32))
+    fs = [f_host.to(dev) for _ in range(ROTATE)]
+    tuning = q.qdvm_tune_batched(plans, cp, co, fs[0], "f32_kahan",
+                                 workspace=torch.empty(q.batched_workspace_bytes(plans, N_CELLS, "f32_kahan"),
+                                                       dtype=torch.uint8, device=dev))
+    wsb = q.rk2_workspace_bytes(plans, N_CELLS, b.total, "f32_kahan")
+    wss = [torch.empty(wsb, dtype=torch.uint8, device=dev) for _ in range(ROTATE)]
+    Ms = [torch.empty((N_CELLS, 4), dtype=torch.float64, device=dev) for _ in range(ROTATE)]
+    graphs = [q.RK2Graph(plans, cp, co, fs[k], dt, K, "f32_kahan", moments=Ms[k], workspace=wss[k])
+              for k in range(ROTATE)]
+    for g in graphs:
+        g.launch()
+    torch.cuda.synchronize(dev)
+    for k in range(ROTATE):
+        fs[k].copy_(f_host.to(dev))
+    _, m0 = q.qdvm_rk2_batched(plans, cp, co, fs[0].clone(), dt, 0, "f32_kahan", moments=True)
+    stream = torch.cuda.current_stream(dev)
+    for k in range(args.warmup):
+        graphs[k % ROTATE].launch()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        e0.record(stream)
+        for k in range(args.steps):
+            graphs[(args.warmup + k) % ROTATE].launch()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    # accuracy: one step of the first cell of each size against the oracle's stepping
+    errs = []
+    for n in NS:
+        c = int(np.nonzero(b.Ns == n)[0][0])
+        f0 = b.cell(c, b.f.astype(np.float32).astype(np.float64))
+        ft = torch.tensor(f0, dtype=torch.float32, device=dev).reshape(-1)
+        q.qdvm_rk2_batched([plans[idx[n]]], torch.zeros(1, dtype=torch.int32, device=dev),
+                           torch.zeros(1, dtype=torch.int64, device=dev), ft, dt, 1, "f32_kahan")
+        ref = oracle.rk2(f0, L, NBAR, dt, 1)
+        sc = np.max(np.abs(f0)) + dt * np.max(oracle.q(f0, L, NBAR)["scale"])
+        errs.append(float(np.max(np.abs(ft.cpu().numpy().reshape(f0.shape) - ref)) / sc))
+    # mass of graph 0's batch after all its replays, against the start
+    m_end = graphs[0].moments.cpu().numpy()
+    m_start = m0.cpu().numpy()
+    mass_defect = float(np.max(np.abs(m_end[:, 0] - m_start[:, 0]) / np.abs(m_start[:, 0])))
+    evals = 2 * K * b.total
+    line = {"metric": METRIC, "value": evals / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"time stepping: 4096-cell batched 2D workload (N~U{{16,32,48,64}}, Nbar=8, "
+                                   f"seed 0), {K} TVD-RK2 steps of dt={dt} per graph launch (2 Q evaluations per "
+                                   "step), FP32 state + compensated Q sums",
+                       "rk2_steps_per_launch": K, "tuning": tuning,
+                       "l2": "6 rotating batch copies with their own workspaces (> 129 MB L2)"},
+            "rk2_ms_per_time_step": ms / K,
+            "accuracy": {"one_step_rel_err_vs_fp64_oracle_rk2": max(errs), "mass_defect_rel": mass_defect},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def run_gpu_workload(args):
     """Other measured workloads (single GPU): 3D hard spheres on 32^3 cells.
       batch3d   Q on 256 cells, Nbar = 5 (577 lines), FP32
@@ -531,7 +608,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--loss-fft", type=int, default=1, choices=[0, 1],
                     help="single3d, jvp3d: loss as an FFT convolution with row-form gain (1) or the line engine (0)")
-    ap.add_argument("--workload", default="batch2d", choices=["batch2d", "batch3d", "jvp3d", "vjp3d", "single3d"])
+    ap.add_argument("--workload", default="batch2d",
+                    choices=["batch2d", "batch3d", "jvp3d", "vjp3d", "single3d", "rk2"])
+    ap.add_argument("--rk2-steps", type=int, default=10, help="rk2: time steps per graph launch")
     ap.add_argument("--nbar", type=int, default=None)
     ap.add_argument("--cells", type=int, default=256, help="batch3d / jvp3d / vjp3d: number of 32^3 cells")
     ap.add_argument("--tuning", default=None,
@@ -543,6 +622,8 @@ def main():
     if args.impl == "reference":
         args.ref_cells = args.ref_cells or REF_STEP_CELLS
         run_reference(args)
+    elif args.workload == "rk2":
+        run_rk2_workload(args)
     elif args.workload != "batch2d":
         run_gpu_workload(args)
     else:

@@ -204,6 +204,33 @@ qdvm_status qdvm_graph_capture_batched(qdvm_graph_t* out, const qdvm_plan_t* pla
 qdvm_status qdvm_graph_launch(qdvm_graph_t graph, void* stream);
 qdvm_status qdvm_graph_destroy(qdvm_graph_t graph);
 
+/* Space-homogeneous time stepping df/dt = Q(f) of every cell of a batch by
+ * the second-order total-variation-diminishing Runge-Kutta scheme of
+ * Section 4, in the Shu-Osher form
+ *   f1 = f + dt Q(f),   f <- (f + f1 + dt Q(f1)) / 2,
+ * repeated n_steps times, in place on f.  f: device, n_elems values of the
+ * given precision, the cells laid out as for qdvm_eval_batched (n_elems =
+ * total number of values).  Each Q evaluation is a qdvm_eval_batched call
+ * with the plans' tuning.  moments: device, n_cells x (d + 2) doubles, or
+ * NULL; receives the FP64 moments h^d sum f phi of the final f.  The
+ * workspace (size from qdvm_rk2_workspace) holds the evaluator's workspace,
+ * f1 and Q; it is the caller's.  Stream-ordered, no host synchronisation,
+ * capturable (qdvm_graph_capture_rk2).  Errors: INVALID_ARG for negative
+ * counts, a non-finite dt, NULL arrays or a small workspace; the
+ * evaluator's errors otherwise. */
+qdvm_status qdvm_rk2_workspace(const qdvm_plan_t* plans, int n_plans, int n_cells, int64_t n_elems, int prec,
+                               size_t* bytes);
+qdvm_status qdvm_rk2_batched(const qdvm_plan_t* plans, int n_plans, int n_cells, const int* cell_plan,
+                             const int64_t* cell_offset, int64_t n_elems, void* f, double dt, int n_steps,
+                             double* moments, int prec, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Capture qdvm_rk2_batched (n_steps steps, all pointers fixed) into an
+ * executable graph for qdvm_graph_launch: one launch runs the whole loop. */
+qdvm_status qdvm_graph_capture_rk2(qdvm_graph_t* out, const qdvm_plan_t* plans, int n_plans, int n_cells,
+                                   const int* cell_plan, const int64_t* cell_offset, int64_t n_elems, void* f,
+                                   double dt, int n_steps, double* moments, int prec, void* workspace,
+                                   size_t workspace_bytes);
+
 /* Largest batch accepted by qdvm_eval_batched_noalloc. */
 #define QDVM_NOALLOC_MAX_CELLS 65536
 

@@ -19,6 +19,9 @@ Functions and the passages they follow:
   transpose of its Jacobian (scattered term by term); ``jvp_points`` /
   ``vjp_points`` the same at selected points (the VJP as a gather).
 * ``moments``                -- mass, momentum and energy of Section 2.1.
+* ``rk2(...)``               -- the second-order TVD Runge-Kutta time
+  stepping of Section 4 for df/dt = Q(f) (Shu-Osher form), in numpy around
+  ``q``.
 * ``default_ntilde(N)``      -- Ntilde = floor(N / (3 + sqrt 2)), Section 4.
 
 Parity status: every function above is pinned by ``tests/test_oracle_*.py``
@@ -169,6 +172,18 @@ def q_points(f, L: float, Nbar: int, idx=None, kernel: str = "unit", Ntilde: int
 
 def q(f, L: float, Nbar: int, kernel: str = "unit", Ntilde: int | None = None) -> dict:
     return q_points(f, L, Nbar, None, kernel, Ntilde)
+
+
+def rk2(f, L: float, Nbar: int, dt: float, n_steps: int, kernel: str = "unit",
+        Ntilde: int | None = None) -> np.ndarray:
+    """n_steps of the second-order total-variation-diminishing Runge-Kutta
+    scheme that Section 4 uses for its runs, for df/dt = Q(f):
+    f1 = f + dt Q(f), then f <- (f + f1 + dt Q(f1)) / 2."""
+    f = _f64(f).copy()
+    for _ in range(n_steps):
+        f1 = f + dt * q(f, L, Nbar, kernel=kernel, Ntilde=Ntilde)["Q"]
+        f = 0.5 * (f + (f1 + dt * q(f1, L, Nbar, kernel=kernel, Ntilde=Ntilde)["Q"]))
+    return f
 
 
 def jvp(f, df, L: float, Nbar: int, kernel: str = "unit", Ntilde: int | None = None) -> np.ndarray:

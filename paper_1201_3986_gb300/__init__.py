@@ -85,6 +85,11 @@ _sig("qdvm_graph_capture_batched", [_P(_vp), _P(_vp), _i, _i, _vp, _vp, _vp, _vp
 _sig("qdvm_graph_launch", [_vp, _vp])
 _sig("qdvm_graph_destroy", [_vp])
 _sig("qdvm_eval_batched_noalloc", [_P(_vp), _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp])
+_sig("qdvm_rk2_workspace", [_P(_vp), _i, _i, ctypes.c_int64, _i, _P(_sz)])
+_sig("qdvm_rk2_batched", [_P(_vp), _i, _i, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_double, _i, _vp, _i, _vp, _sz,
+                          _vp])
+_sig("qdvm_graph_capture_rk2", [_P(_vp), _P(_vp), _i, _i, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_double, _i, _vp,
+                                _i, _vp, _sz])
 QDVM_NOALLOC_MAX_CELLS = 65536
 _lib.qdvm_status_string.argtypes = [_i]
 _lib.qdvm_status_string.restype = ctypes.c_char_p
@@ -274,6 +279,70 @@ class BatchedGraph:
                                                _ptr(self.workspace),
                                                0 if self.workspace is None else self.workspace.numel()),
                "qdvm_graph_capture_batched")
+        self.handle = h
+        self.device = f.device
+
+    def launch(self):
+        _check(_lib.qdvm_graph_launch(self.handle, _stream(self.device)), "qdvm_graph_launch")
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.qdvm_graph_destroy(self.handle)
+            self.handle = None
+
+
+def rk2_workspace_bytes(plans, n_cells: int, n_elems: int, prec) -> int:
+    b = ctypes.c_size_t()
+    _check(_lib.qdvm_rk2_workspace(_plan_array(plans), len(plans), n_cells, int(n_elems), _prec(prec), ctypes.byref(b)),
+           "qdvm_rk2_workspace")
+    return b.value
+
+
+def _rk2_args(plans, cell_plan, cell_offset, f, prec, moments, workspace):
+    p = _prec(prec)
+    n_cells = int(cell_plan.numel())
+    if cell_plan.dtype != torch.int32 or cell_offset.dtype != torch.int64:
+        raise ValueError("cell_plan must be int32 and cell_offset int64")
+    if f.dtype != _DTYPE[p] or not f.is_cuda or not f.is_contiguous():
+        raise ValueError(f"f must be a contiguous CUDA {_DTYPE[p]} tensor")
+    mom = None
+    if isinstance(moments, torch.Tensor):
+        mom = moments
+    elif moments:
+        mom = torch.empty((n_cells, plans[0].d + 2), dtype=torch.float64, device=f.device)
+    ws = workspace if workspace is not None else _workspace(rk2_workspace_bytes(plans, n_cells, f.numel(), p),
+                                                            f.device)
+    return p, n_cells, mom, ws
+
+
+def qdvm_rk2_batched(plans, cell_plan: torch.Tensor, cell_offset: torch.Tensor, f: torch.Tensor, dt: float,
+                     n_steps: int, prec="f32_kahan", moments: torch.Tensor | bool | None = False,
+                     workspace: torch.Tensor | None = None):
+    """Advance every cell of a ragged batch by n_steps second-order TVD
+    Runge-Kutta steps of df/dt = Q(f), in place on f.  Returns (f, moments
+    of the final f or None)."""
+    p, n_cells, mom, ws = _rk2_args(plans, cell_plan, cell_offset, f, prec, moments, workspace)
+    _check(_lib.qdvm_rk2_batched(_plan_array(plans), len(plans), n_cells, _ptr(cell_plan), _ptr(cell_offset), f.numel(),
+                                 _ptr(f), float(dt), int(n_steps), _ptr(mom), p, _ptr(ws),
+                                 0 if ws is None else ws.numel(), _stream(f.device)), "qdvm_rk2_batched")
+    return f, mom
+
+
+class RK2Graph:
+    """n_steps of qdvm_rk2_batched (fixed tensors, f updated in place)
+    captured into one CUDA graph; ``launch()`` replays the whole loop."""
+
+    def __init__(self, plans, cell_plan, cell_offset, f, dt, n_steps, prec="f32_kahan", moments=None,
+                 workspace=None):
+        p, n_cells, mom, ws = _rk2_args(plans, cell_plan, cell_offset, f, prec, moments, workspace)
+        self._keep = (plans, cell_plan, cell_offset, f, mom)
+        self.workspace = ws
+        self.moments = mom
+        self.handle = None
+        h = ctypes.c_void_p()
+        _check(_lib.qdvm_graph_capture_rk2(ctypes.byref(h), _plan_array(plans), len(plans), n_cells, _ptr(cell_plan),
+                                           _ptr(cell_offset), f.numel(), _ptr(f), float(dt), int(n_steps), _ptr(mom),
+                                           p, _ptr(ws), 0 if ws is None else ws.numel()), "qdvm_graph_capture_rk2")
         self.handle = h
         self.device = f.device
 

@@ -1,6 +1,6 @@
-// CUDA-graph capture of a batched evaluation: the schedule and the persistent
-// evaluator become one executable graph with fixed device pointers, replayed
-// with a single launch per step.
+// CUDA-graph capture of a batched evaluation (the schedule and the persistent
+// evaluator) or of a loop of time steps: one executable graph with fixed
+// device pointers, replayed with a single launch.
 #include "qdvm_internal.cuh"
 
 #define QDVM_GRAPH_MAGIC 0x51445647u  // "QDVG"
@@ -10,10 +10,11 @@ struct qdvm_graph_s {
     cudaGraphExec_t exec;
 };
 
-extern "C" qdvm_status qdvm_graph_capture_batched(qdvm_graph_t* out, const qdvm_plan_t* plans, int n_plans,
-                                                  int n_cells, const int* cell_plan, const int64_t* cell_offset,
-                                                  const void* f, void* Q, double* moments, int prec, void* ws,
-                                                  size_t ws_bytes) {
+namespace {
+
+// Captures the stream work of fn(stream) into an executable graph.
+template <typename Fn>
+qdvm_status capture(qdvm_graph_t* out, Fn fn) {
     if (!out) return qdvm_fail(QDVM_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     cudaStream_t s = nullptr;
@@ -23,8 +24,7 @@ extern "C" qdvm_status qdvm_graph_capture_batched(qdvm_graph_t* out, const qdvm_
         cudaStreamDestroy(s);
         return qdvm_cuda_status(e, "cudaStreamBeginCapture");
     }
-    qdvm_status st = qdvm_eval_batched(plans, n_plans, n_cells, cell_plan, cell_offset, f, Q, moments, prec, ws,
-                                       ws_bytes, s);
+    qdvm_status st = fn(s);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(s, &g);
     cudaStreamDestroy(s);
@@ -46,6 +46,27 @@ extern "C" qdvm_status qdvm_graph_capture_batched(qdvm_graph_t* out, const qdvm_
     h->exec = exec;
     *out = h;
     return QDVM_OK;
+}
+
+}  // namespace
+
+extern "C" qdvm_status qdvm_graph_capture_batched(qdvm_graph_t* out, const qdvm_plan_t* plans, int n_plans,
+                                                  int n_cells, const int* cell_plan, const int64_t* cell_offset,
+                                                  const void* f, void* Q, double* moments, int prec, void* ws,
+                                                  size_t ws_bytes) {
+    return capture(out, [&](cudaStream_t s) {
+        return qdvm_eval_batched(plans, n_plans, n_cells, cell_plan, cell_offset, f, Q, moments, prec, ws, ws_bytes, s);
+    });
+}
+
+extern "C" qdvm_status qdvm_graph_capture_rk2(qdvm_graph_t* out, const qdvm_plan_t* plans, int n_plans, int n_cells,
+                                              const int* cell_plan, const int64_t* cell_offset, int64_t n_elems,
+                                              void* f, double dt, int n_steps, double* moments, int prec, void* ws,
+                                              size_t ws_bytes) {
+    return capture(out, [&](cudaStream_t s) {
+        return qdvm_rk2_batched(plans, n_plans, n_cells, cell_plan, cell_offset, n_elems, f, dt, n_steps, moments, prec,
+                                ws, ws_bytes, s);
+    });
 }
 
 extern "C" qdvm_status qdvm_graph_launch(qdvm_graph_t g, void* stream) {
