@@ -487,6 +487,88 @@ def run_rk2_workload(args):
     print(json.dumps(line), flush=True)
 
 
+# Table 2 of the paper: CPU time (s) of the fast DVM to T = 1 with dt = 0.01
+# (100 TVD-RK2 steps) on one 2D BKW cell, hardware unstated; keys (N, Nbar).
+TABLE2_S = {(16, 3): 0.5, (32, 3): 3.19, (32, 7): 14.52, (64, 3): 16.2, (64, 7): 73.4, (64, 14): 283.0,
+            (128, 3): 85.8, (128, 7): 378.0, (128, 14): 1382.0, (128, 28): 5531.0}
+# velocity domain half-width per N used for those runs (Section 4)
+TABLE2_L = {16: 5.5, 32: 7.0, 64: 8.0, 128: 8.0}
+
+
+def run_bkw_workload(args):
+    """The paper's timing run (Table 2): one 2D BKW cell, 100 TVD-RK2 steps of
+    dt = 0.01 to T = 1, captured in one CUDA graph.  The weights are the
+    h-scaled ones (c_e = h^3 |e|): with them a step changes f by about 1% on
+    every grid, whereas the unscaled unit weights make dt = 0.01 unstable
+    from N = 128 on.  The cost does not depend on the weights.  The value
+    counts Q evaluations per second (200 per run)."""
+    import torch
+
+    import oracle
+    import paper_1201_3986_gb300 as q
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    N, nb = args.n, args.nbar or 14
+    prec = args.prec
+    Lh = TABLE2_L.get(N, 8.0)
+    dt, n_steps = 0.01, 100
+    f_np = synth.bkw_2d(N, Lh)
+    plan = q.Plan(2, N, nb, Lh, kernel="hp")
+    plan.set_tuning(loss_fft=0 if args.loss_fft is None else args.loss_fft)
+    dtype = torch.float64 if prec == "f64" else torch.float32
+    f0 = torch.tensor(f_np, dtype=dtype, device=dev)
+    f = f0.clone()
+    wsb = q.rk2_workspace_single_bytes(plan, prec)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    q.qdvm_rk2(plan, f, dt, 1, prec, workspace=ws)  # first call outside capture
+    torch.cuda.synchronize(dev)
+    f.copy_(f0)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        q.qdvm_rk2(plan, f, dt, n_steps, prec, workspace=ws)
+    m0 = q.qdvm_moments(plan, f0, prec).cpu().numpy()
+    f.copy_(f0)
+    g.replay()  # one run to T = 1 from the datum
+    torch.cuda.synchronize(dev)
+    m1 = q.qdvm_moments(plan, f, prec).cpu().numpy()
+    for _ in range(args.warmup):
+        g.replay()
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    acc = {"mass_defect_rel_T1": float(abs(m1[0] - m0[0]) / abs(m0[0]))}
+    if N <= 64:
+        f.copy_(f0)
+        q.qdvm_rk2(plan, f, dt, 1, prec, workspace=ws)
+        ref = oracle.rk2(f_np, Lh, nb, dt, 1, kernel="hp")
+        sc = np.max(np.abs(f_np)) + dt * np.max(oracle.q(f_np, Lh, nb, kernel="hp")["scale"])
+        acc["one_step_rel_err_vs_fp64_oracle_rk2"] = float(np.max(np.abs(f.cpu().numpy() - ref)) / sc)
+    evals = 2 * n_steps * N * N
+    paper = TABLE2_S.get((N, nb))
+    value = evals / (ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": (value / (evals / paper)) if paper else None, "dtype": "f64" if prec == "f64" else "f32",
+            "data": "synthetic",
+            "config": {"workload": f"paper Table 2 run: 2D BKW datum (S = 0.6), N={N} on [-{Lh},{Lh}]^2, Nbar={nb} "
+                                   f"({plan.n_lines} lines), h-scaled weights c_e = h^3|e|, TVD-RK2 dt=0.01 to "
+                                   f"T=1 (100 steps, 200 Q evaluations) per step of this line, one CUDA graph",
+                       "N": N, "Nbar": nb, "prec": prec, "tuning": plan.tuning(),
+                       "paper_table2_s": paper,
+                       "vs_baseline_note": "Q evaluations per second against Table 2's time to T = 1 "
+                                           "(CPU, hardware unstated): context, not a target"},
+            "time_to_T1_ms": ms, "accuracy": acc, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def run_gpu_workload(args):
     """Other measured workloads (single GPU): 3D hard spheres on 32^3 cells.
       batch3d   Q on 256 cells, Nbar = 5 (577 lines), FP32
@@ -507,7 +589,7 @@ def run_gpu_workload(args):
         nb = args.nbar or 5
         f_np = synth.trimaxwellian_3d(32, 6.0)
         plan = q.Plan(3, 32, nb, 6.0, kernel="hp")
-        plan.set_tuning(loss_fft=args.loss_fft)
+        plan.set_tuning(loss_fft=1 if args.loss_fft is None else args.loss_fft)
         rot = 8  # 8 x 128 KB inputs + outputs; the scratch dominates anyway
         fs = [torch.tensor(f_np, dtype=torch.float32, device=dev) for _ in range(rot)]
         outs = [torch.empty_like(fs[0]) for _ in range(rot)]
@@ -538,7 +620,7 @@ def run_gpu_workload(args):
             plan.set_tuning(loss_fft=fft)
             wsb.append(q.batched_workspace_bytes([plan], b.n_cells, "f32"))
         ws = torch.empty(2 * max(wsb), dtype=torch.uint8, device=dev)
-        plan.set_tuning(loss_fft=args.loss_fft)
+        plan.set_tuning(loss_fft=1 if args.loss_fft is None else args.loss_fft)
         if wl == "batch3d":
             if args.tuning:
                 th, dj, fft, ch = (int(v) for v in args.tuning.split(","))
@@ -606,10 +688,13 @@ def main():
     ap.add_argument("--impl", default="qdvm", choices=["qdvm", "reference"])
     ap.add_argument("--ref-cells", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--loss-fft", type=int, default=1, choices=[0, 1],
-                    help="single3d, jvp3d: loss as an FFT convolution with row-form gain (1) or the line engine (0)")
+    ap.add_argument("--loss-fft", type=int, default=None, choices=[0, 1],
+                    help="single3d, jvp3d, vjp3d (default 1): loss as an FFT convolution with row-form gain, or the "
+                         "line engine (0); bkw (default 0): FFT loss in the single-cell 2D evaluator")
     ap.add_argument("--workload", default="batch2d",
-                    choices=["batch2d", "batch3d", "jvp3d", "vjp3d", "single3d", "rk2"])
+                    choices=["batch2d", "batch3d", "jvp3d", "vjp3d", "single3d", "rk2", "bkw"])
+    ap.add_argument("--n", type=int, default=64, help="bkw: points per axis")
+    ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f32_kahan"], help="bkw: precision")
     ap.add_argument("--rk2-steps", type=int, default=10, help="rk2: time steps per graph launch")
     ap.add_argument("--nbar", type=int, default=None)
     ap.add_argument("--cells", type=int, default=256, help="batch3d / jvp3d / vjp3d: number of 32^3 cells")
@@ -624,6 +709,8 @@ def main():
         run_reference(args)
     elif args.workload == "rk2":
         run_rk2_workload(args)
+    elif args.workload == "bkw":
+        run_bkw_workload(args)
     elif args.workload != "batch2d":
         run_gpu_workload(args)
     else:

@@ -224,6 +224,13 @@ qdvm_status qdvm_rk2_batched(const qdvm_plan_t* plans, int n_plans, int n_cells,
                              const int64_t* cell_offset, int64_t n_elems, void* f, double dt, int n_steps,
                              double* moments, int prec, void* workspace, size_t workspace_bytes, void* stream);
 
+/* The same time stepping for one cell f (device, N^d values), with
+ * qdvm_eval for each Q evaluation (a single cell's lines spread over the
+ * whole GPU).  Workspace from qdvm_rk2_workspace_single.  Same errors. */
+qdvm_status qdvm_rk2_workspace_single(qdvm_plan_t plan, int prec, size_t* bytes);
+qdvm_status qdvm_rk2(qdvm_plan_t plan, void* f, double dt, int n_steps, int prec, void* workspace,
+                     size_t workspace_bytes, void* stream);
+
 /* Capture qdvm_rk2_batched (n_steps steps, all pointers fixed) into an
  * executable graph for qdvm_graph_launch: one launch runs the whole loop. */
 qdvm_status qdvm_graph_capture_rk2(qdvm_graph_t* out, const qdvm_plan_t* plans, int n_plans, int n_cells,

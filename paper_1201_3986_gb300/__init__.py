@@ -88,6 +88,8 @@ _sig("qdvm_eval_batched_noalloc", [_P(_vp), _i, _i, _vp, _vp, _vp, _vp, _vp, _i,
 _sig("qdvm_rk2_workspace", [_P(_vp), _i, _i, ctypes.c_int64, _i, _P(_sz)])
 _sig("qdvm_rk2_batched", [_P(_vp), _i, _i, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_double, _i, _vp, _i, _vp, _sz,
                           _vp])
+_sig("qdvm_rk2_workspace_single", [_vp, _i, _P(_sz)])
+_sig("qdvm_rk2", [_vp, _vp, ctypes.c_double, _i, _i, _vp, _sz, _vp])
 _sig("qdvm_graph_capture_rk2", [_P(_vp), _P(_vp), _i, _i, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_double, _i, _vp,
                                 _i, _vp, _sz])
 QDVM_NOALLOC_MAX_CELLS = 65536
@@ -326,6 +328,26 @@ def qdvm_rk2_batched(plans, cell_plan: torch.Tensor, cell_offset: torch.Tensor, 
                                  _ptr(f), float(dt), int(n_steps), _ptr(mom), p, _ptr(ws),
                                  0 if ws is None else ws.numel(), _stream(f.device)), "qdvm_rk2_batched")
     return f, mom
+
+
+def rk2_workspace_single_bytes(plan: Plan, prec) -> int:
+    b = ctypes.c_size_t()
+    _check(_lib.qdvm_rk2_workspace_single(plan.handle, _prec(prec), ctypes.byref(b)), "qdvm_rk2_workspace_single")
+    return b.value
+
+
+def qdvm_rk2(plan: Plan, f: torch.Tensor, dt: float, n_steps: int, prec="f64",
+             workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """Advance one cell by n_steps second-order TVD Runge-Kutta steps of
+    df/dt = Q(f), in place on f."""
+    p = _prec(prec)
+    if f.dtype != _DTYPE[p] or not f.is_cuda or not f.is_contiguous():
+        raise ValueError(f"f must be a contiguous CUDA {_DTYPE[p]} tensor")
+    if workspace is None:
+        workspace = _workspace(rk2_workspace_single_bytes(plan, p), f.device)
+    _check(_lib.qdvm_rk2(plan.handle, _ptr(f), float(dt), int(n_steps), p, _ptr(workspace),
+                         0 if workspace is None else workspace.numel(), _stream(f.device)), "qdvm_rk2")
+    return f
 
 
 class RK2Graph:

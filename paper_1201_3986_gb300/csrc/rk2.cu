@@ -109,3 +109,68 @@ extern "C" qdvm_status qdvm_rk2_batched(const qdvm_plan_t* plans, int n_plans, i
     }
     return QDVM_OK;
 }
+
+// One cell (the same scheme with qdvm_eval, which spreads a single cell's
+// lines over the whole GPU): workspace = evaluator workspace, f1, Q.
+namespace {
+
+qdvm_status rk2_single_layout(qdvm_plan_t p, int prec, Rk2Layout* g) {
+    size_t eval = 0;
+    qdvm_status s = qdvm_eval_workspace(p, prec, &eval);
+    if (s != QDVM_OK) return s;
+    const size_t es = prec == QDVM_F64 ? sizeof(double) : sizeof(float);
+    const size_t n = (size_t)p->N * p->N * (p->d == 3 ? p->N : 1);
+    g->eval = r256(eval);
+    g->off_f1 = g->eval;
+    g->off_q = g->off_f1 + r256(n * es);
+    g->total = g->off_q + r256(n * es);
+    return QDVM_OK;
+}
+
+}  // namespace
+
+extern "C" qdvm_status qdvm_rk2_workspace_single(qdvm_plan_t p, int prec, size_t* bytes) {
+    if (!qdvm_plan_ok(p)) return qdvm_fail(QDVM_ERR_BAD_PLAN, "bad plan handle");
+    if (!bytes) return qdvm_fail(QDVM_ERR_INVALID_ARG, "NULL bytes");
+    Rk2Layout g;
+    qdvm_status s = rk2_single_layout(p, prec, &g);
+    if (s != QDVM_OK) return s;
+    *bytes = g.total;
+    return QDVM_OK;
+}
+
+extern "C" qdvm_status qdvm_rk2(qdvm_plan_t p, void* f, double dt, int n_steps, int prec, void* ws, size_t ws_bytes,
+                                void* stream) {
+    if (!qdvm_plan_ok(p)) return qdvm_fail(QDVM_ERR_BAD_PLAN, "bad plan handle");
+    if (n_steps < 0) return qdvm_fail(QDVM_ERR_INVALID_ARG, "negative n_steps");
+    if (!std::isfinite(dt)) return qdvm_fail(QDVM_ERR_INVALID_ARG, "dt must be finite");
+    if (prec != QDVM_F64 && prec != QDVM_F32 && prec != QDVM_F32_KAHAN)
+        return qdvm_fail(QDVM_ERR_INVALID_ARG, "bad precision");
+    if (!f) return qdvm_fail(QDVM_ERR_INVALID_ARG, "f must be a device pointer");
+    Rk2Layout g;
+    qdvm_status s = rk2_single_layout(p, prec, &g);
+    if (s != QDVM_OK) return s;
+    if (!ws || ws_bytes < g.total) return qdvm_fail(QDVM_ERR_INVALID_ARG, "workspace too small for qdvm_rk2");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t n = (int64_t)p->N * p->N * (p->d == 3 ? p->N : 1);
+    char* base = static_cast<char*>(ws);
+    void* f1 = base + g.off_f1;
+    void* q = base + g.off_q;
+    for (int k = 0; k < n_steps; ++k) {
+        s = qdvm_eval(p, f, q, prec, ws, g.eval, st);
+        if (s != QDVM_OK) return s;
+        if (prec == QDVM_F64)
+            launch_stage<double>(1, n, static_cast<double*>(f), static_cast<double*>(f1), static_cast<double*>(q), dt, st);
+        else
+            launch_stage<float>(1, n, static_cast<float*>(f), static_cast<float*>(f1), static_cast<float*>(q), dt, st);
+        QDVM_LAUNCH_CHECK("rk2 stage 1");
+        s = qdvm_eval(p, f1, q, prec, ws, g.eval, st);
+        if (s != QDVM_OK) return s;
+        if (prec == QDVM_F64)
+            launch_stage<double>(2, n, static_cast<double*>(f), static_cast<double*>(f1), static_cast<double*>(q), dt, st);
+        else
+            launch_stage<float>(2, n, static_cast<float*>(f), static_cast<float*>(f1), static_cast<float*>(q), dt, st);
+        QDVM_LAUNCH_CHECK("rk2 stage 2");
+    }
+    return QDVM_OK;
+}

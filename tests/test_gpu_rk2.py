@@ -110,3 +110,19 @@ def test_rk2_zero_steps_and_argument_errors(q, torch):
     with pytest.raises(q.QdvmError):
         q.qdvm_rk2_batched(plans, cp, co, f, 0.01, 1, "f32", workspace=small)
     assert torch.equal(f, f0)
+
+
+@pytest.mark.parametrize("d,N,Nbar,kernel,dt,loss_fft", [(2, 32, 7, "unit", 0.002, 0), (2, 32, 7, "unit", 0.002, 1),
+                                                          (2, 80, 4, "unit", 0.002, 0), (3, 16, 3, "hp", 0.05, 1)])
+def test_rk2_single_cell_matches_oracle(q, torch, d, N, Nbar, kernel, dt, loss_fft):
+    """One cell through qdvm_rk2 (the single-cell evaluator, lines spread
+    over the GPU; N = 80 takes the generic engine), FP64."""
+    f0 = synth.bkw_2d(N, 8.0) if d == 2 else synth.mixture(3, N, 6.0, np.random.default_rng(2))
+    L = 8.0 if d == 2 else 6.0
+    plan = q.Plan(d, N, Nbar, L, kernel=kernel)
+    plan.set_tuning(loss_fft=loss_fft)
+    f = torch.tensor(f0, dtype=torch.float64, device="cuda")
+    q.qdvm_rk2(plan, f, dt, 2, "f64")
+    ref = oracle.rk2(f0, L, Nbar, dt, 2, kernel=kernel)
+    assert np.max(np.abs(f.cpu().numpy() - ref)) <= 1e-12 * _bound(f0, L, Nbar, kernel, dt, 2)
+    assert np.max(np.abs(ref - f0)) > 1e-4 * np.max(np.abs(f0))
