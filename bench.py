@@ -487,6 +487,104 @@ def run_rk2_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def run_adaptive_workload(args):
+    """Space-dependent Nbar on a 4096-cell 2D batch at various distances from
+    equilibrium (synth.batch_2d_relaxing): each step computes the per-cell
+    equilibrium indicator, selects Nbar in {2, 4, 8} with thresholds
+    (0.02, 0.1) and evaluates the batch; one CUDA graph per rotating batch
+    copy.  Compared with the fixed Nbar = 8 evaluation of the same batch."""
+    import torch
+
+    import oracle
+    import paper_1201_3986_gb300 as q
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    nbars, thr = (2, 4, 8), (0.02, 0.1)
+    b = synth.batch_2d_relaxing(N_CELLS, Ns=NS, L=L, seed=3)
+    plans = [q.Plan(2, n, nb, L, kernel="unit") for n in NS for nb in nbars]
+    level_plan = np.arange(len(plans)).reshape(len(NS), len(nbars))
+    idx = {n: i for i, n in enumerate(NS)}
+    cb = torch.tensor([idx[int(n)] for n in b.Ns], dtype=torch.int32, device=dev)
+    co = torch.tensor(b.offsets, dtype=torch.int64, device=dev)
+    f_host = torch.from_numpy(b.f.astype(np.float32))
+    fs = [f_host.to(dev) for _ in range(ROTATE)]
+    eps = [torch.empty(N_CELLS, dtype=torch.float64, device=dev) for _ in range(ROTATE)]
+    cps = [torch.empty(N_CELLS, dtype=torch.int32, device=dev) for _ in range(ROTATE)]
+    Qs = [torch.empty_like(fs[0]) for _ in range(ROTATE)]
+    base = plans[::len(nbars)]  # one plan per N: the indicator needs each cell's N and L
+    q.equilibrium_distance(base, cb, co, fs[0], "f32_kahan", out=eps[0])
+    q.select_levels(eps[0], cb, thr, level_plan, out=cps[0])
+    wsb = q.batched_workspace_bytes(plans, N_CELLS, "f32_kahan")
+    ws = [torch.empty(wsb, dtype=torch.uint8, device=dev) for _ in range(ROTATE)]
+    tuning = q.qdvm_tune_batched(plans, cps[0], co, fs[0], "f32_kahan", workspace=ws[0])
+    # fixed Nbar = 8 on the same batch (level 2 for every cell)
+    cp8 = (cb * len(nbars) + 2).to(torch.int32)
+
+    def capture(fn):
+        g = torch.cuda.CUDAGraph()
+        fn()
+        torch.cuda.synchronize(dev)
+        with torch.cuda.graph(g):
+            fn()
+        return g
+
+    def adaptive(k):
+        return lambda: (q.equilibrium_distance(base, cb, co, fs[k], "f32_kahan", out=eps[k]),
+                        q.select_levels(eps[k], cb, thr, level_plan, out=cps[k]),
+                        q.qdvm_eval_batched(plans, cps[k], co, fs[k], "f32_kahan", out=Qs[k], moments=False,
+                                            workspace=ws[k]))
+
+    def fixed(k):
+        return lambda: q.qdvm_eval_batched(plans, cp8, co, fs[k], "f32_kahan", out=Qs[k], moments=False,
+                                           workspace=ws[k])
+
+    def timed(graphs):
+        for k in range(args.warmup):
+            graphs[k % ROTATE].replay()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st = torch.cuda.current_stream(dev)
+        e0.record(st)
+        for k in range(args.steps):
+            graphs[(args.warmup + k) % ROTATE].replay()
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / args.steps
+
+    g_fix = [capture(fixed(k)) for k in range(ROTATE)]
+    ms_fixed = timed(g_fix)
+    Q8 = Qs[0].clone()
+    g_ad = [capture(adaptive(k)) for k in range(ROTATE)]
+    with ClockSampler(dev.index) as clk:
+        ms = timed(g_ad)
+    adaptive(0)()
+    torch.cuda.synchronize(dev)
+    lev = (cps[0].cpu().numpy() % len(nbars))
+    fractions = [float((lev == i).mean()) for i in range(len(nbars))]
+    Qa = Qs[0].cpu().numpy().astype(np.float64)
+    Q8n = Q8.cpu().numpy().astype(np.float64)
+    fin = fs[0].cpu().numpy().astype(np.float64)
+    err, trunc = 0.0, 0.0
+    for c in (0, 1, 2, 3, N_CELLS - 1):
+        r = oracle.q(b.cell(c, fin), L, nbars[lev[c]])
+        err = max(err, oracle.rel_linf(b.cell(c, Qa), r["Q"], r["scale"]))
+        trunc = max(trunc, float(np.max(np.abs(b.cell(c, Qa) - b.cell(c, Q8n))) / np.max(r["scale"])))
+    line = {"metric": METRIC, "value": b.total / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "space-dependent Nbar: 4096 2D cells N~U{16,32,48,64} at various distances from "
+                                   "equilibrium (second-Maxwellian weight 0.5 U^3, seed 3), Nbar in {2,4,8} by the "
+                                   "indicator sum|f-M[f]|/sum|f| with thresholds (0.02, 0.1); indicator, selection "
+                                   "and evaluation in one CUDA graph per rotating batch copy (6 copies > L2)",
+                       "tuning": tuning, "level_fractions_nbar_2_4_8": fractions},
+            "fixed_nbar8_ms_per_step": ms_fixed, "speedup_vs_fixed_nbar8": ms_fixed / ms,
+            "accuracy": {"rel_linf_vs_fp64_oracle_at_selected_nbar": err,
+                         "truncation_vs_nbar8_rel_to_scale": trunc},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 # Table 2 of the paper: CPU time (s) of the fast DVM to T = 1 with dt = 0.01
 # (100 TVD-RK2 steps) on one 2D BKW cell, hardware unstated; keys (N, Nbar).
 TABLE2_S = {(16, 3): 0.5, (32, 3): 3.19, (32, 7): 14.52, (64, 3): 16.2, (64, 7): 73.4, (64, 14): 283.0,
@@ -692,7 +790,7 @@ def main():
                     help="single3d, jvp3d, vjp3d (default 1): loss as an FFT convolution with row-form gain, or the "
                          "line engine (0); bkw (default 0): FFT loss in the single-cell 2D evaluator")
     ap.add_argument("--workload", default="batch2d",
-                    choices=["batch2d", "batch3d", "jvp3d", "vjp3d", "single3d", "rk2", "bkw"])
+                    choices=["batch2d", "batch3d", "jvp3d", "vjp3d", "single3d", "rk2", "bkw", "adaptive"])
     ap.add_argument("--n", type=int, default=64, help="bkw: points per axis")
     ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f32_kahan"], help="bkw: precision")
     ap.add_argument("--rk2-steps", type=int, default=10, help="rk2: time steps per graph launch")
@@ -711,6 +809,8 @@ def main():
         run_rk2_workload(args)
     elif args.workload == "bkw":
         run_bkw_workload(args)
+    elif args.workload == "adaptive":
+        run_adaptive_workload(args)
     elif args.workload != "batch2d":
         run_gpu_workload(args)
     else:

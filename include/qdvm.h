@@ -231,6 +231,35 @@ qdvm_status qdvm_rk2_workspace_single(qdvm_plan_t plan, int prec, size_t* bytes)
 qdvm_status qdvm_rk2(qdvm_plan_t plan, void* f, double dt, int n_steps, int prec, void* workspace,
                      size_t workspace_bytes, void* stream);
 
+/* Space-dependent truncation (Section 3.3: Nbar may vary from cell to cell,
+ * with fewer directions where the distribution is close to equilibrium).
+ *
+ * qdvm_equilibrium_distance: for every cell of a batch (layout as for
+ * qdvm_eval_batched; each cell's plan gives N, d and L), the distance to
+ * the Maxwellian with the cell's own discrete moments (per-point sums in
+ * FP32 with compensation, reduced in FP64: accurate to about 1e-7):
+ *   rho = h^d sum f, u = h^d sum f v / rho, T = (h^d sum f |v|^2 / rho - |u|^2) / d,
+ *   M(v) = rho (2 pi T)^(-d/2) exp(-|v - u|^2 / (2 T)),
+ *   eps = sum |f - M| / sum |f|     (v_j = -L + j h, h = 2L/N),
+ * written to eps (device, n_cells doubles); +inf where rho <= 0, T <= 0 or
+ * sum |f| = 0, and for cells whose plan index is out of range.
+ *
+ * qdvm_select_levels: cell_plan_out[c] = level_plan[cell_base[c] * n_levels
+ * + level] with level = number of thresholds t_k (n_levels - 1 of them,
+ * finite, strictly increasing, HOST array) such that eps[c] >= t_k (NaN
+ * counts as beyond every threshold).  level_plan: HOST array of n_base x
+ * n_levels plan indices (< QDVM_MAX_BATCH_PLANS) into the plans array the
+ * caller then passes to qdvm_eval_batched with cell_plan_out.  Cells whose
+ * base index is outside [0, n_base) get -1 (skipped by the evaluator).
+ * eps, cell_base, cell_plan_out: device.  Both calls are stream-ordered and
+ * capturable (the host tables are copied into the launch).  Errors:
+ * INVALID_ARG for bad counts, tables or NULL arrays. */
+#define QDVM_MAX_LEVELS 8
+qdvm_status qdvm_equilibrium_distance(const qdvm_plan_t* plans, int n_plans, int n_cells, const int* cell_plan,
+                                      const int64_t* cell_offset, const void* f, int prec, double* eps, void* stream);
+qdvm_status qdvm_select_levels(int n_cells, const double* eps, const int* cell_base, int n_base, int n_levels,
+                               const double* thresholds, const int* level_plan, int* cell_plan_out, void* stream);
+
 /* Capture qdvm_rk2_batched (n_steps steps, all pointers fixed) into an
  * executable graph for qdvm_graph_launch: one launch runs the whole loop. */
 qdvm_status qdvm_graph_capture_rk2(qdvm_graph_t* out, const qdvm_plan_t* plans, int n_plans, int n_cells,

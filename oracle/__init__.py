@@ -19,6 +19,9 @@ Functions and the passages they follow:
   transpose of its Jacobian (scattered term by term); ``jvp_points`` /
   ``vjp_points`` the same at selected points (the VJP as a gather).
 * ``moments``                -- mass, momentum and energy of Section 2.1.
+* ``equilibrium_distance``   -- the distance of a cell to the Maxwellian
+  with its own discrete moments, the indicator for a space-dependent Nbar
+  (Section 3.3 leaves the indicator open; this is the reading used).
 * ``rk2(...)``               -- the second-order TVD Runge-Kutta time
   stepping of Section 4 for df/dt = Q(f) (Shu-Osher form), in numpy around
   ``q``.
@@ -172,6 +175,28 @@ def q_points(f, L: float, Nbar: int, idx=None, kernel: str = "unit", Ntilde: int
 
 def q(f, L: float, Nbar: int, kernel: str = "unit", Ntilde: int | None = None) -> dict:
     return q_points(f, L, Nbar, None, kernel, Ntilde)
+
+
+def equilibrium_distance(f, L: float) -> float:
+    """sum |f - M| / sum |f| with M the Maxwellian of the discrete moments
+    rho = h^d sum f, u = h^d sum f v / rho, T = (h^d sum f |v|^2 / rho -
+    |u|^2) / d on the grid v_j = -L + j h; +inf when rho <= 0, T <= 0 or
+    sum |f| = 0."""
+    f = _f64(f)
+    d, N = f.ndim, f.shape[0]
+    h = 2.0 * L / N
+    axes = np.meshgrid(*([-L + h * np.arange(N)] * d), indexing="ij")
+    rho = h ** d * f.sum()
+    if not rho > 0.0:
+        return float("inf")
+    u = [h ** d * (f * v).sum() / rho for v in axes]
+    T = (h ** d * (f * sum(v * v for v in axes)).sum() / rho - sum(x * x for x in u)) / d
+    if not T > 0.0 or not np.isfinite(T):
+        return float("inf")
+    w2 = sum((v - x) ** 2 for v, x in zip(axes, u))
+    M = rho * (2.0 * np.pi * T) ** (-0.5 * d) * np.exp(-w2 / (2.0 * T))
+    den = np.abs(f).sum()
+    return float(np.abs(f - M).sum() / den) if den > 0.0 else float("inf")
 
 
 def rk2(f, L: float, Nbar: int, dt: float, n_steps: int, kernel: str = "unit",

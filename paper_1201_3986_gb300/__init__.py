@@ -90,6 +90,9 @@ _sig("qdvm_rk2_batched", [_P(_vp), _i, _i, _vp, _vp, ctypes.c_int64, _vp, ctypes
                           _vp])
 _sig("qdvm_rk2_workspace_single", [_vp, _i, _P(_sz)])
 _sig("qdvm_rk2", [_vp, _vp, ctypes.c_double, _i, _i, _vp, _sz, _vp])
+_sig("qdvm_equilibrium_distance", [_P(_vp), _i, _i, _vp, _vp, _vp, _i, _vp, _vp])
+_sig("qdvm_select_levels", [_i, _vp, _vp, _i, _i, _P(ctypes.c_double), _P(_i), _vp, _vp])
+QDVM_MAX_LEVELS = 8
 _sig("qdvm_graph_capture_rk2", [_P(_vp), _P(_vp), _i, _i, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_double, _i, _vp,
                                 _i, _vp, _sz])
 QDVM_NOALLOC_MAX_CELLS = 65536
@@ -348,6 +351,38 @@ def qdvm_rk2(plan: Plan, f: torch.Tensor, dt: float, n_steps: int, prec="f64",
     _check(_lib.qdvm_rk2(plan.handle, _ptr(f), float(dt), int(n_steps), p, _ptr(workspace),
                          0 if workspace is None else workspace.numel(), _stream(f.device)), "qdvm_rk2")
     return f
+
+
+def equilibrium_distance(plans, cell_plan: torch.Tensor, cell_offset: torch.Tensor, f: torch.Tensor,
+                         prec="f32_kahan", out: torch.Tensor | None = None) -> torch.Tensor:
+    """Per-cell FP64 distance sum|f - M[f]| / sum|f| to the Maxwellian with
+    the cell's own discrete moments (+inf where undefined)."""
+    p = _prec(prec)
+    n_cells = int(cell_plan.numel())
+    if f.dtype != _DTYPE[p] or not f.is_cuda or not f.is_contiguous():
+        raise ValueError(f"f must be a contiguous CUDA {_DTYPE[p]} tensor")
+    eps = torch.empty(n_cells, dtype=torch.float64, device=f.device) if out is None else out
+    _check(_lib.qdvm_equilibrium_distance(_plan_array(plans), len(plans), n_cells, _ptr(cell_plan), _ptr(cell_offset),
+                                          _ptr(f), p, _ptr(eps), _stream(f.device)), "qdvm_equilibrium_distance")
+    return eps
+
+
+def select_levels(eps: torch.Tensor, cell_base: torch.Tensor, thresholds, level_plan,
+                  out: torch.Tensor | None = None) -> torch.Tensor:
+    """cell_plan[c] = level_plan[cell_base[c]][level], level = number of the
+    (strictly increasing) thresholds that eps[c] reaches."""
+    lp = np.ascontiguousarray(np.asarray(level_plan, dtype=np.int32))
+    if lp.ndim != 2:
+        raise ValueError("level_plan must be a 2-D table (base, level)")
+    thr = np.ascontiguousarray(np.asarray(thresholds, dtype=np.float64).reshape(-1))
+    if thr.size != lp.shape[1] - 1:
+        raise ValueError("need one threshold fewer than levels")
+    n_cells = int(eps.numel())
+    res = torch.empty(n_cells, dtype=torch.int32, device=eps.device) if out is None else out
+    _check(_lib.qdvm_select_levels(n_cells, _ptr(eps), _ptr(cell_base), lp.shape[0], lp.shape[1],
+                                   thr.ctypes.data_as(_P(ctypes.c_double)) if thr.size else None,
+                                   lp.ctypes.data_as(_P(_i)), _ptr(res), _stream(eps.device)), "qdvm_select_levels")
+    return res
 
 
 class RK2Graph:

@@ -139,6 +139,27 @@ def batch_2d(n_cells: int = 4096, Ns=(16, 32, 48, 64), L: float = 8.0, seed: int
     return Batch(2, L, Nc, np.concatenate(parts))
 
 
+def batch_2d_relaxing(n_cells: int = 4096, Ns=(16, 32, 48, 64), L: float = 8.0, seed: int = 3) -> Batch:
+    """Cells at different distances from equilibrium, as in a space-
+    inhomogeneous solve where most of the domain has relaxed: each cell is
+    (1 - w) M(u1, T1) + w M(u2, T2) with drifts U[-1,1]^2, temperatures
+    U[0.5,2] and a second-component weight w = 0.5 U^3 (U uniform on
+    [0, 1]: half the cells have w < 0.0625), unit discrete mass."""
+    rng = np.random.default_rng(seed)
+    Nc = rng.choice(np.asarray(Ns, dtype=np.int64), size=n_cells)
+    parts = []
+    for n in Nc:
+        n = int(n)
+        w = 0.5 * rng.uniform() ** 3
+        f = np.zeros((n, n))
+        for wt in (1.0 - w, w):
+            u = rng.uniform(-1.0, 1.0, size=2)
+            T = rng.uniform(0.5, 2.0)
+            f = f + maxwellian(2, n, L, wt, u, T)
+        parts.append(normalize_mass(f, 2, n, L).ravel())
+    return Batch(2, L, Nc, np.concatenate(parts))
+
+
 def batch_3d(n_cells: int = 256, N: int = 32, L: float = 6.0, seed: int = 1) -> Batch:
     """Cells of a fixed N, each a two-Maxwellian mixture in 3D (drifts
     U[-1,1]^3, temperatures U[0.5,2])."""
