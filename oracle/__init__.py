@@ -19,6 +19,9 @@ Functions and the passages they follow:
   transpose of its Jacobian (scattered term by term); ``jvp_points`` /
   ``vjp_points`` the same at selected points (the VJP as a gather).
 * ``moments``                -- mass, momentum and energy of Section 2.1.
+* ``dtr(...)``               -- the box-truncated operator D^tr of Section
+  2.3 (the same terms, counted only when all four velocities lie in the
+  grid): exactly conservative, not a convolution.
 * ``equilibrium_distance``   -- the distance of a cell to the Maxwellian
   with its own discrete moments, the indicator for a space-dependent Nbar
   (Section 3.3 leaves the indicator open; this is the reading used).
@@ -84,6 +87,9 @@ def _load():
         lib.oracle_q_points.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_double, dbl_p, i64_p, ctypes.c_int64, dbl_p, dbl_p, dbl_p, dbl_p]
         lib.oracle_q_points.restype = ctypes.c_int
+        lib.oracle_dtr.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_double, dbl_p, dbl_p, dbl_p]
+        lib.oracle_dtr.restype = ctypes.c_int
         for name in ("oracle_jvp", "oracle_vjp"):
             fn = getattr(lib, name)
             fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -175,6 +181,19 @@ def q_points(f, L: float, Nbar: int, idx=None, kernel: str = "unit", Ntilde: int
 
 def q(f, L: float, Nbar: int, kernel: str = "unit", Ntilde: int | None = None) -> dict:
     return q_points(f, L, Nbar, None, kernel, Ntilde)
+
+
+def dtr(f, L: float, Nbar: int, kernel: str = "unit", Ntilde: int | None = None) -> dict:
+    """The box-truncated operator D^tr of Section 2.3 with the terms of ``q``:
+    no periodisation, a term counts only when its four velocities lie in
+    the grid.  Returns Q and scale = sum of |terms|."""
+    f = _f64(f)
+    d, N, Nt, m, h = _params(f, L, Nbar, Ntilde)
+    Q, sc = np.zeros_like(f), np.zeros_like(f)
+    rc = _load().oracle_dtr(d, N, Nt, m, KERNELS[kernel], h, _dp(f), _dp(Q), _dp(sc))
+    if rc != 0:
+        raise RuntimeError(f"oracle_dtr failed ({rc})")
+    return {"Q": Q, "scale": sc}
 
 
 def equilibrium_distance(f, L: float) -> float:

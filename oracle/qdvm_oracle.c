@@ -290,6 +290,54 @@ int oracle_q(int d, int N, int Ntilde, int m, int kernel, double h, const double
     return oracle_q_points(d, N, Ntilde, m, kernel, h, f, NULL, 0, Q, gain, loss, scale);
 }
 
+/* Flat index of c + s1 + s2 inside the box [0, N)^d, or -1 outside. */
+static int64_t flat_box(const int* c, const int* s1, const int* s2, int d, int N) {
+    int64_t r = 0;
+    for (int a = 0; a < d; ++a) {
+        int x = c[a] + (s1 ? s1[a] : 0) + (s2 ? s2[a] : 0);
+        if (x < 0 || x >= N) return -1;
+        r = r * N + x;
+    }
+    return r;
+}
+
+/* The box-truncated operator D^tr of Section 2.3 with the same terms as Q
+ * (k, l in [-Ntilde, Ntilde]^d, k.l = 0, k's line in A_m, weight a(k)):
+ * no periodisation, a term counts only when i + k, i + l and i + k + l all
+ * lie in the grid.  Q and scale (sum of |terms|) at every point. */
+int oracle_dtr(int d, int N, int Ntilde, int m, int kernel, double h, const double* f, double* Q,
+               double* scale) {
+    if (check_args(d, N, Ntilde, m)) return -1;
+    term_t* T = NULL;
+    int nt = build_terms(d, Ntilde, m, kernel, h, &T);
+    if (nt < 0) return -2;
+    int64_t total = 1;
+    for (int a = 0; a < d; ++a) total *= N;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < total; ++i) {
+        int c[ORACLE_MAX_D];
+        unflatten(i, d, N, c);
+        nsum_t q = {0, 0}, sc = {0, 0};
+        double fi = f[i];
+        for (int t = 0; t < nt; ++t) {
+            int64_t ik = flat_box(c, T[t].k, NULL, d, N);
+            int64_t il = flat_box(c, T[t].l, NULL, d, N);
+            int64_t ikl = flat_box(c, T[t].k, T[t].l, d, N);
+            if (ik < 0 || il < 0 || ikl < 0) continue;
+            double gain_t = T[t].w * f[ik] * f[il];
+            double loss_t = T[t].w * fi * f[ikl];
+            nsum_add(&q, gain_t);
+            nsum_add(&q, -loss_t);
+            nsum_add(&sc, fabs(gain_t));
+            nsum_add(&sc, fabs(loss_t));
+        }
+        Q[i] = nsum_value(&q);
+        if (scale) scale[i] = nsum_value(&sc);
+    }
+    free(T);
+    return 0;
+}
+
 /* Directional derivative of Q at f along df (Q is quadratic in f):
  *   dQ_i = sum Gamma [df_{i+k} f_{i+l} + f_{i+k} df_{i+l}
  *                     - df_i f_{i+k+l} - f_i df_{i+k+l}],
