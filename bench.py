@@ -585,6 +585,70 @@ def run_adaptive_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def run_dtr_workload(args):
+    """The box-truncated operator D^tr (Section 2.3) term by term on a batch
+    of 2D cells, with its conservation defects, beside the same direct sum
+    with periodic indices and the fast evaluator of the periodised operator
+    on the same batch."""
+    import torch
+
+    import paper_1201_3986_gb300 as q
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    Ns, nb, Lh = (16, 32, 48, 64), 8, 8.0
+    b = synth.batch_2d(args.cells, Ns=Ns, L=Lh, seed=0)
+    plans = [q.Plan(2, n, nb, Lh, kernel="hp") for n in Ns]
+    cp = torch.tensor([Ns.index(int(n)) for n in b.Ns], dtype=torch.int32, device=dev)
+    co = torch.tensor(b.offsets, dtype=torch.int64, device=dev)
+    f = torch.tensor(b.f, dtype=torch.float32, device=dev)
+    Q = torch.empty_like(f)
+    M = torch.empty((b.n_cells, 4), dtype=torch.float64, device=dev)
+    ws = torch.empty(q.batched_workspace_bytes(plans, b.n_cells, "f32_kahan"), dtype=torch.uint8, device=dev)
+
+    def timeit(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st = torch.cuda.current_stream(dev)
+        e0.record(st)
+        for _ in range(args.steps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / args.steps
+
+    with ClockSampler(dev.index) as clk:
+        ms_box = timeit(lambda: q.qdvm_eval_direct_batched(plans, cp, co, f, "f32_kahan", "box", out=Q, moments=M))
+    mom_box = M.cpu().numpy()
+    ms_per = timeit(lambda: q.qdvm_eval_direct_batched(plans, cp, co, f, "f32_kahan", "periodic", out=Q, moments=M))
+    mom_per = M.cpu().numpy()
+    ms_fast = timeit(lambda: q.qdvm_eval_batched(plans, cp, co, f, "f32_kahan", out=Q, moments=M, workspace=ws))
+    # conservation: |moment| relative to the energy-weighted gain of the cell
+    Qb, _ = q.qdvm_eval_direct_batched(plans, cp, co, f, "f32_kahan", "box")
+    absq = torch.zeros(b.n_cells, dtype=torch.float64)
+    Qa = Qb.abs().cpu().numpy().astype(np.float64)
+    h2 = (2 * Lh / b.Ns.astype(np.float64)) ** 2
+    for c in range(b.n_cells):
+        absq[c] = h2[c] * b.cell(c, Qa).sum()
+    ref = absq.numpy()
+    defect = lambda m, k, w: float(np.max(np.abs(m[:, k]) / (w * ref)))
+    line = {"metric": METRIC, "value": b.total / (ms_box / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_box, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"box-truncated D^tr, term by term: {b.n_cells} 2D cells N~U{{16,32,48,64}} "
+                                   f"(seed 0), L=8, Nbar=8, h-scaled weights, FP32 + compensated sums, FP64 moments",
+                       "n_cells": b.n_cells},
+            "direct_periodic_ms": ms_per, "fast_periodic_ms": ms_fast,
+            "conservation_defect_box": {"mass": defect(mom_box, 0, 1.0), "momentum": defect(mom_box, 1, Lh),
+                                        "energy": defect(mom_box, 3, 2 * Lh * Lh)},
+            "conservation_defect_periodic": {"momentum": defect(mom_per, 1, Lh),
+                                             "energy": defect(mom_per, 3, 2 * Lh * Lh)},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 # Table 2 of the paper: CPU time (s) of the fast DVM to T = 1 with dt = 0.01
 # (100 TVD-RK2 steps) on one 2D BKW cell, hardware unstated; keys (N, Nbar).
 TABLE2_S = {(16, 3): 0.5, (32, 3): 3.19, (32, 7): 14.52, (64, 3): 16.2, (64, 7): 73.4, (64, 14): 283.0,
@@ -790,12 +854,12 @@ def main():
                     help="single3d, jvp3d, vjp3d (default 1): loss as an FFT convolution with row-form gain, or the "
                          "line engine (0); bkw (default 0): FFT loss in the single-cell 2D evaluator")
     ap.add_argument("--workload", default="batch2d",
-                    choices=["batch2d", "batch3d", "jvp3d", "vjp3d", "single3d", "rk2", "bkw", "adaptive"])
+                    choices=["batch2d", "batch3d", "jvp3d", "vjp3d", "single3d", "rk2", "bkw", "adaptive", "dtr"])
     ap.add_argument("--n", type=int, default=64, help="bkw: points per axis")
     ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f32_kahan"], help="bkw: precision")
     ap.add_argument("--rk2-steps", type=int, default=10, help="rk2: time steps per graph launch")
     ap.add_argument("--nbar", type=int, default=None)
-    ap.add_argument("--cells", type=int, default=256, help="batch3d / jvp3d / vjp3d: number of 32^3 cells")
+    ap.add_argument("--cells", type=int, default=256, help="batch3d / jvp3d / vjp3d: number of 32^3 cells; dtr: 2D cells")
     ap.add_argument("--tuning", default=None,
                     help="pin the launch configuration instead of autotuning: batch2d threads,direct_j,loss_fft; "
                          "batch3d threads,direct_j,loss_fft,line_chunks")
@@ -811,6 +875,8 @@ def main():
         run_bkw_workload(args)
     elif args.workload == "adaptive":
         run_adaptive_workload(args)
+    elif args.workload == "dtr":
+        run_dtr_workload(args)
     elif args.workload != "batch2d":
         run_gpu_workload(args)
     else:

@@ -260,6 +260,30 @@ qdvm_status qdvm_equilibrium_distance(const qdvm_plan_t* plans, int n_plans, int
 qdvm_status qdvm_select_levels(int n_cells, const double* eps, const int* cell_base, int n_base, int n_levels,
                                const double* thresholds, const int* level_plan, int* cell_plan_out, void* stream);
 
+/* Direct term-by-term evaluation, one thread per output point: every
+ * (k, l) of the restricted operator (k = j e for e in A_m, 0 < |j| <= J_e;
+ * l in the offset list of e, eq. (decDVM); weight c_e), with
+ *   QDVM_BOUNDARY_PERIODIC: the periodised operator of eq. (DR) -- the Q of
+ *     qdvm_eval computed without the line/plane decomposition;
+ *   QDVM_BOUNDARY_BOX: the box-truncated operator D^tr of Section 2.3 -- a
+ *     term counts only when i + k, i + l and i + k + l all lie in the grid.
+ *     D^tr conserves mass, momentum and energy exactly for any f; the box
+ *     couples k and l, so it has no fast (convolution) form.
+ * Cost: one term per (point, k, l); use the fast paths for the periodised
+ * operator.  Batched layout as for qdvm_eval_batched; moments (device,
+ * n_cells x (d + 2), or NULL) receive the FP64 moments of the result.  The
+ * single-cell call needs a 256-byte device workspace
+ * (qdvm_eval_direct_workspace).  Errors: INVALID_ARG for a bad boundary,
+ * precision, counts or NULL arrays. */
+#define QDVM_BOUNDARY_PERIODIC 0
+#define QDVM_BOUNDARY_BOX 1
+qdvm_status qdvm_eval_direct_batched(const qdvm_plan_t* plans, int n_plans, int n_cells, const int* cell_plan,
+                                     const int64_t* cell_offset, const void* f, void* Q, double* moments, int prec,
+                                     int boundary, void* stream);
+qdvm_status qdvm_eval_direct_workspace(size_t* bytes);
+qdvm_status qdvm_eval_direct(qdvm_plan_t plan, const void* f, void* Q, int prec, int boundary, void* workspace,
+                             size_t workspace_bytes, void* stream);
+
 /* Capture qdvm_rk2_batched (n_steps steps, all pointers fixed) into an
  * executable graph for qdvm_graph_launch: one launch runs the whole loop. */
 qdvm_status qdvm_graph_capture_rk2(qdvm_graph_t* out, const qdvm_plan_t* plans, int n_plans, int n_cells,

@@ -93,6 +93,10 @@ _sig("qdvm_rk2", [_vp, _vp, ctypes.c_double, _i, _i, _vp, _sz, _vp])
 _sig("qdvm_equilibrium_distance", [_P(_vp), _i, _i, _vp, _vp, _vp, _i, _vp, _vp])
 _sig("qdvm_select_levels", [_i, _vp, _vp, _i, _i, _P(ctypes.c_double), _P(_i), _vp, _vp])
 QDVM_MAX_LEVELS = 8
+_sig("qdvm_eval_direct_batched", [_P(_vp), _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _i, _vp])
+_sig("qdvm_eval_direct_workspace", [_P(_sz)])
+_sig("qdvm_eval_direct", [_vp, _vp, _vp, _i, _i, _vp, _sz, _vp])
+_BOUNDARY = {"periodic": 0, "box": 1}
 _sig("qdvm_graph_capture_rk2", [_P(_vp), _P(_vp), _i, _i, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_double, _i, _vp,
                                 _i, _vp, _sz])
 QDVM_NOALLOC_MAX_CELLS = 65536
@@ -351,6 +355,40 @@ def qdvm_rk2(plan: Plan, f: torch.Tensor, dt: float, n_steps: int, prec="f64",
     _check(_lib.qdvm_rk2(plan.handle, _ptr(f), float(dt), int(n_steps), p, _ptr(workspace),
                          0 if workspace is None else workspace.numel(), _stream(f.device)), "qdvm_rk2")
     return f
+
+
+def qdvm_eval_direct(plan: Plan, f: torch.Tensor, prec="f64", boundary="box",
+                     out: torch.Tensor | None = None) -> torch.Tensor:
+    """Term-by-term evaluation of one cell: boundary "box" gives the exactly
+    conservative D^tr, "periodic" the periodised Q without the fast
+    decomposition."""
+    p = _prec(prec)
+    if f.dtype != _DTYPE[p] or not f.is_cuda or not f.is_contiguous():
+        raise ValueError(f"f must be a contiguous CUDA {_DTYPE[p]} tensor")
+    Q = torch.empty_like(f) if out is None else out
+    ws = torch.empty(256, dtype=torch.uint8, device=f.device)
+    _check(_lib.qdvm_eval_direct(plan.handle, _ptr(f), _ptr(Q), p, _BOUNDARY[boundary], _ptr(ws), ws.numel(),
+                                 _stream(f.device)), "qdvm_eval_direct")
+    return Q
+
+
+def qdvm_eval_direct_batched(plans, cell_plan: torch.Tensor, cell_offset: torch.Tensor, f: torch.Tensor,
+                             prec="f32_kahan", boundary="box", out: torch.Tensor | None = None,
+                             moments: torch.Tensor | bool | None = True):
+    """Term-by-term evaluation of a ragged batch; returns (Q, moments)."""
+    p = _prec(prec)
+    n_cells = int(cell_plan.numel())
+    if cell_plan.dtype != torch.int32 or cell_offset.dtype != torch.int64:
+        raise ValueError("cell_plan must be int32 and cell_offset int64")
+    if f.dtype != _DTYPE[p] or not f.is_cuda or not f.is_contiguous():
+        raise ValueError(f"f must be a contiguous CUDA {_DTYPE[p]} tensor")
+    Q = torch.empty_like(f) if out is None else out
+    mom = moments if isinstance(moments, torch.Tensor) else (
+        torch.empty((n_cells, plans[0].d + 2), dtype=torch.float64, device=f.device) if moments else None)
+    _check(_lib.qdvm_eval_direct_batched(_plan_array(plans), len(plans), n_cells, _ptr(cell_plan), _ptr(cell_offset),
+                                         _ptr(f), _ptr(Q), _ptr(mom), p, _BOUNDARY[boundary], _stream(f.device)),
+           "qdvm_eval_direct_batched")
+    return Q, mom
 
 
 def equilibrium_distance(plans, cell_plan: torch.Tensor, cell_offset: torch.Tensor, f: torch.Tensor,
