@@ -263,9 +263,10 @@ def run_gpu(args):
     # the library's autotuner picks the launch configuration on this batch;
     # each rotating buffer set is then captured once into a CUDA graph
     if args.tuning:
-        th, dj, fft = (int(v) for v in args.tuning.split(","))
+        vals = [int(v) for v in args.tuning.split(",")]
+        th, dj, fft = vals[:3]
         for p in plans:
-            p.set_tuning(threads=th, direct_j=dj, loss_fft=fft)
+            p.set_tuning(threads=th, direct_j=dj, loss_fft=fft, scan_j=vals[3] if len(vals) > 3 else None)
         tuning = plans[0].tuning()
     else:
         tuning = q.qdvm_tune_batched(plans, cp, co, fs[0], "f32_kahan", workspace=wss)
@@ -861,7 +862,7 @@ def main():
     ap.add_argument("--nbar", type=int, default=None)
     ap.add_argument("--cells", type=int, default=256, help="batch3d / jvp3d / vjp3d: number of 32^3 cells; dtr: 2D cells")
     ap.add_argument("--tuning", default=None,
-                    help="pin the launch configuration instead of autotuning: batch2d threads,direct_j,loss_fft; "
+                    help="pin the launch configuration instead of autotuning: batch2d threads,direct_j,loss_fft[,scan_j]; "
                          "batch3d threads,direct_j,loss_fft,line_chunks")
     args = ap.parse_args()
     if args.warmup < 3:

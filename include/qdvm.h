@@ -66,10 +66,21 @@ typedef enum {
 
 enum { QDVM_KERNEL_UNIT = 0, QDVM_KERNEL_HP = 1 };
 enum { QDVM_F64 = 0, QDVM_F32 = 1, QDVM_F32_KAHAN = 2 };
-/* Line-sum engines.  DIRECT: gathers of each window from an on-chip copy of
- * the cell.  SCAN: running (prefix) sums along the lattice lines of e.
- * AUTO lets the library (and qdvm_tune) choose. */
+/* Line-sum engines of the on-chip 2D evaluator (the windows W_e, the alpha_p
+ * factors of eq. (decDVM)).  DIRECT: each window gathered term by term from
+ * an on-chip copy of the cell (2J loads per point and line).  SCAN: segmented
+ * running sums along the orbits of e on the torus (the lattice lines of
+ * Section 3.2): a thread walks S consecutive points of a line, adding the
+ * entering and subtracting the leaving value (2 loads per point and line
+ * after the first window).  The engine given to qdvm_plan_create_ex sets
+ * the initial qdvm_tuning.scan_j (DIRECT: 0, SCAN: 1, AUTO:
+ * QDVM_SCAN_J_DEFAULT, i.e. DIRECT until qdvm_tune_batched measures
+ * otherwise).  Measured on GB300: SCAN halves the shared-memory traffic of
+ * a pair but adds integer work, so it pays for long windows (J >= 7) and in
+ * the single-cell FP64 evaluation; batched FP32 evaluations with Nbar = 8 are
+ * fastest with DIRECT. */
 enum { QDVM_ENGINE_AUTO = 0, QDVM_ENGINE_DIRECT = 1, QDVM_ENGINE_SCAN = 2 };
+#define QDVM_SCAN_J_DEFAULT 0
 
 /* Maximum number of distinct plans in one batched call. */
 #define QDVM_MAX_BATCH_PLANS 16
@@ -88,12 +99,18 @@ enum { QDVM_ENGINE_AUTO = 0, QDVM_ENGINE_DIRECT = 1, QDVM_ENGINE_SCAN = 2 };
  *               (mixed radix 2/3/4; cells of 16, 32, 48 or 64 points per axis
  *               with the default truncation); the lines then only sum the
  *               gain.  Rounding differs from the direct sums (no longer
- *               bit-exact on integer data).  0: direct sums. */
+ *               bit-exact on integer data).  0: direct sums.
+ *   scan_j      with loss_fft = 1 in the on-chip 2D evaluator (cells of 16,
+ *               32, 48 or 64 points per axis with the default truncation):
+ *               pairs {e, e^perp} with J >= scan_j compute both windows with
+ *               the SCAN engine, the others with DIRECT gathers; 0 = DIRECT
+ *               for every pair.  0 <= scan_j <= 64.  Ignored elsewhere. */
 typedef struct {
     int threads;
     int direct_j;
     int line_chunks;
     int loss_fft;
+    int scan_j;
 } qdvm_tuning;
 
 /* ------------------------------------------------------------------ plans */

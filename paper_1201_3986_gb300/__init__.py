@@ -30,6 +30,7 @@ QDVM_MAX_BATCH_PLANS = 16
 KERNELS = {"unit": QDVM_KERNEL_UNIT, "hp": QDVM_KERNEL_HP}
 PRECS = {"f64": QDVM_F64, "f32": QDVM_F32, "f32_kahan": QDVM_F32_KAHAN}
 ENGINES = {"auto": QDVM_ENGINE_AUTO, "direct": QDVM_ENGINE_DIRECT, "scan": QDVM_ENGINE_SCAN}
+QDVM_SCAN_J_DEFAULT = 0  # initial tuning scan_j of plans created with engine "auto" (qdvm.h)
 _DTYPE = {QDVM_F64: torch.float64, QDVM_F32: torch.float32, QDVM_F32_KAHAN: torch.float32}
 
 
@@ -75,7 +76,12 @@ _sig("qdvm_vjp_batched", [_P(_vp), _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _sz
 _sig("qdvm_moments", [_vp, _vp, _i, _vp, _vp])
 class QdvmTuning(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int), ("direct_j", ctypes.c_int), ("line_chunks", ctypes.c_int),
-                ("loss_fft", ctypes.c_int)]
+                ("loss_fft", ctypes.c_int), ("scan_j", ctypes.c_int)]
+
+
+def _tuning_dict(t) -> dict:
+    return {"threads": t.threads, "direct_j": t.direct_j, "line_chunks": t.line_chunks, "loss_fft": t.loss_fft,
+            "scan_j": t.scan_j}
 
 
 _sig("qdvm_plan_get_tuning", [_vp, _P(QdvmTuning)])
@@ -183,14 +189,15 @@ class Plan:
     def tuning(self) -> dict:
         t = QdvmTuning()
         _check(_lib.qdvm_plan_get_tuning(self.handle, ctypes.byref(t)), "qdvm_plan_get_tuning")
-        return {"threads": t.threads, "direct_j": t.direct_j, "line_chunks": t.line_chunks, "loss_fft": t.loss_fft}
+        return _tuning_dict(t)
 
-    def set_tuning(self, threads=None, direct_j=None, line_chunks=None, loss_fft=None) -> None:
+    def set_tuning(self, threads=None, direct_j=None, line_chunks=None, loss_fft=None, scan_j=None) -> None:
         cur = self.tuning()
         t = QdvmTuning(cur["threads"] if threads is None else int(threads),
                        cur["direct_j"] if direct_j is None else int(direct_j),
                        cur["line_chunks"] if line_chunks is None else int(line_chunks),
-                       cur["loss_fft"] if loss_fft is None else int(loss_fft))
+                       cur["loss_fft"] if loss_fft is None else int(loss_fft),
+                       cur["scan_j"] if scan_j is None else int(scan_j))
         _check(_lib.qdvm_plan_set_tuning(self.handle, ctypes.byref(t)), "qdvm_plan_set_tuning")
 
     @property
@@ -462,7 +469,7 @@ def qdvm_tune_batched(plans, cell_plan: torch.Tensor, cell_offset: torch.Tensor,
     _check(_lib.qdvm_tune_batched(_plan_array(plans), len(plans), n_cells, _ptr(cell_plan), _ptr(cell_offset), _ptr(f),
                                   _ptr(Q), p, _ptr(ws), 0 if ws is None else ws.numel(), _stream(f.device),
                                   ctypes.byref(t)), "qdvm_tune_batched")
-    return {"threads": t.threads, "direct_j": t.direct_j, "line_chunks": t.line_chunks, "loss_fft": t.loss_fft}
+    return _tuning_dict(t)
 
 
 def qdvm_eval_batched_noalloc(plans, cell_plan: torch.Tensor, cell_offset: torch.Tensor, f: torch.Tensor, Q: torch.Tensor,

@@ -202,16 +202,20 @@ extern "C" qdvm_status qdvm_tune_batched(const qdvm_plan_t* plans, int n_plans, 
     std::vector<qdvm_tuning> cand;
     if (all_fused2d(plans, n_plans, d, prec)) {
         for (int th : {256, 512})
-            for (int dj : {0, 1, 2}) cand.push_back(qdvm_tuning{th, dj, saved.line_chunks, 0});
-        for (int th : {256, 512}) cand.push_back(qdvm_tuning{th, saved.direct_j, saved.line_chunks, 1});
+            for (int dj : {0, 1, 2}) cand.push_back(qdvm_tuning{th, dj, saved.line_chunks, 0, saved.scan_j});
+        // FFT loss; the gain windows by DIRECT gathers (scan_j = 0) or by the
+        // SCAN engine from window half-length scan_j up
+        for (int th : {256, 512})
+            for (int sj : {0, 2, 3, 4, 5, 7})
+                cand.push_back(qdvm_tuning{th, saved.direct_j, saved.line_chunks, 1, sj});
     } else {
-        const qdvm_tuning fft{saved.threads, saved.direct_j, 0, 1};
+        const qdvm_tuning fft{saved.threads, saved.direct_j, 0, 1, saved.scan_j};
         const bool f3 = use_fast3d(QDVM_MODE_FWD, b, fft, prec);
         for (int c : {0, 1, 2, 3, 4, 6, 8}) {
             if (engine_workspace(QDVM_MODE_FWD, b, n_cells, prec, false, c) <= ws_bytes)
-                cand.push_back(qdvm_tuning{saved.threads, saved.direct_j, c, 0});
+                cand.push_back(qdvm_tuning{saved.threads, saved.direct_j, c, 0, saved.scan_j});
             if (f3 && fast3d_workspace(QDVM_MODE_FWD, b, n_cells, prec, false, c) <= ws_bytes)
-                cand.push_back(qdvm_tuning{saved.threads, saved.direct_j, c, 1});
+                cand.push_back(qdvm_tuning{saved.threads, saved.direct_j, c, 1, saved.scan_j});
         }
     }
     if (cand.empty()) return qdvm_fail(QDVM_ERR_INVALID_ARG, "workspace too small for every candidate");

@@ -1,0 +1,996 @@
+// Fused 2D evaluation of the restricted periodized DVM operator, one cell per
+// CTA, everything on chip.
+//
+// For a pair of orthogonal lines {e, e^perp} (Remark 3.4(3): in 2D the lines
+// of A_m come in such pairs, with c_e = c_{e^perp} for the unit and
+// Heintz-Panferov weights), eq. (decD) contributes
+//     2 c_e [ W_e(i) W_{e^perp}(i) - f_i V_e(i) ],
+//     W_e(i)  = sum_{0<|j|<=J} f(i + j e)            (alpha_p of eq. (decDVM))
+//     P(i)    = W_{e^perp}(i)                        (alpha'_p: e^perp ∩ box)
+//     V_e(i)  = sum_{0<|j|<=J} P(i + j e)            (beta(L,L) of eq. (betaKL))
+// with J = floor(Ntilde / |e|_inf) for both lines.
+//
+// Layout: the cell is copied into shared memory with a periodic halo of width
+// 2H (H = Ntilde) on every side (padded row stride congruent to N mod 32, see
+// pad2d_stride), so every window gather is base + j*step without any modulo,
+// and a warp of 32 consecutive points reads 32 distinct banks for every
+// direction.  Pairs with J = 1 read V_e straight from the cell at
+// i +- e +- e^perp (|e +- e^perp|_inf <= 2|e|_inf <= 2H) with no barrier.  Each thread owns the points tid + k*blockDim.x and keeps their
+// accumulators in registers for all pairs; P goes through shared memory
+// (with its halo images) because V gathers it along e.
+//
+// With the loss as one FFT convolution per cell (fftloss_body), the pairs
+// only sum the gain 2 c_e W_e W_{e^perp}, and the two windows of a pair come
+// from one of two line-sum engines: DIRECT gathers (2J loads per point and
+// line) or SCAN, segmented running sums along the orbits of e and e^perp on
+// the torus (scan_walks), chosen per pair by the tuning threshold scan_j.
+#pragma once
+
+#include <algorithm>
+
+#include "fft.cuh"
+#include "qdvm_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// Deterministic block reduction of NV doubles per thread; result in out[] of
+// thread 0.  Uses a fixed tree (shuffle-down, then warps in order).
+template <int NV>
+__device__ __forceinline__ void block_reduce_fixed(double (&v)[NV], double* red /* smem, 32*NV */) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) red[wid * NV + i] = v[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += red[w * NV + i];
+            v[i] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// One cell, pairs [pb, pe).  Writes Q (or a partial sum of Q) to qcell and,
+// when mom != nullptr, the FP64 moments of the stored values to mom[0..3].
+template <typename T, bool KAHAN, int PPT>
+__device__ __forceinline__ void fused2d_body(const int N, const int H, const int4* __restrict__ pairs,
+                                             const double* __restrict__ pair_c, const int pb, const int pe,
+                                             const double h, const double L, const T* __restrict__ fcell,
+                                             T* __restrict__ qcell, double* __restrict__ mom, T* __restrict__ sF,
+                                             T* __restrict__ sP, double* red, const int jd) {
+    const int RS = pad2d_stride(N, H), RF = pad2d_rows_f(N, H), HF = 2 * H;
+    const int NT = blockDim.x, tid = threadIdx.x;
+    const int NN = N * N;
+    // P buffer viewed in the f buffer's coordinates (P rows start H rows and
+    // H columns later than f rows)
+    T* const sPf = sP - (H * RS + H);
+
+    // periodic fill of the padded cell, rows/cols [-2H, N+2H)
+    for (int p = tid; p < RF * RF; p += NT) {
+        const int py = p / RF, px = p - py * RF;
+        int sy = py - HF, sx = px - HF;
+        sy += sy < 0 ? N : 0;
+        sy -= sy >= N ? N : 0;
+        sx += sx < 0 ? N : 0;
+        sx -= sx >= N ? N : 0;
+        sF[py * RS + px] = fcell[sy * N + sx];
+    }
+
+    // per owned point: padded address (low 16 bits) and the mask of its halo
+    // images (bits 16..24), or -1 when the slot is past the end of the cell
+    int pk[PPT];
+    T acc[PPT], cmp[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int idx = tid + k * NT;
+        const int y = idx / N, x = idx - (idx / N) * N;
+        int v = -1;
+        if (idx < NN) {
+            // image (dy, dx) of point (y, x) lies in the padded window iff the
+            // shifted coordinates stay in [-H, N+H)
+            const bool oy[3] = {y >= N - H, true, y < H};
+            const bool ox[3] = {x >= N - H, true, x < H};
+            unsigned msk = 0;
+#pragma unroll
+            for (int b = 0; b < 9; ++b)
+                if (b != 4 && oy[b / 3] && ox[b % 3]) msk |= 1u << b;
+            v = (y + HF) * RS + x + HF + (int)(msk << 16);
+        }
+        pk[k] = v;
+        acc[k] = T(0);
+        cmp[k] = T(0);
+    }
+    __syncthreads();
+
+    for (int pr = pb; pr < pe; ++pr) {
+        const int4 e = pairs[pr];
+        const T c2 = (T)(2.0 * pair_c[pr]);
+        const int se = e.x * RS + e.y;   // +e       (axis 0 = rows, axis 1 = columns)
+        const int sp = -e.y * RS + e.x;  // +e^perp = (-e1, e0)
+        const int J = e.z;
+        if (J <= jd) {
+            // short windows: V_e(i) = sum_{j,j'} f(i + j e + j' e^perp) read
+            // directly from the cell ((2J)^2 loads, |j e + j' e^perp|_inf <= 2H)
+            // -- no P buffer, no barrier
+            if (J == 1) {
+                const int d1 = se + sp, d2 = se - sp;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    if (pk[k] >= 0) {
+                        const int a = pk[k] & 0xFFFF;
+                        const T w = sF[a + se] + sF[a - se];
+                        const T pp = sF[a + sp] + sF[a - sp];
+                        const T v = (sF[a + d1] + sF[a - d1]) + (sF[a + d2] + sF[a - d2]);
+                        const T t = c2 * w * pp - c2 * sF[a] * v;
+                        comp_add<T, KAHAN>(acc[k], cmp[k], t);
+                    }
+                }
+            } else {  // J == 2
+                const int se2 = 2 * se, sp2 = 2 * sp;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    if (pk[k] >= 0) {
+                        const int a = pk[k] & 0xFFFF;
+                        const T w = (sF[a + se] + sF[a - se]) + (sF[a + se2] + sF[a - se2]);
+                        const T pp = (sF[a + sp] + sF[a - sp]) + (sF[a + sp2] + sF[a - sp2]);
+                        T v = T(0);
+#pragma unroll
+                        for (int j = 1; j <= 2; ++j) {
+#pragma unroll
+                            for (int jp = 1; jp <= 2; ++jp) {
+                                const int d1 = j * se + jp * sp, d2 = j * se - jp * sp;
+                                v += (sF[a + d1] + sF[a - d1]) + (sF[a + d2] + sF[a - d2]);
+                            }
+                        }
+                        const T t = c2 * w * pp - c2 * sF[a] * v;
+                        comp_add<T, KAHAN>(acc[k], cmp[k], t);
+                    }
+                }
+            }
+            continue;
+        }
+        // (A) W_e and P = W_{e^perp}; j outside, points inside: PPT independent
+        // accumulator pairs per thread
+        T W[PPT], Pv[PPT];
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            W[k] = T(0);
+            Pv[k] = T(0);
+        }
+        for (int j = 1; j <= J; ++j) {
+            const int o = j * se, q = j * sp;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (pk[k] >= 0) {
+                    const int a = pk[k] & 0xFFFF;
+                    W[k] += sF[a + o] + sF[a - o];
+                    Pv[k] += sF[a + q] + sF[a - q];
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            if (pk[k] >= 0) {
+                const int a = pk[k] & 0xFFFF;
+                sPf[a] = Pv[k];
+                unsigned msk = (unsigned)pk[k] >> 16;
+                while (msk) {
+                    const int b = __ffs(msk) - 1;
+                    msk &= msk - 1;
+                    sPf[a + (b / 3 - 1) * N * RS + (b % 3 - 1) * N] = Pv[k];
+                }
+                W[k] = c2 * W[k] * Pv[k];  // gain, 2 c_e W_e W_{e^perp}
+                Pv[k] = T(0);
+            }
+        }
+        __syncthreads();
+        // (B) V_e = window of P along e; loss 2 c_e f V_e
+        for (int j = 1; j <= J; ++j) {
+            const int o = j * se;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (pk[k] >= 0) {
+                    const int a = pk[k] & 0xFFFF;
+                    Pv[k] += sPf[a + o] + sPf[a - o];
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            if (pk[k] >= 0) {
+                const int a = pk[k] & 0xFFFF;
+                const T t = W[k] - c2 * sF[a] * Pv[k];
+                comp_add<T, KAHAN>(acc[k], cmp[k], t);
+            }
+        }
+        __syncthreads();
+    }
+
+    double m[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int idx = tid + k * NT;
+        if (idx < NN) {
+            const T q = KAHAN ? acc[k] + cmp[k] : acc[k];
+            qcell[idx] = q;
+            if (mom) {
+                const int y = idx / N, x = idx - (idx / N) * N;
+                const double v0 = -L + y * h, v1 = -L + x * h, qd = (double)q;
+                m[0] += qd;
+                m[1] += qd * v0;
+                m[2] += qd * v1;
+                m[3] += qd * (v0 * v0 + v1 * v1);
+            }
+        }
+    }
+    if (mom) {
+        block_reduce_fixed<4>(m, red);
+        if (tid == 0) {
+            const double h2 = h * h;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) mom[i] = h2 * m[i];
+        }
+    }
+}
+
+// Cell body specialised for a compile-time N and H = Ntilde (the common cell
+// sizes with the default truncation).  Thread t owns column x = t mod N and
+// rows y0 + k R (R = rows per step), so its k-th point sits k*R*stride words
+// after its first: one address add per window offset serves all of the
+// thread's points, each gather being a load with an immediate offset.
+template <int N, int H>
+struct Geo2 {
+    static constexpr int HF = 2 * H;
+    static constexpr int W = N + 4 * H;
+    static constexpr int RS = W + (((N % 32) - (W % 32) + 32) % 32);
+};
+
+template <typename T, bool KAHAN, int N, int H, int NT>
+__device__ __forceinline__ void fixed_body(const int4* __restrict__ pairs, const double* __restrict__ pair_c,
+                                           const int pb, const int pe, const double h, const double L,
+                                           const T* __restrict__ fcell, T* __restrict__ qcell,
+                                           double* __restrict__ mom, T* __restrict__ sF, T* __restrict__ sP,
+                                           double* red, const int jd) {
+    using G = Geo2<N, H>;
+    constexpr int RS = G::RS, HF = G::HF, WF = G::W;
+    constexpr int R = (NT / N < N) ? NT / N : N;  // rows per step
+    constexpr int PPT = (N + R - 1) / R;          // points per thread
+    constexpr int ACT = R * N;                    // threads that own points
+    constexpr int DK = R * RS;                    // address step between a thread's points
+    constexpr bool PARTIAL = (N % R) != 0;
+    static_assert(pad2d_rows_f(N, H) == WF, "layout");
+    const int tid = threadIdx.x;
+    T* const sPf = sP - (H * RS + H);
+
+    for (int p = tid; p < WF * WF; p += NT) {
+        const int py = p / WF, px = p - py * WF;
+        int sy = py - HF, sx = px - HF;
+        sy += sy < 0 ? N : 0;
+        sy -= sy >= N ? N : 0;
+        sx += sx < 0 ? N : 0;
+        sx -= sx >= N ? N : 0;
+        sF[py * RS + px] = fcell[sy * N + sx];
+    }
+    const bool active = tid < ACT;
+    const int x = tid % N, y0 = tid / N;
+    const int a0 = (y0 + HF) * RS + x + HF;
+    const bool last_ok = !PARTIAL || (y0 + (PPT - 1) * R < N);
+    const int ax = x < H ? N : (x >= N - H ? -N : 0);  // column image offset of P
+    T acc[PPT], cmp[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        acc[k] = T(0);
+        cmp[k] = T(0);
+    }
+    __syncthreads();
+
+    for (int pr = pb; pr < pe; ++pr) {
+        const int4 e = pairs[pr];
+        const T c2 = (T)(2.0 * pair_c[pr]);
+        const int se = e.x * RS + e.y;
+        const int sp = -e.y * RS + e.x;
+        const int J = e.z;
+        if (J <= jd) {
+            if (active) {
+                T w[PPT], pp[PPT], v[PPT];
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) w[k] = pp[k] = v[k] = T(0);
+                const T* b;
+#define QDVM_GATHER(arr, off)                                                           \
+    b = sF + a0 + (off);                                                                \
+    _Pragma("unroll") for (int k = 0; k < PPT; ++k) if (k < PPT - 1 || last_ok) arr[k] += b[k * DK];
+                for (int j = 1; j <= J; ++j) {
+                    QDVM_GATHER(w, j * se)
+                    QDVM_GATHER(w, -j * se)
+                    QDVM_GATHER(pp, j * sp)
+                    QDVM_GATHER(pp, -j * sp)
+                    for (int jp = 1; jp <= J; ++jp) {
+                        QDVM_GATHER(v, j * se + jp * sp)
+                        QDVM_GATHER(v, -j * se - jp * sp)
+                        QDVM_GATHER(v, j * se - jp * sp)
+                        QDVM_GATHER(v, -j * se + jp * sp)
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    if (k < PPT - 1 || last_ok) {
+                        const T t = c2 * w[k] * pp[k] - c2 * sF[a0 + k * DK] * v[k];
+                        comp_add<T, KAHAN>(acc[k], cmp[k], t);
+                    }
+                }
+            }
+            continue;
+        }
+        // (A) W_e and P = W_{e^perp} into registers and the P buffer
+        T W[PPT], Pv[PPT];
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) W[k] = Pv[k] = T(0);
+        if (active) {
+            const T* b;
+            for (int j = 1; j <= J; ++j) {
+                QDVM_GATHER(W, j * se)
+                QDVM_GATHER(W, -j * se)
+                QDVM_GATHER(Pv, j * sp)
+                QDVM_GATHER(Pv, -j * sp)
+            }
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (k < PPT - 1 || last_ok) {
+                    const int y = y0 + k * R;
+                    const int a = a0 + k * DK;
+                    const int ay = y < H ? N * RS : (y >= N - H ? -N * RS : 0);
+                    sPf[a] = Pv[k];
+                    if (ay) sPf[a + ay] = Pv[k];
+                    if (ax) sPf[a + ax] = Pv[k];
+                    if (ay && ax) sPf[a + ay + ax] = Pv[k];
+                    W[k] = c2 * W[k] * Pv[k];
+                    Pv[k] = T(0);
+                }
+            }
+        }
+        __syncthreads();
+        // (B) V_e = window of P along e
+        if (active) {
+            const T* b;
+            for (int j = 1; j <= J; ++j) {
+                b = sPf + a0 + j * se;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k)
+                    if (k < PPT - 1 || last_ok) Pv[k] += b[k * DK];
+                b = sPf + a0 - j * se;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k)
+                    if (k < PPT - 1 || last_ok) Pv[k] += b[k * DK];
+            }
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (k < PPT - 1 || last_ok) {
+                    const T t = W[k] - c2 * sF[a0 + k * DK] * Pv[k];
+                    comp_add<T, KAHAN>(acc[k], cmp[k], t);
+                }
+            }
+        }
+        __syncthreads();
+    }
+#undef QDVM_GATHER
+
+    double m[4] = {0.0, 0.0, 0.0, 0.0};
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            if (k < PPT - 1 || last_ok) {
+                const int y = y0 + k * R;
+                const T q = KAHAN ? acc[k] + cmp[k] : acc[k];
+                qcell[y * N + x] = q;
+                if (mom) {
+                    const double v0 = -L + y * h, v1 = -L + x * h, qd = (double)q;
+                    m[0] += qd;
+                    m[1] += qd * v0;
+                    m[2] += qd * v1;
+                    m[3] += qd * (v0 * v0 + v1 * v1);
+                }
+            }
+        }
+    }
+    if (mom) {
+        block_reduce_fixed<4>(m, red);
+        if (tid == 0) {
+            const double h2 = h * h;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) mom[i] = h2 * m[i];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// Loss as one convolution (the paper's remark that the loss part is a plain
+// convolution): sum_e c_e V_e(i) = sum_m K(m) f(i + m) = (K * f)(i), K the
+// weighted displacement histogram of the terms (plan table, transformed).
+// An on-chip 2D FFT (Stockham, mixed radix 2/3/4, ping-pong between two
+// N x (N+1) complex buffers) gives K * f for the whole cell; the pair loop
+// then only sums the gain 2 c_e W_e W_{e^perp} -- no P buffer, no barrier.
+
+// One Stockham pass of radix R over all N lines (rows, or columns with
+// COLS), NS = product of the radices already applied.  Butterfly b works on
+// line b % N, so a warp touches consecutive lines (row stride LD = N + 1
+// complex: no bank conflicts on columns or rows).
+template <typename C, int N, int LD, int R, int NS, bool INV, bool COLS>
+__device__ __forceinline__ void fft_pass(const C* __restrict__ src, C* __restrict__ dst, const C* __restrict__ tw) {
+    constexpr int NB = N / R;
+    for (int b = threadIdx.x; b < N * NB; b += blockDim.x) {
+        const int line = b % N, j = b / N;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int e = j + r * NB;
+            v[r] = src[COLS ? e * LD + line : line * LD + e];
+        }
+        const int jm = j % NS;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            C w = tw[(jm * (N / (NS * R)) * r) % N];
+            if (INV) w.y = -w.y;
+            v[r] = cmul(v[r], w);
+        }
+        dft_small<R, INV>(v);
+        const int idxD = (j / NS) * NS * R + jm;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int e = idxD + r * NS;
+            dst[COLS ? e * LD + line : line * LD + e] = v[r];
+        }
+    }
+}
+
+template <typename C, int N, int LD, bool INV, bool COLS, int NS, int R, int... Rs>
+__device__ __forceinline__ C* fft_passes(C* a, C* b, const C* tw) {
+    fft_pass<C, N, LD, R, NS, INV, COLS>(a, b, tw);
+    __syncthreads();
+    if constexpr (sizeof...(Rs) > 0)
+        return fft_passes<C, N, LD, INV, COLS, NS * R, Rs...>(b, a, tw);
+    else
+        return b;
+}
+
+// All N line transforms of length N; returns the buffer holding the result.
+template <typename C, int N, int LD, bool INV, bool COLS>
+__device__ __forceinline__ C* fft_lines(C* a, C* b, const C* tw) {
+    if constexpr (N == 64) return fft_passes<C, N, LD, INV, COLS, 1, 4, 4, 4>(a, b, tw);
+    else if constexpr (N == 48) return fft_passes<C, N, LD, INV, COLS, 1, 3, 4, 4>(a, b, tw);
+    else if constexpr (N == 32) return fft_passes<C, N, LD, INV, COLS, 1, 2, 4, 4>(a, b, tw);
+    else return fft_passes<C, N, LD, INV, COLS, 1, 4, 4>(a, b, tw);  // N == 16
+}
+
+// Layouts of the FFT body.  Without the SCAN engine: the cell with a
+// periodic halo of width H (all the direct gathers need), then two
+// N x (N+1) complex FFT buffers.  With it: a running-sum segment reaches
+// (S - 1 + 2J)|e|_inf <= 4H rows or columns across, so the cell carries a
+// 2H halo, followed by the two N x N window fields; the FFT buffers of the
+// loss phase alias both (a cell of 64^2 FP32 fits twice per SM either way).
+template <int N, int H, bool SCAN>
+struct GeoF {
+    static constexpr int HW = SCAN ? 2 * H : H;  // halo width of the cell copy
+    static constexpr int W = N + 2 * HW;
+    static constexpr int RS = W + (((N % 32) - (W % 32) + 32) % 32);
+    static constexpr int LD = N + 1;
+};
+
+template <typename T, int N, int H, bool SCAN>
+__host__ __device__ constexpr size_t cell_bytes() {
+    return ((size_t)GeoF<N, H, SCAN>::W * GeoF<N, H, SCAN>::RS * sizeof(T) + 15) / 16 * 16;
+}
+
+// Scan engine: R_v(i) = sum_{|j| <= J} f(i + j v) for v = e and v = e^perp
+// (the window W_v plus the centre) into sRe and sRp (N x N, row-major).
+// The torus is cut along each line into segments of S consecutive points:
+// with the complement w of v (det[v w] = 1), segment (k, beta) is
+// {(kS + t) v + beta w : 0 <= t < S}, and the N^2/S segments of v tile Z_N^2.
+// A thread takes a segment, sums its first window (2J + 1 loads), then
+// slides: R += f(i + (J+1) v) - f(i - J v).  The segment's base is placed
+// at the periodic image that keeps every load inside the 2H halo.
+// Consecutive threads take consecutive beta, whose bases differ by w; w has
+// an odd column component, so for N = 32, 64 (row strides = 0 mod 32) a
+// warp's loads and stores hit 32 distinct banks.
+// One running-sum segment in flight: read pointers, canonical write
+// position and the running value.
+template <typename T>
+struct ScanWalk {
+    const T* lead;
+    const T* trail;
+    T* out;
+    int yw, xw, vy, vx;
+    T R;
+};
+
+template <typename T, int N, int H>
+__device__ __forceinline__ ScanWalk<T> scan_start(const T* __restrict__ sF, T* sRe, T* sRp, const int4 e, const int4 w,
+                                                  const int u, const int nseg) {
+    using G = GeoF<N, H, true>;
+    constexpr int RS = G::RS, HF = G::HW;
+    const int J = e.z, S = e.w;
+    const bool perp = u >= nseg;
+    const int g = perp ? u - nseg : u;
+    ScanWalk<T> s;
+    s.vy = perp ? -e.y : e.x;
+    s.vx = perp ? e.x : e.y;
+    const int wy = perp ? w.z : w.x, wx = perp ? w.w : w.y;
+    const int beta = g % N, a = (g / N) * S;
+    int by = (a * s.vy + beta * wy) % N;
+    by += by < 0 ? N : 0;
+    int bx = (a * s.vx + beta * wx) % N;
+    bx += bx < 0 ? N : 0;
+    // steps t in [-J, S - 1 + J] are read
+    const int y0 = -J * s.vy, y1 = (S - 1 + J) * s.vy, x0 = -J * s.vx, x1 = (S - 1 + J) * s.vx;
+    int ry = by, rx = bx;
+    if (ry + max(y0, y1) > N + HF - 1) ry -= N;
+    else if (ry + min(y0, y1) < -HF) ry += N;
+    if (rx + max(x0, x1) > N + HF - 1) rx -= N;
+    else if (rx + min(x0, x1) < -HF) rx += N;
+    const int sv = s.vy * RS + s.vx;
+    const T* c = sF + (ry + HF) * RS + (rx + HF);
+    T R0 = c[0], R1 = T(0);
+#pragma unroll 4
+    for (int j = 1; j <= J; ++j) {
+        R0 += c[j * sv];
+        R1 += c[-j * sv];
+    }
+    s.R = R0 + R1;
+    s.out = perp ? sRp : sRe;
+    s.yw = by;
+    s.xw = bx;
+    s.out[by * N + bx] = s.R;
+    s.lead = c + (J + 1) * sv;
+    s.trail = c - J * sv;
+    return s;
+}
+
+template <typename T, int N, int RS>
+__device__ __forceinline__ void scan_step(ScanWalk<T>& s) {
+    const int sv = s.vy * RS + s.vx;
+    s.R += *s.lead - *s.trail;
+    s.lead += sv;
+    s.trail += sv;
+    s.yw += s.vy;
+    s.yw -= s.yw >= N ? N : 0;
+    s.yw += s.yw < 0 ? N : 0;
+    s.xw += s.vx;
+    s.xw -= s.xw >= N ? N : 0;
+    s.xw += s.xw < 0 ? N : 0;
+    s.out[s.yw * N + s.xw] = s.R;
+}
+
+// Scan engine: R_v(i) = sum_{|j| <= J} f(i + j v) for v = e and v = e^perp
+// (the window W_v plus the centre) into sRe and sRp (N x N, row-major).
+// The torus is cut along each line into segments of S consecutive points:
+// with the complement w of v (det[v w] = 1), segment (k, beta) is
+// {(kS + t) v + beta w : 0 <= t < S}, and the N^2/S segments of v tile Z_N^2.
+// A thread takes a segment, sums its first window (2J + 1 loads), then
+// slides: R += f(i + (J+1) v) - f(i - J v).  The segment's base is placed
+// at the periodic image that keeps every load inside the 2H halo.
+// Consecutive threads take consecutive beta, whose bases differ by w; w has
+// an odd column component, so for N = 32, 64 (row strides = 0 mod 32) a
+// warp's loads and stores hit 32 distinct banks.  A thread advances two of
+// its segments side by side (two independent running sums).
+template <typename T, int N, int H, int NT>
+__device__ __forceinline__ void scan_walks(const T* __restrict__ sF, T* __restrict__ sRe, T* __restrict__ sRp,
+                                           const int4 e, const int4 w) {
+    constexpr int RS = GeoF<N, H, true>::RS;
+    const int S = e.w;
+    const int nseg = N * N / S, items = 2 * nseg;
+    int u = threadIdx.x;
+    for (; u + NT < items; u += 2 * NT) {
+        ScanWalk<T> a = scan_start<T, N, H>(sF, sRe, sRp, e, w, u, nseg);
+        ScanWalk<T> b = scan_start<T, N, H>(sF, sRe, sRp, e, w, u + NT, nseg);
+#pragma unroll 2
+        for (int t = 1; t < S; ++t) {
+            scan_step<T, N, RS>(a);
+            scan_step<T, N, RS>(b);
+        }
+    }
+    if (u < items) {
+        ScanWalk<T> a = scan_start<T, N, H>(sF, sRe, sRp, e, w, u, nseg);
+#pragma unroll 4
+        for (int t = 1; t < S; ++t) scan_step<T, N, RS>(a);
+    }
+}
+
+// SCAN: pairs with J >= scan_j take the SCAN engine (the caller instantiates
+// SCAN = true only when some pair of the cell does); the others, and every
+// pair when !SCAN, gather their windows directly.
+template <typename T, bool KAHAN, int N, int H, int NT, bool SCAN>
+__device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, const int pe, const T* __restrict__ fcell,
+                                             T* __restrict__ qcell, double* __restrict__ mom, unsigned char* smem,
+                                             double* red, const bool do_loss, const int scan_j) {
+    using C = typename Cplx<T>::type;
+    using G = GeoF<N, H, SCAN>;
+    constexpr int W = G::W, RS = G::RS, HW = G::HW, LD = G::LD;
+    constexpr int R = (NT / N < N) ? NT / N : N;
+    constexpr int PPT = (N + R - 1) / R;
+    constexpr int ACT = R * N;
+    constexpr int DK = R * RS;
+    constexpr int DH = R * N;  // address step between a thread's points in the window fields
+    constexpr bool PARTIAL = (N % R) != 0;
+    const int tid = threadIdx.x;
+    T* sF = reinterpret_cast<T*>(smem);
+    T* sRe = reinterpret_cast<T*>(smem + cell_bytes<T, N, H, SCAN>());
+    T* sRp = sRe + N * N;
+    C* A = reinterpret_cast<C*>(SCAN ? smem : smem + cell_bytes<T, N, H, SCAN>());
+    C* B = A + N * LD;
+    const C* tw;
+    const T* kh;
+    if constexpr (sizeof(T) == 8) {
+        tw = reinterpret_cast<const C*>(P.tw);
+        kh = reinterpret_cast<const T*>(P.khat);
+    } else {
+        tw = reinterpret_cast<const C*>(P.tw_f);
+        kh = reinterpret_cast<const T*>(P.khat_f);
+    }
+
+    const bool active = tid < ACT;
+    const int x = tid % N, y0 = tid / N;
+    const int a0 = (y0 + HW) * RS + x + HW;
+    const bool last_ok = !PARTIAL || (y0 + (PPT - 1) * R < N);
+    T acc[PPT], cmp[PPT];
+
+    // the direct gathers of the gain's two windows, 2 c_e W_e W_{e^perp}
+    auto gain_direct = [&](const int4 e, const T c2) {
+        const int se = e.x * RS + e.y;
+        const int sp = -e.y * RS + e.x;
+        T w[PPT], pp[PPT];
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) w[k] = pp[k] = T(0);
+        const T* b;
+        for (int j = 1; j <= e.z; ++j) {
+#define QDVM_GATHER(arr, off)                                                                \
+    b = sF + a0 + (off);                                                                     \
+    _Pragma("unroll") for (int k = 0; k < PPT; ++k) if (k < PPT - 1 || last_ok) arr[k] += b[k * DK];
+            QDVM_GATHER(w, j * se)
+            QDVM_GATHER(w, -j * se)
+            QDVM_GATHER(pp, j * sp)
+            QDVM_GATHER(pp, -j * sp)
+#undef QDVM_GATHER
+        }
+#pragma unroll
+        for (int k = 0; k < PPT; ++k)
+            if (k < PPT - 1 || last_ok) comp_add<T, KAHAN>(acc[k], cmp[k], c2 * w[k] * pp[k]);
+    };
+    // the loss -f (K * f) from the FFT buffers A, B (K's transform in kh);
+    // fk(k) gives f at the k-th owned point
+    auto loss_fft = [&](auto fk) {
+        C* r = fft_lines<C, N, LD, false, false>(A, B, tw);
+        r = fft_lines<C, N, LD, false, true>(r, r == A ? B : A, tw);
+        for (int i = tid; i < N * N; i += NT) {
+            C& z = r[(i / N) * LD + (i % N)];
+            const T k = kh[i];
+            z.x *= k;
+            z.y *= k;
+        }
+        __syncthreads();
+        r = fft_lines<C, N, LD, true, true>(r, r == A ? B : A, tw);
+        r = fft_lines<C, N, LD, true, false>(r, r == A ? B : A, tw);
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (k < PPT - 1 || last_ok) {
+                    const int y = y0 + k * R;
+                    acc[k] = -fk(k) * r[y * LD + x].x;
+                }
+            }
+        }
+    };
+    auto fill_cell = [&]() {
+        for (int p = tid; p < W * W; p += NT) {
+            const int py = p / W, px = p - py * W;
+            int sy = py - HW, sx = px - HW;
+            sy += sy < 0 ? N : 0;
+            sy -= sy >= N ? N : 0;
+            sx += sx < 0 ? N : 0;
+            sx -= sx >= N ? N : 0;
+            sF[py * RS + px] = fcell[sy * N + sx];
+        }
+    };
+
+    if constexpr (!SCAN) {
+        fill_cell();
+        if (do_loss)
+            for (int i = tid; i < N * N; i += NT) A[(i / N) * LD + (i % N)] = C{fcell[i], T(0)};
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            acc[k] = T(0);
+            cmp[k] = T(0);
+        }
+        if (do_loss) loss_fft([&](int k) { return sF[a0 + k * DK]; });
+        if (active) {
+            for (int pr = pb; pr < pe; ++pr) gain_direct(P.pairs[pr], (T)(2.0 * P.pair_c[pr]));
+        }
+    } else {
+        // the FFT buffers occupy the cell's place: f at the owned points is
+        // read before the FFT (the loss and the running sums' centres need
+        // it), the cell is copied after it
+        const int h0 = y0 * N + x;
+        T fh[PPT];
+        if (do_loss)
+            for (int i = tid; i < N * N; i += NT) A[(i / N) * LD + (i % N)] = C{fcell[i], T(0)};
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            fh[k] = (active && (k < PPT - 1 || last_ok)) ? fcell[(y0 + k * R) * N + x] : T(0);
+            acc[k] = T(0);
+            cmp[k] = T(0);
+        }
+        __syncthreads();
+        if (do_loss) {
+            loss_fft([&](int k) { return fh[k]; });
+            __syncthreads();
+        }
+        fill_cell();
+        __syncthreads();
+        bool pending = false;  // window fields still being read by the previous scanned pair
+        for (int pr = pb; pr < pe; ++pr) {
+            const int4 e = P.pairs[pr];
+            const T c2 = (T)(2.0 * P.pair_c[pr]);
+            if (e.z >= scan_j && e.w > 0) {
+                if (pending) __syncthreads();
+                scan_walks<T, N, H, NT>(sF, sRe, sRp, e, P.pair_scan[pr]);
+                __syncthreads();
+                if (active) {
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) {
+                        if (k < PPT - 1 || last_ok) {
+                            const T we = sRe[h0 + k * DH] - fh[k], wp = sRp[h0 + k * DH] - fh[k];
+                            comp_add<T, KAHAN>(acc[k], cmp[k], c2 * we * wp);
+                        }
+                    }
+                }
+                pending = true;
+            } else if (active) {
+                gain_direct(e, c2);
+            }
+        }
+    }
+
+    double m[4] = {0.0, 0.0, 0.0, 0.0};
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            if (k < PPT - 1 || last_ok) {
+                const int y = y0 + k * R;
+                const T q = KAHAN ? acc[k] + cmp[k] : acc[k];
+                qcell[y * N + x] = q;
+                if (mom) {
+                    const double v0 = -P.L + y * P.h, v1 = -P.L + x * P.h, qd = (double)q;
+                    m[0] += qd;
+                    m[1] += qd * v0;
+                    m[2] += qd * v1;
+                    m[3] += qd * (v0 * v0 + v1 * v1);
+                }
+            }
+        }
+    }
+    if (mom) {
+        block_reduce_fixed<4>(m, red);
+        if (tid == 0) {
+            const double h2 = P.h * P.h;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) mom[i] = h2 * m[i];
+        }
+    }
+}
+
+// elements of the f buffer; the P buffer follows it
+__host__ __device__ inline size_t buf_f_elems(int N, int H) {
+    return (size_t)pad2d_rows_f(N, H) * (size_t)pad2d_stride(N, H);
+}
+__host__ __device__ inline size_t buf_p_elems(int N, int H) {
+    return (size_t)pad2d_rows_p(N, H) * (size_t)pad2d_stride(N, H);
+}
+
+// Points per thread instantiated for a CTA of NT threads (cells up to 64^2).
+template <int NT>
+__host__ __device__ constexpr int ppt_max() { return NT == 256 ? 16 : 8; }
+__host__ __device__ inline int ppt_pick(int NT, int need) {
+    if (NT == 256) return need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : need <= 9 ? 9 : 16;
+    return need <= 1 ? 1 : need <= 2 ? 2 : need <= 5 ? 5 : 8;
+}
+
+// One cell with the smallest body that covers it (no predicated-off slots).
+template <typename T, bool KAHAN, int NT>
+__device__ __forceinline__ void run_cell(const PlanDev& P, int pb, int pe, const T* f, T* q, double* mom, T* sF, T* sP,
+                                         double* red, int jd, int fft, int sj, bool do_loss) {
+    // the common cell sizes with the default truncation floor(N/(3+sqrt 2))
+#define QDVM_FIXED(NN, HH)                                                                                        \
+    if (P.N == NN && P.Ntilde == HH) {                                                                            \
+        if (fft && P.khat) {                                                                                      \
+            unsigned char* sm = reinterpret_cast<unsigned char*>(sF);                                             \
+            if (sj > 0 && sj <= HH)                                                                               \
+                fftloss_body<T, KAHAN, NN, HH, NT, true>(P, pb, pe, f, q, mom, sm, red, do_loss, sj);             \
+            else                                                                                                  \
+                fftloss_body<T, KAHAN, NN, HH, NT, false>(P, pb, pe, f, q, mom, sm, red, do_loss, 0);             \
+        } else {                                                                                                  \
+            fixed_body<T, KAHAN, NN, HH, NT>(P.pairs, P.pair_c, pb, pe, P.h, P.L, f, q, mom, sF, sP, red, jd);   \
+        }                                                                                                         \
+        return;                                                                                                   \
+    }
+    QDVM_FIXED(64, 14)
+    QDVM_FIXED(48, 10)
+    QDVM_FIXED(32, 7)
+    QDVM_FIXED(16, 3)
+#undef QDVM_FIXED
+    const int k = ppt_pick(NT, (P.N * P.N + NT - 1) / NT);
+#define QDVM_BODY(K)                                                                                          \
+    fused2d_body<T, KAHAN, K>(P.N, P.Ntilde, P.pairs, P.pair_c, pb, pe, P.h, P.L, f, q, mom, sF, sP, red, jd); \
+    return
+    if (NT == 256) {
+        if (k == 1) { QDVM_BODY(1); }
+        if (k == 2) { QDVM_BODY(2); }
+        if (k == 4) { QDVM_BODY(4); }
+        if (k == 9) { QDVM_BODY(9); }
+        QDVM_BODY(ppt_max<NT>());
+    } else {
+        if (k == 1) { QDVM_BODY(1); }
+        if (k == 2) { QDVM_BODY(2); }
+        if (k == 5) { QDVM_BODY(5); }
+        QDVM_BODY(ppt_max<NT>());
+    }
+#undef QDVM_BODY
+}
+
+template <typename T, bool KAHAN, int NT>
+__global__ void __launch_bounds__(NT, 2) k_fused2d_single(PlanDev P, const T* __restrict__ f, T* __restrict__ out,
+                                                          int pairs_per_cta, size_t slot_stride, int jd, int fft,
+                                                          int sj) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32 * 4];
+    T* sF = reinterpret_cast<T*>(smem_raw);
+    T* sP = sF + buf_f_elems(P.N, P.Ntilde);
+    const int pb = blockIdx.x * pairs_per_cta;
+    const int pe = min(pb + pairs_per_cta, P.n_pairs);
+    run_cell<T, KAHAN, NT>(P, pb, pe, f, out + blockIdx.x * slot_stride, nullptr, sF, sP, red, jd, fft, sj,
+                           blockIdx.x == 0);
+}
+
+// Deterministic sum of S partial results (fixed order s = 0..S-1).
+template <typename T, bool KAHAN>
+__global__ void k_reduce_partials(const T* __restrict__ part, int S, int n, T* __restrict__ Q) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T s = T(0), c = T(0);
+    for (int k = 0; k < S; ++k) comp_add<T, KAHAN>(s, c, part[(size_t)k * n + i]);
+    Q[i] = KAHAN ? s + c : s;
+}
+
+template <typename T, bool KAHAN, int NT>
+__global__ void __launch_bounds__(NT, 2) k_fused2d_batched(BatchDev B, int n_cells, const int* __restrict__ cell_plan,
+                                                           const int64_t* __restrict__ cell_offset,
+                                                           const int* __restrict__ order, int* counter,
+                                                           const T* __restrict__ f, T* __restrict__ Q,
+                                                           double* __restrict__ moments, int jd, int fft, int sj) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32 * 4];
+    __shared__ int s_cell;
+    __shared__ PlanDev s_plan;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int c = atomicAdd(counter, 1);
+            s_cell = c < n_cells ? order[c] : -1;
+            if (s_cell >= 0) {
+                const int pi = cell_plan[s_cell];
+#pragma unroll
+                for (int q = 0; q < QDVM_MAX_BATCH_PLANS; ++q)
+                    if (q == pi) s_plan = B.p[q];
+            }
+        }
+        __syncthreads();
+        const int cell = s_cell;
+        if (cell < 0) break;
+        const PlanDev P = s_plan;
+        const int64_t off = cell_offset[cell];
+        T* sF = reinterpret_cast<T*>(smem_raw);
+        T* sP = sF + buf_f_elems(P.N, P.Ntilde);
+        run_cell<T, KAHAN, NT>(P, 0, P.n_pairs, f + off, Q + off, moments ? moments + (size_t)cell * 4 : nullptr, sF,
+                               sP, red, jd, fft, sj, true);
+        __syncthreads();
+    }
+}
+
+template <typename T, bool KAHAN, int NT>
+qdvm_status launch_single_t(const qdvm_plan_s* p, const T* f, T* Q, T* part, int S, int ppc, size_t smem, int jd,
+                            int fft, int sj, cudaStream_t st) {
+    cudaFuncSetAttribute(k_fused2d_single<T, KAHAN, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const PlanDev P = plan_dev(p);
+    const int n = p->N * p->N;
+    if (S == 1) {
+        k_fused2d_single<T, KAHAN, NT><<<1, NT, smem, st>>>(P, f, Q, ppc, 0, jd, fft, sj);
+    } else {
+        k_fused2d_single<T, KAHAN, NT><<<S, NT, smem, st>>>(P, f, part, ppc, (size_t)n, jd, fft, sj);
+        k_reduce_partials<T, KAHAN><<<(n + 255) / 256, 256, 0, st>>>(part, S, n, Q);
+    }
+    QDVM_LAUNCH_CHECK("fused2d single-cell launch");
+    return QDVM_OK;
+}
+
+template <typename T, bool KAHAN>
+qdvm_status dispatch_single(const qdvm_plan_s* p, const void* f, void* Q, void* ws, int S, int ppc, size_t smem,
+                            cudaStream_t st) {
+    const T* fi = static_cast<const T*>(f);
+    T* qo = static_cast<T*>(Q);
+    T* part = static_cast<T*>(ws);
+    const int jd = p->tune.direct_j, fft = p->tune.loss_fft, sj = p->tune.scan_j;
+    if (p->tune.threads == 512)
+        return launch_single_t<T, KAHAN, 512>(p, fi, qo, part, S, ppc, smem, jd, fft, sj, st);
+    return launch_single_t<T, KAHAN, 256>(p, fi, qo, part, S, ppc, smem, jd, fft, sj, st);
+}
+
+inline void split_pairs(int n_pairs, int max_ctas, int* S, int* ppc) {
+    int s = std::max(1, std::min(n_pairs, max_ctas));
+    int per = (n_pairs + s - 1) / s;
+    *ppc = per;
+    *S = (n_pairs + per - 1) / per;
+}
+
+template <typename T, bool KAHAN, int NT>
+qdvm_status launch_batched_t(const BatchDev& b, int n_cells, const int* cell_plan, const int64_t* cell_offset,
+                             const int* order, int* counter, const T* f, T* Q, double* moments, size_t smem, int jd,
+                             int fft, int sj, cudaStream_t st) {
+    auto k = k_fused2d_batched<T, KAHAN, NT>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem);
+    per_sm = std::max(per_sm, 1);
+    const int grid = std::max(1, std::min(n_cells, per_sm * qdvm_num_sms()));
+    k<<<grid, NT, smem, st>>>(b, n_cells, cell_plan, cell_offset, order, counter, f, Q, moments, jd, fft, sj);
+    QDVM_LAUNCH_CHECK("fused2d batched launch");
+    return QDVM_OK;
+}
+
+template <typename T, bool KAHAN>
+qdvm_status dispatch_batched(const BatchDev& b, const qdvm_tuning& tu, int n_cells, const int* cell_plan,
+                             const int64_t* cell_offset, const int* order, int* counter, const void* f, void* Q,
+                             double* moments, size_t smem, cudaStream_t st) {
+    const T* fi = static_cast<const T*>(f);
+    T* qo = static_cast<T*>(Q);
+    if (tu.threads == 512)
+        return launch_batched_t<T, KAHAN, 512>(b, n_cells, cell_plan, cell_offset, order, counter, fi, qo, moments,
+                                               smem, tu.direct_j, tu.loss_fft, tu.scan_j, st);
+    return launch_batched_t<T, KAHAN, 256>(b, n_cells, cell_plan, cell_offset, order, counter, fi, qo, moments, smem,
+                                           tu.direct_j, tu.loss_fft, tu.scan_j, st);
+}
+
+
+}  // namespace
+
+// Per-precision entry points, one translation unit each (fused2d_f64.cu,
+// fused2d_f32.cu, fused2d_f32k.cu), so that the instantiations compile in
+// parallel.
+#define QDVM_FUSED2D_DECLARE(sfx)                                                                                  \
+    qdvm_status fused2d_single_##sfx(const qdvm_plan_s* p, const void* f, void* Q, void* ws, int S, int ppc,      \
+                                     size_t smem, cudaStream_t st);                                                \
+    qdvm_status fused2d_batched_##sfx(const BatchDev& b, const qdvm_tuning& tu, int n_cells, const int* cell_plan, \
+                                      const int64_t* cell_offset, const int* order, int* counter, const void* f,   \
+                                      void* Q, double* moments, size_t smem, cudaStream_t st);
+QDVM_FUSED2D_DECLARE(f64)
+QDVM_FUSED2D_DECLARE(f32)
+QDVM_FUSED2D_DECLARE(f32k)
+#undef QDVM_FUSED2D_DECLARE
+
+#define QDVM_FUSED2D_INSTANTIATE(sfx, T, KAHAN)                                                                    \
+    qdvm_status fused2d_single_##sfx(const qdvm_plan_s* p, const void* f, void* Q, void* ws, int S, int ppc,      \
+                                     size_t smem, cudaStream_t st) {                                               \
+        return dispatch_single<T, KAHAN>(p, f, Q, ws, S, ppc, smem, st);                                           \
+    }                                                                                                              \
+    qdvm_status fused2d_batched_##sfx(const BatchDev& b, const qdvm_tuning& tu, int n_cells, const int* cell_plan, \
+                                      const int64_t* cell_offset, const int* order, int* counter, const void* f,   \
+                                      void* Q, double* moments, size_t smem, cudaStream_t st) {                    \
+        return dispatch_batched<T, KAHAN>(b, tu, n_cells, cell_plan, cell_offset, order, counter, f, Q, moments,   \
+                                          smem, st);                                                               \
+    }

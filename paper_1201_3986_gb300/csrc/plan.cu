@@ -210,6 +210,75 @@ __global__ void k_pairs(int n_lines, const int4* lines, const double* c, int4* p
     if (threadIdx.x == 0) *n_out = base;
 }
 
+// Unimodular complement of a primitive v = (p, q): w = (r, s) with
+// p s - q r = 1, so that (alpha, beta) -> alpha v + beta w is a bijection of
+// the torus Z_N^2 for every N.  Among the complements w + c v the one
+// returned has s odd (possible for every primitive v: if s is even, q r is
+// odd, so q is odd and s + q is odd).
+__device__ void unimodular_complement(int p, int q, int* r, int* s) {
+    int r0 = p, r1 = q, x0 = 1, x1 = 0, y0 = 0, y1 = 1;  // extended Euclid: p x + q y = +-1
+    while (r1 != 0) {
+        const int k = r0 / r1;
+        int t = r0 - k * r1;
+        r0 = r1;
+        r1 = t;
+        t = x0 - k * x1;
+        x0 = x1;
+        x1 = t;
+        t = y0 - k * y1;
+        y0 = y1;
+        y1 = t;
+    }
+    if (r0 < 0) {
+        x0 = -x0;
+        y0 = -y0;
+    }
+    int rr = -y0, ss = x0;
+    if ((ss & 1) == 0) {
+        rr += p;
+        ss += q;
+    }
+    *r = rr;
+    *s = ss;
+}
+
+// Tables of the running-sum (scan) line-sum engine of the 2D evaluator, one
+// thread per pair {e, e^perp}:
+//   scan[i] = (complement of e, complement of e^perp), each as (row, column);
+//   pairs[i].w = S, the segment length of the running sums.  A segment is S
+//   consecutive points of an e-orbit; its loads span (S - 1 + 2J) steps of
+//   |e|_inf, which must fit in the 4H rows/columns of the on-chip halo.
+//   Among the divisors of N allowed by that (at most 32), S minimises a
+//   per-thread cost model of a 256-thread CTA: rounds of segments times
+//   (2J + 1 first-window loads + 3 shared-memory accesses per further step
+//   + a fixed set-up).
+__global__ void k_pair_scan(int n_pairs, int N, int H, int4* pairs, int4* scan) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pairs) return;
+    int4 e = pairs[i];
+    const int p = e.x, q = e.y, J = e.z;
+    const int n = max(abs(p), abs(q));
+    const int smax = min(32, (4 * H) / n - 2 * J + 1);
+    int best = 0;
+    long long best_cost = 0;
+    for (int S = 1; S <= smax; ++S) {
+        if (N % S) continue;
+        const long long items = 2LL * N * N / S;
+        const long long rounds = (items + 255) / 256;
+        const long long cost = rounds * (2 * J + 1 + 3 * (S - 1) + 12);
+        if (best == 0 || cost <= best_cost) {
+            best = S;
+            best_cost = cost;
+        }
+    }
+    int r0, s0, r1, s1;
+    unimodular_complement(p, q, &r0, &s0);
+    unimodular_complement(-q, p, &r1, &s1);
+    e.w = best;
+    pairs[i] = e;
+    scan[i] = make_int4(r0, s0, r1, s1);
+}
+
 // Size of e^perp ∩ [-Nt, Nt]^d \ {0} per line (one block per line).
 __global__ void k_plane_count(int d, int n_lines, const int4* lines, int Nt, int* counts) {
     const int4 e = lines[blockIdx.x];
@@ -354,6 +423,7 @@ static void plan_free(qdvm_plan_s* p) {
     cudaFree(p->d_c);
     cudaFree(p->d_pairs);
     cudaFree(p->d_pair_c);
+    cudaFree(p->d_pair_scan);
     cudaFree(p->d_plane_start);
     cudaFree(p->d_plane);
     cudaFree(p->d_khat);
@@ -425,6 +495,10 @@ static qdvm_status build_tables(qdvm_plan_s* p) {
         p->n_pairs = np;
         cudaFree(d_tmp);
         d_tmp = nullptr;
+        if ((e = cudaMalloc(&p->d_pair_scan, np * sizeof(int4))) != cudaSuccess)
+            return fail(qdvm_cuda_status(e, "pair scan table"));
+        k_pair_scan<<<(np + 127) / 128, 128>>>(np, p->N, p->Ntilde, p->d_pairs, p->d_pair_scan);
+        if ((e = cudaGetLastError()) != cudaSuccess) return fail(qdvm_cuda_status(e, "k_pair_scan"));
     }
     // plane lists e^perp ∩ [-Ntilde, Ntilde]^d \ {0} (in 2D: the segment along e^perp)
     if ((e = cudaMalloc(&d_tmp, total * sizeof(int))) != cudaSuccess) return fail(qdvm_cuda_status(e, "plane counts"));
@@ -519,6 +593,8 @@ extern "C" qdvm_status qdvm_plan_create_ex(qdvm_plan_t* out, int d, int N, int N
     p->tune.direct_j = 2;
     p->tune.line_chunks = 0;
     p->tune.loss_fft = 0;
+    // the engine only sets the initial choice; qdvm_tune_batched may change it
+    p->tune.scan_j = engine == QDVM_ENGINE_SCAN ? 1 : engine == QDVM_ENGINE_DIRECT ? 0 : QDVM_SCAN_J_DEFAULT;
     cudaGetDevice(&p->device);
     qdvm_status s = build_tables(p);
     if (s != QDVM_OK) {
@@ -588,6 +664,7 @@ extern "C" qdvm_status qdvm_plan_set_tuning(qdvm_plan_t p, const qdvm_tuning* t)
     if (t->direct_j < 0 || t->direct_j > 2) return qdvm_fail(QDVM_ERR_INVALID_ARG, "direct_j must be 0, 1 or 2");
     if (t->line_chunks < 0) return qdvm_fail(QDVM_ERR_INVALID_ARG, "line_chunks must be >= 0");
     if (t->loss_fft != 0 && t->loss_fft != 1) return qdvm_fail(QDVM_ERR_INVALID_ARG, "loss_fft must be 0 or 1");
+    if (t->scan_j < 0 || t->scan_j > 64) return qdvm_fail(QDVM_ERR_INVALID_ARG, "scan_j must be in [0, 64]");
     p->tune = *t;
     return QDVM_OK;
 }

@@ -28,8 +28,9 @@ struct qdvm_plan_s {
     // device tables (owned)
     int4* d_lines;        // (e0, e1, e2, J)
     double* d_c;          // c_e
-    int4* d_pairs;        // 2D: (e0, e1, J, 0), one per pair
+    int4* d_pairs;        // 2D: (e0, e1, J, S), one per pair
     double* d_pair_c;     // 2D: c_e (= c_{e^perp})
+    int4* d_pair_scan;    // 2D: unimodular complements of e and e^perp (scan engine; S in d_pairs[].w)
     int* d_plane_start;   // 3D: n_lines + 1 offsets into d_plane
     char4* d_plane;       // (l0, l1, l2, 0), l in e^perp, 0 < |l|_inf <= Ntilde
     // 2D with N <= 64 and 3D with N <= 32: the loss as one convolution,
@@ -64,6 +65,7 @@ struct PlanDev {
     const double* c;
     const int4* pairs;
     const double* pair_c;
+    const int4* pair_scan;
     const int* plane_start;
     const char4* plane;
     const double* khat;
@@ -96,6 +98,7 @@ inline PlanDev plan_dev(const qdvm_plan_s* p) {
     v.c = p->d_c;
     v.pairs = p->d_pairs;
     v.pair_c = p->d_pair_c;
+    v.pair_scan = p->d_pair_scan;
     v.plane_start = p->d_plane_start;
     v.plane = p->d_plane;
     v.khat = p->d_khat;

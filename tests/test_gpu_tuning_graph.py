@@ -106,7 +106,10 @@ def test_tuning_rejects_bad_values(q):
         p.set_tuning(direct_j=3)
     with pytest.raises(q.QdvmError):
         p.set_tuning(loss_fft=2)
-    assert p.tuning() == {"threads": 256, "direct_j": 2, "line_chunks": 0, "loss_fft": 0}
+    with pytest.raises(q.QdvmError):
+        p.set_tuning(scan_j=-1)
+    assert p.tuning() == {"threads": 256, "direct_j": 2, "line_chunks": 0, "loss_fft": 0,
+                          "scan_j": q.QDVM_SCAN_J_DEFAULT}
 
 
 def test_autotuner_2d_then_parity(q, torch):
@@ -116,6 +119,7 @@ def test_autotuner_2d_then_parity(q, torch):
     cp, co, f = _batch(torch, b, Ns, "f32_kahan")
     best = q.qdvm_tune_batched(plans, cp, co, f, "f32_kahan")
     assert best["threads"] in (256, 512) and best["direct_j"] in (0, 1, 2) and best["loss_fft"] in (0, 1)
+    assert 0 <= best["scan_j"] <= 64
     assert all(p.tuning() == best for p in plans)
     Q, _ = q.qdvm_eval_batched(plans, cp, co, f, "f32_kahan")
     Qn = Q.cpu().numpy().astype(np.float64)
