@@ -54,7 +54,8 @@ REF_STEP_CELLS = 96  # reference arm: one step = the first 96 cells (~1 s)
 
 
 def workload_config(extra=None):
-    cfg = {"workload": "batched 2D DVM Q: 4096 cells, N~U{16,32,48,64} (seed 0), L=8, Nbar=8, unit kernel, "
+    ns = ",".join(str(n) for n in NS)
+    cfg = {"workload": f"batched 2D DVM Q: {N_CELLS} cells, N~U{{{ns}}} (seed 0), L={L:g}, Nbar={NBAR}, unit kernel, "
                        "two-Maxwellian mixtures, FP32 + compensated direction sums, FP64 moments",
            "n_cells": N_CELLS, "Ns": list(NS), "Nbar": NBAR, "L": L, "prec": "f32_kahan",
            "l2": f"{ROTATE} rotating input/output batch copies (> 129 MB L2)"}
@@ -71,8 +72,8 @@ def dist_env():
 
 
 PROFILE = os.path.join(ROOT, "profiles", "k_fused2d_batched__batch2d_4096cells.md")
-KERNEL_SOURCES = ["paper_1201_3986_gb300/csrc/fused2d.cu", "paper_1201_3986_gb300/csrc/fft.cuh",
-                  "paper_1201_3986_gb300/csrc/qdvm_internal.cuh"]
+KERNEL_SOURCES = ["paper_1201_3986_gb300/csrc/fused2d.cuh", "paper_1201_3986_gb300/csrc/fused2d_f32k.cu",
+                  "paper_1201_3986_gb300/csrc/fft.cuh", "paper_1201_3986_gb300/csrc/qdvm_internal.cuh"]
 
 
 def kernel_source_hash() -> str:
@@ -860,6 +861,7 @@ def main():
     ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f32_kahan"], help="bkw: precision")
     ap.add_argument("--rk2-steps", type=int, default=10, help="rk2: time steps per graph launch")
     ap.add_argument("--nbar", type=int, default=None)
+    ap.add_argument("--ns", default=None, help="batch2d: comma-separated cell sizes (default 16,32,48,64)")
     ap.add_argument("--cells", type=int, default=256, help="batch3d / jvp3d / vjp3d: number of 32^3 cells; dtr: 2D cells")
     ap.add_argument("--tuning", default=None,
                     help="pin the launch configuration instead of autotuning: batch2d threads,direct_j,loss_fft[,scan_j]; "
@@ -881,6 +883,13 @@ def main():
     elif args.workload != "batch2d":
         run_gpu_workload(args)
     else:
+        # other cell sizes or Nbar for the batched 2D workload (the default,
+        # N in {16,32,48,64} with Nbar = 8, is the measured configuration)
+        global NS, NBAR
+        if args.nbar:
+            NBAR = args.nbar
+        if args.ns:
+            NS = tuple(int(v) for v in args.ns.split(","))
         args.ref_cells = args.ref_cells or ORACLE_SAMPLE_CELLS
         run_gpu(args)
 
