@@ -29,6 +29,11 @@ Functions and the passages they follow:
   stepping of Section 4 for df/dt = Q(f) (Shu-Osher form), in numpy around
   ``q``.
 * ``default_ntilde(N)``      -- Ntilde = floor(N / (3 + sqrt 2)), Section 4.
+* ``spectral_beta(...)`` / ``q_spectral(...)`` -- the pseudo-spectral form
+  of Section 3.1: the kernel modes beta(K, L) of eq. (betaKL) summed term by
+  term over the (k, l) pairs, beta~(K, L) = beta(K, L) - beta(L, L), and
+  Q through eq. (sysDiff) with numpy's FFT (small grids only: the table
+  has N^{2d} entries).
 
 Parity status: every function above is pinned by ``tests/test_oracle_*.py``
 (closed forms, invariants, brute force through the general DVM form of
@@ -289,6 +294,74 @@ def vjp_points(f, g, L: float, Nbar: int, idx, kernel: str = "unit", Ntilde: int
     if rc != 0:
         raise RuntimeError(f"oracle_vjp_points failed ({rc})")
     return out, sc
+
+
+def _weight(k, kernel: str, h: float, d: int) -> float:
+    """a(k) of the decoupled weights after eq. (decoup): 1 (unit kernel) or
+    h^{2d-1} |k| / gcd(k) (Heintz-Panferov weights, b(l) = 1)."""
+    if kernel == "unit":
+        return 1.0
+    g = 0
+    for x in k:
+        g = np.gcd(g, abs(int(x)))
+    return h ** (2 * d - 1) * float(np.sqrt(np.dot(k, k))) / g
+
+
+def spectral_beta(d: int, N: int, L: float, Nbar: int, kernel: str = "unit", Ntilde: int | None = None) -> np.ndarray:
+    """beta~(K, L) = beta(K, L) - beta(L, L) for K, L in Z_N^d (flat
+    row-major indices), shape (N^d, N^d), real.
+
+    beta(K, L) = sum_{k, l} Gamma(k) e_K(k) e_L(l) over the pairs of eq.
+    (betaKL): k, l in [-Ntilde, Ntilde]^d minus 0 with k . l = 0 and the line
+    of k in A_m (eq. (decDVM)), e_K(k) = exp(2 pi i K . k / N).  Summed pair
+    by pair (grouped by k), without the line decomposition."""
+    Nt = default_ntilde(N) if Ntilde is None else int(Ntilde)
+    m = min(int(Nbar), Nt)
+    h = 2.0 * L / N
+    rng = np.arange(-Nt, Nt + 1)
+    box = np.array(np.meshgrid(*([rng] * d), indexing="ij")).reshape(d, -1).T
+    box = box[np.any(box != 0, axis=1)]
+    modes = np.array(np.meshgrid(*([np.arange(N)] * d), indexing="ij")).reshape(d, -1).T
+    ks, ws, S = [], [], []
+    for k in box:
+        g = 0
+        for x in k:
+            g = np.gcd(g, abs(int(x)))
+        if np.max(np.abs(k // g)) > m:
+            continue  # the line of k is not in A_m
+        ls = box[box @ k == 0]
+        if ls.size == 0:
+            continue
+        ks.append(k)
+        ws.append(_weight(k, kernel, h, d))
+        S.append(np.exp(2j * np.pi * (modes @ ls.T) / N).sum(axis=1))  # sum_l e_L(l)
+    Ek = np.exp(2j * np.pi * (modes @ np.array(ks).T) / N)  # (N^d, #k)
+    beta = (Ek * np.array(ws)) @ np.array(S)  # (N^d, N^d)
+    if np.max(np.abs(beta.imag)) > 1e-9 * max(1.0, np.max(np.abs(beta.real))):
+        raise RuntimeError("beta is not real: the term set is not symmetric")
+    beta = beta.real
+    return beta - np.diag(beta)[None, :]
+
+
+def q_spectral(f, L: float, Nbar: int, kernel: str = "unit", Ntilde: int | None = None,
+               beta: np.ndarray | None = None) -> np.ndarray:
+    """Q through eq. (sysDiff): Qhat_I = sum_{K + L = I} beta~(K, L) fhat_K
+    fhat_L with fhat_I = N^{-d} sum_i f_i e_{-I}(i), then Q_i = sum_I
+    Qhat_I e_I(i)."""
+    f = _f64(f)
+    d, N = f.ndim, f.shape[0]
+    if beta is None:
+        beta = spectral_beta(d, N, L, Nbar, kernel, Ntilde)
+    M = N ** d
+    modes = np.array(np.meshgrid(*([np.arange(N)] * d), indexing="ij")).reshape(d, -1).T
+    fh = np.fft.fftn(f).ravel() / M
+    Qh = np.zeros(M, dtype=complex)
+    for I in range(M):
+        Lm = (modes[I][None, :] - modes) % N  # L = I - K for every K
+        Li = np.ravel_multi_index(Lm.T, (N,) * d)
+        Qh[I] = np.sum(beta[np.arange(M), Li] * fh * fh[Li])
+    Q = np.fft.ifftn(Qh.reshape((N,) * d)) * M
+    return Q.real
 
 
 def moments(Q, L: float) -> np.ndarray:
