@@ -651,6 +651,86 @@ def run_dtr_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def run_spectral_workload(args):
+    """The pseudo-spectral route of Section 3.1 (eq. (sysDiff)): Q of a batch
+    of 2D cells of one size through their Fourier modes with the dense table
+    beta~, O(N^{2d}) per cell, beside the fast evaluator on the same cells.
+    An L2 flush (a 256 MB write) separates the timed steps, each timed with
+    its own events: the FP32 table (N^{2d} floats, 67 MB at N = 64) would
+    otherwise stay in the 129 MB L2."""
+    import torch
+
+    import oracle
+    import paper_1201_3986_gb300 as q
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    N, nb, Lh = args.n, args.nbar or 8, 8.0
+    prec = args.prec
+    n_cells = args.cells
+    rng = np.random.default_rng(0)
+    cells = np.stack([synth.mixture(2, N, Lh, rng) for _ in range(n_cells)])
+    dtype = torch.float64 if prec == "f64" else torch.float32
+    f = torch.tensor(cells, dtype=dtype, device=dev)
+    plan = q.Plan(2, N, nb, Lh, kernel="unit")
+    table = q.spectral_table(plan, prec)
+    Q = torch.empty_like(f)
+    ws = torch.empty(q.spectral_workspace_bytes(plan, n_cells, prec), dtype=torch.uint8, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        total = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn()
+            e1.record(st)
+            torch.cuda.synchronize(dev)
+            total += e0.elapsed_time(e1)
+        return total / args.steps
+
+    with ClockSampler(dev.index) as clk:
+        ms = timed(lambda: q.qdvm_eval_spectral(plan, table, f, prec, out=Q, workspace=ws))
+    Qn = Q.cpu().numpy().astype(np.float64)
+    fin = f.cpu().numpy().astype(np.float64)
+    errs = []
+    for c in (0, n_cells - 1):
+        r = oracle.q(fin[c], Lh, nb)
+        errs.append(oracle.rel_linf(Qn[c], r["Q"], r["scale"]))
+    # the fast evaluator on the same cells (FFT loss, tuned launch)
+    cp = torch.zeros(n_cells, dtype=torch.int32, device=dev)
+    co = torch.arange(n_cells, dtype=torch.int64, device=dev) * (N * N)
+    plan.set_tuning(loss_fft=1)
+    wsf = torch.empty(q.batched_workspace_bytes([plan], n_cells, prec), dtype=torch.uint8, device=dev)
+    ff = f.reshape(-1)
+    Qf = torch.empty_like(ff)
+    ms_fast = timed(lambda: q.qdvm_eval_batched([plan], cp, co, ff, prec, out=Qf, moments=False, workspace=wsf))
+    M = N * N
+    flops = 10.0 * M * M * n_cells  # per (I, K, cell): complex product, scale, accumulate
+    peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    line = {"metric": METRIC, "value": n_cells * M / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == "f64" else "f32", "data": "synthetic",
+            "config": {"workload": f"pseudo-spectral route (eq. (sysDiff)): {n_cells} 2D cells N={N} on [-8,8]^2, "
+                                   f"Nbar={nb} ({plan.n_lines} lines), unit kernel, two-Maxwellian mixtures "
+                                   f"(seed 0), dense table of {M * M} entries, {prec}",
+                       "N": N, "Nbar": nb, "n_cells": n_cells, "prec": prec,
+                       "l2": "256 MB flush between timed steps"},
+            "roofline": {"bound": "alu", "kernel": "k_spec_conv",
+                         "achieved": flops / (ms / 1e3) / 1e12 if prec != "f64" else None,
+                         "peak": peak if prec != "f64" else None, "unit": "TFLOP/s",
+                         "frac": flops / (ms / 1e3) / 1e12 / peak if prec != "f64" else None,
+                         "note": "10 flops per (I, K, cell); FP32 peak 152 x 128 x 2 x 2.07 GHz; the whole "
+                                 "evaluation (DFTs included) timed"},
+            "fast_evaluator_ms": ms_fast, "fast_over_spectral_speedup": ms / ms_fast,
+            "accuracy": {"rel_linf_vs_fp64_oracle_max": max(errs)}, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 # Table 2 of the paper: CPU time (s) of the fast DVM to T = 1 with dt = 0.01
 # (100 TVD-RK2 steps) on one 2D BKW cell, hardware unstated; keys (N, Nbar).
 TABLE2_S = {(16, 3): 0.5, (32, 3): 3.19, (32, 7): 14.52, (64, 3): 16.2, (64, 7): 73.4, (64, 14): 283.0,
@@ -856,9 +936,10 @@ def main():
                     help="single3d, jvp3d, vjp3d (default 1): loss as an FFT convolution with row-form gain, or the "
                          "line engine (0); bkw (default 0): FFT loss in the single-cell 2D evaluator")
     ap.add_argument("--workload", default="batch2d",
-                    choices=["batch2d", "batch3d", "jvp3d", "vjp3d", "single3d", "rk2", "bkw", "adaptive", "dtr"])
-    ap.add_argument("--n", type=int, default=64, help="bkw: points per axis")
-    ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f32_kahan"], help="bkw: precision")
+                    choices=["batch2d", "batch3d", "jvp3d", "vjp3d", "single3d", "rk2", "bkw", "adaptive", "dtr",
+                             "spectral"])
+    ap.add_argument("--n", type=int, default=64, help="bkw, spectral: points per axis")
+    ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f32_kahan"], help="bkw, spectral: precision")
     ap.add_argument("--rk2-steps", type=int, default=10, help="rk2: time steps per graph launch")
     ap.add_argument("--nbar", type=int, default=None)
     ap.add_argument("--ns", default=None, help="batch2d: comma-separated cell sizes (default 16,32,48,64)")
@@ -880,6 +961,8 @@ def main():
         run_adaptive_workload(args)
     elif args.workload == "dtr":
         run_dtr_workload(args)
+    elif args.workload == "spectral":
+        run_spectral_workload(args)
     elif args.workload != "batch2d":
         run_gpu_workload(args)
     else:

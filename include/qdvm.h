@@ -301,6 +301,40 @@ qdvm_status qdvm_eval_direct_workspace(size_t* bytes);
 qdvm_status qdvm_eval_direct(qdvm_plan_t plan, const void* f, void* Q, int prec, int boundary, void* workspace,
                              size_t workspace_bytes, void* stream);
 
+/* Pseudo-spectral evaluation (Section 3.1): Q through its Fourier modes,
+ *   Qhat_I = sum_{K + L = I} beta~(K, L) fhat_K fhat_L               (eq. (sysDiff))
+ *   beta~(K, L) = beta(K, L) - beta(L, L),
+ *   beta(K, L)  = sum_{(k, l)} Gamma(k) e_K(k) e_L(l)                 (eq. (betaKL))
+ * with fhat_I = N^-d sum_i f_i e_{-I}(i), Q_i = sum_I Qhat_I e_I(i), e_K(k) =
+ * exp(2 pi i K.k / N), over the (k, l) pairs of the plan (lines of A_m).
+ * O(N^{2d}) work per cell and a dense N^d x N^d table: a second, Fourier-side
+ * evaluation of the operator of qdvm_eval, independent of its line sums, for
+ * checking, not for speed.  Supported plans: d = 2 with N <= 64, d = 3 with
+ * N <= 16; others return QDVM_ERR_UNSUPPORTED.
+ *
+ * qdvm_spectral_table_entries: *n = N^{2d}, the entries of the table.
+ * qdvm_spectral_table: fills table[K * N^d + L] = beta~(K, L) (modes K, L
+ *   flat row-major in [0, N)^d).  beta is real (the pair set is symmetric in
+ *   k and in l); it is formed in FP64 as sum_e D_e(K) P_e(L) over the lines e
+ *   (D_e the weighted cosine sum of the window of e, P_e that of the offset
+ *   list of e^perp) and stored as double (QDVM_F64) or float (QDVM_F32,
+ *   QDVM_F32_KAHAN).  table: caller-owned DEVICE memory of
+ *   qdvm_spectral_table_entries elements.  A set-up call: it allocates
+ *   temporaries (2 x lines x N^d doubles) and synchronises the stream.
+ * qdvm_spectral_workspace: bytes of workspace for n_cells cells (two complex
+ *   spectra per cell).
+ * qdvm_eval_spectral: Q of n_cells cells stored back to back (N^d elements
+ *   each, row-major) from f, through two batched DFTs and the sum of eq.
+ *   (sysDiff) (F32_KAHAN: compensated sums).  table from qdvm_spectral_table
+ *   in the same precision; f, Q, workspace: DEVICE; f must not alias Q.
+ *   Stream-ordered, allocates nothing.  Errors: BAD_PLAN, UNSUPPORTED,
+ *   INVALID_ARG (precision, NULL arrays, workspace too small). */
+qdvm_status qdvm_spectral_table_entries(qdvm_plan_t plan, size_t* n);
+qdvm_status qdvm_spectral_table(qdvm_plan_t plan, void* table, int prec, void* stream);
+qdvm_status qdvm_spectral_workspace(qdvm_plan_t plan, int n_cells, int prec, size_t* bytes);
+qdvm_status qdvm_eval_spectral(qdvm_plan_t plan, const void* table, int n_cells, const void* f, void* Q, int prec,
+                               void* workspace, size_t workspace_bytes, void* stream);
+
 /* Capture qdvm_rk2_batched (n_steps steps, all pointers fixed) into an
  * executable graph for qdvm_graph_launch: one launch runs the whole loop. */
 qdvm_status qdvm_graph_capture_rk2(qdvm_graph_t* out, const qdvm_plan_t* plans, int n_plans, int n_cells,

@@ -102,6 +102,10 @@ QDVM_MAX_LEVELS = 8
 _sig("qdvm_eval_direct_batched", [_P(_vp), _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _i, _vp])
 _sig("qdvm_eval_direct_workspace", [_P(_sz)])
 _sig("qdvm_eval_direct", [_vp, _vp, _vp, _i, _i, _vp, _sz, _vp])
+_sig("qdvm_spectral_table_entries", [_vp, _P(_sz)])
+_sig("qdvm_spectral_table", [_vp, _vp, _i, _vp])
+_sig("qdvm_spectral_workspace", [_vp, _i, _i, _P(_sz)])
+_sig("qdvm_eval_spectral", [_vp, _vp, _i, _vp, _vp, _i, _vp, _sz, _vp])
 _BOUNDARY = {"periodic": 0, "box": 1}
 _sig("qdvm_graph_capture_rk2", [_P(_vp), _P(_vp), _i, _i, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_double, _i, _vp,
                                 _i, _vp, _sz])
@@ -376,6 +380,47 @@ def qdvm_eval_direct(plan: Plan, f: torch.Tensor, prec="f64", boundary="box",
     ws = torch.empty(256, dtype=torch.uint8, device=f.device)
     _check(_lib.qdvm_eval_direct(plan.handle, _ptr(f), _ptr(Q), p, _BOUNDARY[boundary], _ptr(ws), ws.numel(),
                                  _stream(f.device)), "qdvm_eval_direct")
+    return Q
+
+
+def spectral_table(plan: Plan, prec="f64", device=None) -> torch.Tensor:
+    """The table beta~(K, L) of the pseudo-spectral route (N^d x N^d, row K,
+    column L), built on the device."""
+    p = _prec(prec)
+    n = ctypes.c_size_t()
+    _check(_lib.qdvm_spectral_table_entries(plan.handle, ctypes.byref(n)), "qdvm_spectral_table_entries")
+    M = plan.N ** plan.d
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    table = torch.empty((M, M), dtype=_DTYPE[p], device=dev)
+    assert table.numel() == n.value
+    _check(_lib.qdvm_spectral_table(plan.handle, _ptr(table), p, _stream(dev)), "qdvm_spectral_table")
+    return table
+
+
+def spectral_workspace_bytes(plan: Plan, n_cells: int, prec) -> int:
+    b = ctypes.c_size_t()
+    _check(_lib.qdvm_spectral_workspace(plan.handle, int(n_cells), _prec(prec), ctypes.byref(b)),
+           "qdvm_spectral_workspace")
+    return b.value
+
+
+def qdvm_eval_spectral(plan: Plan, table: torch.Tensor, f: torch.Tensor, prec="f64", out: torch.Tensor | None = None,
+                       workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """Q of a batch of cells (f of shape (n_cells,) + plan.shape, or one cell
+    of plan.shape) through the Fourier modes, eq. (sysDiff)."""
+    p = _prec(prec)
+    if f.dtype != _DTYPE[p] or not f.is_cuda or not f.is_contiguous():
+        raise ValueError(f"f must be a contiguous CUDA {_DTYPE[p]} tensor")
+    if table.dtype != _DTYPE[p] or not table.is_cuda or not table.is_contiguous():
+        raise ValueError("table must come from spectral_table in the same precision")
+    M = plan.N ** plan.d
+    if f.numel() % M:
+        raise ValueError("f must hold whole cells of N^d points")
+    n_cells = f.numel() // M
+    Q = torch.empty_like(f) if out is None else out
+    ws = workspace if workspace is not None else _workspace(spectral_workspace_bytes(plan, n_cells, p), f.device)
+    _check(_lib.qdvm_eval_spectral(plan.handle, _ptr(table), n_cells, _ptr(f), _ptr(Q), p, _ptr(ws),
+                                   0 if ws is None else ws.numel(), _stream(f.device)), "qdvm_eval_spectral")
     return Q
 
 
