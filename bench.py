@@ -86,23 +86,46 @@ def kernel_source_hash() -> str:
     return h.hexdigest()
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the evaluator from the committed ncu summary,
-    or None when the kernel sources changed since it was captured."""
+def profiled_value(key: str):
+    """A per-launch count of the evaluator from the committed ncu summary
+    (dram_bytes_per_launch, smem_wavefronts_per_launch), or None when the
+    kernel sources changed since it was captured."""
     if not os.path.exists(PROFILE):
         return None
     vals = {}
     for line in open(PROFILE):
         t = line.strip().lstrip("-").strip().strip("`")
-        if t.startswith(("source_sha256:", "dram_bytes_per_launch:")):
+        if t.startswith(("source_sha256:", "dram_bytes_per_launch:", "smem_wavefronts_per_launch:")):
             k, v = t.split(":", 1)
             vals[k.strip()] = v.split("`")[0].split("(")[0].strip()
     if vals.get("source_sha256") != kernel_source_hash():
         return None
     try:
-        return int(vals["dram_bytes_per_launch"])
+        return int(vals[key])
     except (KeyError, ValueError):
         return None
+
+
+def profiled_traffic():
+    return profiled_value("dram_bytes_per_launch")
+
+
+def smem_roofline(kernel_ms: float, clocks: dict, tuning: dict):
+    """The evaluator's binding resource: shared-memory wavefronts (the LSU
+    pipe serves one per SM and cycle).  Wavefronts per launch from the ncu
+    summary (they depend on the code, the workload and the launch
+    configuration, not on timing) over the live kernel time, 152 SMs and the
+    SM clock sampled in the timed region; None when the configuration is not
+    the profiled one."""
+    wf = profiled_value("smem_wavefronts_per_launch")
+    mhz = clocks.get("sm_mhz") or 2070.0
+    t = tuning or {}
+    if wf is None or (t.get("threads"), t.get("loss_fft"), t.get("scan_j")) != (256, 1, 0) or NS != (16, 32, 48, 64) \
+            or NBAR != 8:
+        return None
+    per_cycle = wf / (kernel_ms / 1e3 * 152 * mhz * 1e6)
+    return {"bound": "smem", "achieved": per_cycle, "peak": 1.0, "unit": "wavefronts/cycle/SM",
+            "frac": per_cycle, "wavefronts_per_launch": wf, "sm_mhz": mhz}
 
 
 def peaks():
@@ -418,6 +441,7 @@ def run_gpu(args):
     sm_peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12
     achieved_tflops = alg_flops / (kernel_ms / 1e3) / 1e12
 
+    clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -433,6 +457,7 @@ def run_gpu(args):
                      "frac": achieved_tflops / sm_peak_tflops, "traffic": profiled_traffic(),
                      "kernel": "k_fused2d_batched", "kernel_ms": kernel_ms,
                      "note": "FP32 peak = 152 SMs x 128 lanes x 2 x 2.07 GHz; algorithmic flops = 11 per point-pair"},
+        "roofline_smem": smem_roofline(kernel_ms, clocks, tuning),
         "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved_gbs / hbm_peak, "peak_kind": f"of {peak_kind}",
                          "alg_bytes": alg_bytes},
@@ -440,7 +465,7 @@ def run_gpu(args):
                              "speedup_of_batched_f32": value / ws / fp64_value},
         "accuracy": {"rel_linf_vs_fp64_oracle_max": max(errs), "cells_checked": picks,
                      "mass_defect_rel_max": max(mass_rel)},
-        "clocks": clk.summary(),
+        "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline:
         v, pts, dt, cores, n = oracle_sample(args.ref_cells)
