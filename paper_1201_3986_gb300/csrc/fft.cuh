@@ -1,6 +1,6 @@
 // Small complex FFT building blocks shared by the on-chip 2D FFT (fused2d.cu)
 // and the 3D FFT over global scratch (fast3d.cu): complex type per real
-// type, complex product, and in-register DFTs of radix 2, 3 and 4.
+// type, complex product, and in-register DFTs of radix 2, 3, 4 and 8.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -48,6 +48,28 @@ __device__ __forceinline__ void dft_small(C (&v)[R]) {
         v[1].y = m.y + sy;
         v[2].x = m.x - sx;
         v[2].y = m.y - sy;
+    } else if constexpr (R == 8) {
+        // X[k] = E[k] + w^k O[k], X[k+4] = E[k] - w^k O[k] (k < 4) with E, O
+        // the 4-point DFTs of the even and odd samples, w = exp(-+ 2 pi i / 8)
+        C e[4] = {v[0], v[2], v[4], v[6]};
+        C o[4] = {v[1], v[3], v[5], v[7]};
+        dft_small<4, INV>(e);
+        dft_small<4, INV>(o);
+        const S r = S(0.7071067811865475244008443621048490);  // 1/sqrt(2)
+        // forward: w = (1 - i) r, w^2 = -i, w^3 = (-1 - i) r; inverse: conjugates
+        const C o1 = INV ? C{r * (o[1].x - o[1].y), r * (o[1].x + o[1].y)}
+                         : C{r * (o[1].x + o[1].y), r * (o[1].y - o[1].x)};
+        const C o2 = INV ? C{-o[2].y, o[2].x} : C{o[2].y, -o[2].x};
+        const C o3 = INV ? C{-r * (o[3].x + o[3].y), r * (o[3].x - o[3].y)}
+                         : C{r * (o[3].y - o[3].x), -r * (o[3].x + o[3].y)};
+        v[0] = C{e[0].x + o[0].x, e[0].y + o[0].y};
+        v[4] = C{e[0].x - o[0].x, e[0].y - o[0].y};
+        v[1] = C{e[1].x + o1.x, e[1].y + o1.y};
+        v[5] = C{e[1].x - o1.x, e[1].y - o1.y};
+        v[2] = C{e[2].x + o2.x, e[2].y + o2.y};
+        v[6] = C{e[2].x - o2.x, e[2].y - o2.y};
+        v[3] = C{e[3].x + o3.x, e[3].y + o3.y};
+        v[7] = C{e[3].x - o3.x, e[3].y - o3.y};
     } else {  // R == 4
         const C a0 = {v[0].x + v[2].x, v[0].y + v[2].y};
         const C a1 = {v[0].x - v[2].x, v[0].y - v[2].y};

@@ -27,6 +27,8 @@
 #pragma once
 
 #include <algorithm>
+#include <cstdint>
+#include <type_traits>
 
 #include "fft.cuh"
 #include "qdvm_internal.cuh"
@@ -416,7 +418,7 @@ __device__ __forceinline__ void fixed_body(const int4* __restrict__ pairs, const
 // Loss as one convolution (the paper's remark that the loss part is a plain
 // convolution): sum_e c_e V_e(i) = sum_m K(m) f(i + m) = (K * f)(i), K the
 // weighted displacement histogram of the terms (plan table, transformed).
-// An on-chip 2D FFT (Stockham, mixed radix 2/3/4, ping-pong between two
+// An on-chip 2D FFT (Stockham, mixed radix 3/4/8, ping-pong between two
 // N x (N+1) complex buffers) gives K * f for the whole cell; the pair loop
 // then only sums the gain 2 c_e W_e W_{e^perp} -- no P buffer, no barrier.
 
@@ -465,9 +467,9 @@ __device__ __forceinline__ C* fft_passes(C* a, C* b, const C* tw) {
 // All N line transforms of length N; returns the buffer holding the result.
 template <typename C, int N, int LD, bool INV, bool COLS>
 __device__ __forceinline__ C* fft_lines(C* a, C* b, const C* tw) {
-    if constexpr (N == 64) return fft_passes<C, N, LD, INV, COLS, 1, 4, 4, 4>(a, b, tw);
+    if constexpr (N == 64) return fft_passes<C, N, LD, INV, COLS, 1, 8, 8>(a, b, tw);
     else if constexpr (N == 48) return fft_passes<C, N, LD, INV, COLS, 1, 3, 4, 4>(a, b, tw);
-    else if constexpr (N == 32) return fft_passes<C, N, LD, INV, COLS, 1, 2, 4, 4>(a, b, tw);
+    else if constexpr (N == 32) return fft_passes<C, N, LD, INV, COLS, 1, 4, 8>(a, b, tw);
     else return fft_passes<C, N, LD, INV, COLS, 1, 4, 4>(a, b, tw);  // N == 16
 }
 
@@ -688,22 +690,37 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
             }
         }
     };
-    auto fill_cell = [&]() {
-        for (int p = tid; p < W * W; p += NT) {
-            const int py = p / W, px = p - py * W;
-            int sy = py - HW, sx = px - HW;
-            sy += sy < 0 ? N : 0;
-            sy -= sy >= N ? N : 0;
-            sx += sx < 0 ? N : 0;
-            sx -= sx >= N ? N : 0;
-            sF[py * RS + px] = fcell[sy * N + sx];
+    // The cell copy with its periodic halo of width HW (2 HW < N, so a point
+    // has at most one image per axis), and optionally the FFT input: the N^2
+    // points are read once, 16 bytes per load when the cell is so aligned.
+    auto fill_cell = [&](const bool fft_in) {
+        auto put = [&](const int y, const int x, const T v) {
+            const int a = (y + HW) * RS + x + HW;
+            const int dy = y < HW ? N * RS : (y >= N - HW ? -N * RS : 0);
+            const int dx = x < HW ? N : (x >= N - HW ? -N : 0);
+            sF[a] = v;
+            if (dy) sF[a + dy] = v;
+            if (dx) sF[a + dx] = v;
+            if (dy && dx) sF[a + dy + dx] = v;
+            if (fft_in) A[y * LD + x] = C{v, T(0)};
+        };
+        constexpr int V = 16 / (int)sizeof(T);
+        if ((reinterpret_cast<uintptr_t>(fcell) & 15) == 0) {
+            using VT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+            for (int i = tid; i < N * N / V; i += NT) {
+                const VT v = reinterpret_cast<const VT*>(fcell)[i];
+                const T* e = reinterpret_cast<const T*>(&v);
+                const int y = (i * V) / N, x = (i * V) % N;
+#pragma unroll
+                for (int u = 0; u < V; ++u) put(y, x + u, e[u]);
+            }
+        } else {
+            for (int i = tid; i < N * N; i += NT) put(i / N, i % N, fcell[i]);
         }
     };
 
     if constexpr (!SCAN) {
-        fill_cell();
-        if (do_loss)
-            for (int i = tid; i < N * N; i += NT) A[(i / N) * LD + (i % N)] = C{fcell[i], T(0)};
+        fill_cell(do_loss);
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
@@ -722,6 +739,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
         T fh[PPT];
         if (do_loss)
             for (int i = tid; i < N * N; i += NT) A[(i / N) * LD + (i % N)] = C{fcell[i], T(0)};
+        static_assert(2 * HW < N, "one periodic image per axis");
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
             fh[k] = (active && (k < PPT - 1 || last_ok)) ? fcell[(y0 + k * R) * N + x] : T(0);
@@ -733,7 +751,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
             loss_fft([&](int k) { return fh[k]; });
             __syncthreads();
         }
-        fill_cell();
+        fill_cell(false);
         __syncthreads();
         bool pending = false;  // window fields still being read by the previous scanned pair
         for (int pr = pb; pr < pe; ++pr) {
