@@ -27,8 +27,6 @@
 #pragma once
 
 #include <algorithm>
-#include <cstdint>
-#include <type_traits>
 
 #include "fft.cuh"
 #include "qdvm_internal.cuh"
@@ -426,8 +424,11 @@ __device__ __forceinline__ void fixed_body(const int4* __restrict__ pairs, const
 // COLS), NS = product of the radices already applied.  Butterfly b works on
 // line b % N, so a warp touches consecutive lines (row stride LD = N + 1
 // complex: no bank conflicts on columns or rows).
-template <typename C, int N, int LD, int R, int NS, bool INV, bool COLS>
-__device__ __forceinline__ void fft_pass(const C* __restrict__ src, C* __restrict__ dst, const C* __restrict__ tw) {
+// KH: multiply each output by the real factor kh at its mode (row-major
+// N x N), used on the last forward pass to apply the loss kernel's transform.
+template <typename C, int N, int LD, int R, int NS, bool INV, bool COLS, bool KH = false>
+__device__ __forceinline__ void fft_pass(const C* __restrict__ src, C* __restrict__ dst, const C* __restrict__ tw,
+                                         const decltype(C::x)* __restrict__ kh = nullptr) {
     constexpr int NB = N / R;
     for (int b = threadIdx.x; b < N * NB; b += blockDim.x) {
         const int line = b % N, j = b / N;
@@ -449,28 +450,34 @@ __device__ __forceinline__ void fft_pass(const C* __restrict__ src, C* __restric
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int e = idxD + r * NS;
+            if constexpr (KH) {
+                const auto k = kh[COLS ? e * N + line : line * N + e];
+                v[r].x *= k;
+                v[r].y *= k;
+            }
             dst[COLS ? e * LD + line : line * LD + e] = v[r];
         }
     }
 }
 
-template <typename C, int N, int LD, bool INV, bool COLS, int NS, int R, int... Rs>
-__device__ __forceinline__ C* fft_passes(C* a, C* b, const C* tw) {
-    fft_pass<C, N, LD, R, NS, INV, COLS>(a, b, tw);
+template <typename C, int N, int LD, bool INV, bool COLS, bool KH, int NS, int R, int... Rs>
+__device__ __forceinline__ C* fft_passes(C* a, C* b, const C* tw, const decltype(C::x)* kh) {
+    fft_pass<C, N, LD, R, NS, INV, COLS, KH && sizeof...(Rs) == 0>(a, b, tw, kh);
     __syncthreads();
     if constexpr (sizeof...(Rs) > 0)
-        return fft_passes<C, N, LD, INV, COLS, NS * R, Rs...>(b, a, tw);
+        return fft_passes<C, N, LD, INV, COLS, KH, NS * R, Rs...>(b, a, tw, kh);
     else
         return b;
 }
 
 // All N line transforms of length N; returns the buffer holding the result.
-template <typename C, int N, int LD, bool INV, bool COLS>
-__device__ __forceinline__ C* fft_lines(C* a, C* b, const C* tw) {
-    if constexpr (N == 64) return fft_passes<C, N, LD, INV, COLS, 1, 8, 8>(a, b, tw);
-    else if constexpr (N == 48) return fft_passes<C, N, LD, INV, COLS, 1, 3, 4, 4>(a, b, tw);
-    else if constexpr (N == 32) return fft_passes<C, N, LD, INV, COLS, 1, 4, 8>(a, b, tw);
-    else return fft_passes<C, N, LD, INV, COLS, 1, 4, 4>(a, b, tw);  // N == 16
+// KH: the last pass also multiplies by kh (see fft_pass).
+template <typename C, int N, int LD, bool INV, bool COLS, bool KH = false>
+__device__ __forceinline__ C* fft_lines(C* a, C* b, const C* tw, const decltype(C::x)* kh = nullptr) {
+    if constexpr (N == 64) return fft_passes<C, N, LD, INV, COLS, KH, 1, 8, 8>(a, b, tw, kh);
+    else if constexpr (N == 48) return fft_passes<C, N, LD, INV, COLS, KH, 1, 3, 4, 4>(a, b, tw, kh);
+    else if constexpr (N == 32) return fft_passes<C, N, LD, INV, COLS, KH, 1, 4, 8>(a, b, tw, kh);
+    else return fft_passes<C, N, LD, INV, COLS, KH, 1, 4, 4>(a, b, tw, kh);  // N == 16
 }
 
 // Layouts of the FFT body.  Without the SCAN engine: the cell with a
@@ -670,14 +677,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
     // fk(k) gives f at the k-th owned point
     auto loss_fft = [&](auto fk) {
         C* r = fft_lines<C, N, LD, false, false>(A, B, tw);
-        r = fft_lines<C, N, LD, false, true>(r, r == A ? B : A, tw);
-        for (int i = tid; i < N * N; i += NT) {
-            C& z = r[(i / N) * LD + (i % N)];
-            const T k = kh[i];
-            z.x *= k;
-            z.y *= k;
-        }
-        __syncthreads();
+        r = fft_lines<C, N, LD, false, true, true>(r, r == A ? B : A, tw, kh);  // times Ktilde
         r = fft_lines<C, N, LD, true, true>(r, r == A ? B : A, tw);
         r = fft_lines<C, N, LD, true, false>(r, r == A ? B : A, tw);
         if (active) {
@@ -692,7 +692,8 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
     };
     // The cell copy with its periodic halo of width HW (2 HW < N, so a point
     // has at most one image per axis), and optionally the FFT input: the N^2
-    // points are read once, 16 bytes per load when the cell is so aligned.
+    // points are read once; consecutive threads take consecutive points, so
+    // a warp's loads are coalesced and its stores hit distinct banks.
     auto fill_cell = [&](const bool fft_in) {
         auto put = [&](const int y, const int x, const T v) {
             const int a = (y + HW) * RS + x + HW;
@@ -704,19 +705,8 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
             if (dy && dx) sF[a + dy + dx] = v;
             if (fft_in) A[y * LD + x] = C{v, T(0)};
         };
-        constexpr int V = 16 / (int)sizeof(T);
-        if ((reinterpret_cast<uintptr_t>(fcell) & 15) == 0) {
-            using VT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-            for (int i = tid; i < N * N / V; i += NT) {
-                const VT v = reinterpret_cast<const VT*>(fcell)[i];
-                const T* e = reinterpret_cast<const T*>(&v);
-                const int y = (i * V) / N, x = (i * V) % N;
-#pragma unroll
-                for (int u = 0; u < V; ++u) put(y, x + u, e[u]);
-            }
-        } else {
-            for (int i = tid; i < N * N; i += NT) put(i / N, i % N, fcell[i]);
-        }
+#pragma unroll 4
+        for (int i = tid; i < N * N; i += NT) put(i / N, i % N, fcell[i]);
     };
 
     if constexpr (!SCAN) {
