@@ -1,4 +1,4 @@
-// Small complex FFT building blocks shared by the on-chip 2D FFT (fused2d.cu)
+// Small complex FFT building blocks shared by the on-chip 2D FFT (fused2d.cuh)
 // and the 3D FFT over global scratch (fast3d.cu): complex type per real
 // type, complex product, and in-register DFTs of radix 2, 3, 4 and 8.
 #pragma once
