@@ -58,7 +58,7 @@ def rounding_bound(bt, f, prec):
 
 CASES = [  # d, N, Ntilde (None = default), Nbar, kernel
     (2, 16, None, 16, "unit"), (2, 16, None, 2, "hp"), (2, 20, 4, 3, "hp"), (2, 32, None, 8, "unit"),
-    (3, 8, 2, 2, "hp"), (3, 10, None, 2, "unit"),
+    (3, 8, 2, 2, "hp"), (3, 10, None, 2, "unit"), (3, 16, None, 3, "hp"),  # 16^3: the largest 3D table
 ]
 
 
@@ -118,3 +118,5 @@ def test_spectral_rejects_bad_arguments(q, torch):
     with pytest.raises(q.QdvmError):
         q.qdvm_eval_spectral(plan, table, f, "f64", workspace=torch.empty(16, dtype=torch.uint8, device="cuda"))
     assert float(q.qdvm_eval_spectral(plan, table, f, "f64").abs().max()) == 0.0
+    empty = torch.zeros((0, 16, 16), dtype=torch.float64, device="cuda")
+    assert q.qdvm_eval_spectral(plan, table, empty, "f64").shape == (0, 16, 16)
