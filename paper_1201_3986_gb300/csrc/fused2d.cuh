@@ -33,8 +33,6 @@
 
 namespace {
 
-constexpr int kThreads = 256;
-
 // Deterministic block reduction of NV doubles per thread; result in out[] of
 // thread 0.  Uses a fixed tree (shuffle-down, then warps in order).
 template <int NV>
