@@ -497,17 +497,6 @@ __host__ __device__ constexpr size_t cell_bytes() {
     return ((size_t)GeoF<N, H, SCAN>::W * GeoF<N, H, SCAN>::RS * sizeof(T) + 15) / 16 * 16;
 }
 
-// Scan engine: R_v(i) = sum_{|j| <= J} f(i + j v) for v = e and v = e^perp
-// (the window W_v plus the centre) into sRe and sRp (N x N, row-major).
-// The torus is cut along each line into segments of S consecutive points:
-// with the complement w of v (det[v w] = 1), segment (k, beta) is
-// {(kS + t) v + beta w : 0 <= t < S}, and the N^2/S segments of v tile Z_N^2.
-// A thread takes a segment, sums its first window (2J + 1 loads), then
-// slides: R += f(i + (J+1) v) - f(i - J v).  The segment's base is placed
-// at the periodic image that keeps every load inside the 2H halo.
-// Consecutive threads take consecutive beta, whose bases differ by w; w has
-// an odd column component, so for N = 32, 64 (row strides = 0 mod 32) a
-// warp's loads and stores hit 32 distinct banks.
 // One running-sum segment in flight: read pointers, canonical write
 // position and the running value.
 template <typename T>
