@@ -58,11 +58,70 @@ __device__ __forceinline__ void block_reduce_fixed(double (&v)[NV], double* red 
     __syncthreads();
 }
 
+// The FP64 moments of a cell, h^2 sum_i Q_i phi(v_i) for phi = 1, v_0, v_1,
+// |v|^2 with v = -L + (y, x) h, from the integer-weighted sums
+// M = sum q (1, y, x, y^2 + x^2):
+//   m_0 = h^2 M0,  m_1 = h^2 (h M1 - L M0),  m_2 = h^2 (h M2 - L M0),
+//   m_3 = h^2 (h^2 M3 - 2 L h (M1 + M2) + 2 L^2 M0).
+// A thread sums its points in the kernel's type.  In FP32 the sums are
+// compensated (each product split exactly by an fma, each sum by TwoSum),
+// which over a thread's few points is as accurate as FP64 arithmetic while
+// keeping off the FP64 pipe (1/64 of the FP32 rate on this part); the block
+// reduction and the combination above are FP64.
+template <typename T>
+struct CellMoments {
+    T s[4], c[4];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) s[i] = c[i] = T(0);
+    }
+    __device__ __forceinline__ void add(const T q, const int y, const int x) {
+        if constexpr (sizeof(T) == 4) {
+            const float w[3] = {(float)y, (float)x, (float)(y * y + x * x)};  // exact integers
+            comp_add<float, true>(s[0], c[0], q);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float p = q * w[i];
+                c[i + 1] += fmaf(q, w[i], -p);  // the product's rounding error
+                comp_add<float, true>(s[i + 1], c[i + 1], p);
+            }
+        } else {
+            s[0] += q;
+            s[1] += q * y;
+            s[2] += q * x;
+            s[3] += q * (double)(y * y + x * x);
+        }
+    }
+    __device__ __forceinline__ void finish(double* red, const double h, const double L, double* mom) {
+        double m[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) m[i] = (double)s[i] + (double)c[i];
+        block_reduce_fixed<4>(m, red);
+        if (threadIdx.x == 0) {
+            const double h2 = h * h;
+            mom[0] = h2 * m[0];
+            mom[1] = h2 * (h * m[1] - L * m[0]);
+            mom[2] = h2 * (h * m[2] - L * m[0]);
+            mom[3] = h2 * (h * h * m[3] - 2.0 * L * h * (m[1] + m[2]) + 2.0 * L * L * m[0]);
+        }
+    }
+};
+
+// 2 c_e of pair pr in the kernel's type (FP32 kernels read the plan's FP32
+// copy: no FP64 arithmetic per pair).
+template <typename T>
+__device__ __forceinline__ T pair_weight(const double* __restrict__ pair_c, const float* __restrict__ pair_c2f,
+                                         const int pr) {
+    if constexpr (sizeof(T) == 4) return pair_c2f[pr];
+    else return 2.0 * pair_c[pr];
+}
+
 // One cell, pairs [pb, pe).  Writes Q (or a partial sum of Q) to qcell and,
 // when mom != nullptr, the FP64 moments of the stored values to mom[0..3].
 template <typename T, bool KAHAN, int PPT>
 __device__ __forceinline__ void fused2d_body(const int N, const int H, const int4* __restrict__ pairs,
-                                             const double* __restrict__ pair_c, const int pb, const int pe,
+                                             const double* __restrict__ pair_c, const float* __restrict__ pair_c2f,
+                                             const int pb, const int pe,
                                              const double h, const double L, const T* __restrict__ fcell,
                                              T* __restrict__ qcell, double* __restrict__ mom, T* __restrict__ sF,
                                              T* __restrict__ sP, double* red, const int jd) {
@@ -112,7 +171,7 @@ __device__ __forceinline__ void fused2d_body(const int N, const int H, const int
 
     for (int pr = pb; pr < pe; ++pr) {
         const int4 e = pairs[pr];
-        const T c2 = (T)(2.0 * pair_c[pr]);
+        const T c2 = pair_weight<T>(pair_c, pair_c2f, pr);
         const int se = e.x * RS + e.y;   // +e       (axis 0 = rows, axis 1 = columns)
         const int sp = -e.y * RS + e.x;  // +e^perp = (-e1, e0)
         const int J = e.z;
@@ -214,31 +273,18 @@ __device__ __forceinline__ void fused2d_body(const int N, const int H, const int
         __syncthreads();
     }
 
-    double m[4] = {0.0, 0.0, 0.0, 0.0};
+    CellMoments<T> cm;
+    cm.init();
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         const int idx = tid + k * NT;
         if (idx < NN) {
             const T q = KAHAN ? acc[k] + cmp[k] : acc[k];
             qcell[idx] = q;
-            if (mom) {
-                const int y = idx / N, x = idx - (idx / N) * N;
-                const double v0 = -L + y * h, v1 = -L + x * h, qd = (double)q;
-                m[0] += qd;
-                m[1] += qd * v0;
-                m[2] += qd * v1;
-                m[3] += qd * (v0 * v0 + v1 * v1);
-            }
+            if (mom) cm.add(q, idx / N, idx - (idx / N) * N);
         }
     }
-    if (mom) {
-        block_reduce_fixed<4>(m, red);
-        if (tid == 0) {
-            const double h2 = h * h;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) mom[i] = h2 * m[i];
-        }
-    }
+    if (mom) cm.finish(red, h, L, mom);
 }
 
 // Cell body specialised for a compile-time N and H = Ntilde (the common cell
@@ -255,7 +301,7 @@ struct Geo2 {
 
 template <typename T, bool KAHAN, int N, int H, int NT>
 __device__ __forceinline__ void fixed_body(const int4* __restrict__ pairs, const double* __restrict__ pair_c,
-                                           const int pb, const int pe, const double h, const double L,
+                                           const float* __restrict__ pair_c2f, const int pb, const int pe, const double h, const double L,
                                            const T* __restrict__ fcell, T* __restrict__ qcell,
                                            double* __restrict__ mom, T* __restrict__ sF, T* __restrict__ sP,
                                            double* red, const int jd) {
@@ -294,7 +340,7 @@ __device__ __forceinline__ void fixed_body(const int4* __restrict__ pairs, const
 
     for (int pr = pb; pr < pe; ++pr) {
         const int4 e = pairs[pr];
-        const T c2 = (T)(2.0 * pair_c[pr]);
+        const T c2 = pair_weight<T>(pair_c, pair_c2f, pr);
         const int se = e.x * RS + e.y;
         const int sp = -e.y * RS + e.x;
         const int J = e.z;
@@ -382,7 +428,8 @@ __device__ __forceinline__ void fixed_body(const int4* __restrict__ pairs, const
     }
 #undef QDVM_GATHER
 
-    double m[4] = {0.0, 0.0, 0.0, 0.0};
+    CellMoments<T> cm;
+    cm.init();
     if (active) {
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
@@ -390,24 +437,11 @@ __device__ __forceinline__ void fixed_body(const int4* __restrict__ pairs, const
                 const int y = y0 + k * R;
                 const T q = KAHAN ? acc[k] + cmp[k] : acc[k];
                 qcell[y * N + x] = q;
-                if (mom) {
-                    const double v0 = -L + y * h, v1 = -L + x * h, qd = (double)q;
-                    m[0] += qd;
-                    m[1] += qd * v0;
-                    m[2] += qd * v1;
-                    m[3] += qd * (v0 * v0 + v1 * v1);
-                }
+                if (mom) cm.add(q, y, x);
             }
         }
     }
-    if (mom) {
-        block_reduce_fixed<4>(m, red);
-        if (tid == 0) {
-            const double h2 = h * h;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) mom[i] = h2 * m[i];
-        }
-    }
+    if (mom) cm.finish(red, h, L, mom);
 }
 
 // ------------------------------------------------------------------------
@@ -706,7 +740,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
         }
         if (do_loss) loss_fft([&](int k) { return sF[a0 + k * DK]; });
         if (active) {
-            for (int pr = pb; pr < pe; ++pr) gain_direct(P.pairs[pr], (T)(2.0 * P.pair_c[pr]));
+            for (int pr = pb; pr < pe; ++pr) gain_direct(P.pairs[pr], pair_weight<T>(P.pair_c, P.pair_c2f, pr));
         }
     } else {
         // the FFT buffers occupy the cell's place: f at the owned points is
@@ -733,7 +767,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
         bool pending = false;  // window fields still being read by the previous scanned pair
         for (int pr = pb; pr < pe; ++pr) {
             const int4 e = P.pairs[pr];
-            const T c2 = (T)(2.0 * P.pair_c[pr]);
+            const T c2 = pair_weight<T>(P.pair_c, P.pair_c2f, pr);
             if (e.z >= scan_j && e.w > 0) {
                 if (pending) __syncthreads();
                 scan_walks<T, N, H, NT>(sF, sRe, sRp, e, P.pair_scan[pr]);
@@ -754,7 +788,8 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
         }
     }
 
-    double m[4] = {0.0, 0.0, 0.0, 0.0};
+    CellMoments<T> cm;
+    cm.init();
     if (active) {
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
@@ -762,24 +797,11 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
                 const int y = y0 + k * R;
                 const T q = KAHAN ? acc[k] + cmp[k] : acc[k];
                 qcell[y * N + x] = q;
-                if (mom) {
-                    const double v0 = -P.L + y * P.h, v1 = -P.L + x * P.h, qd = (double)q;
-                    m[0] += qd;
-                    m[1] += qd * v0;
-                    m[2] += qd * v1;
-                    m[3] += qd * (v0 * v0 + v1 * v1);
-                }
+                if (mom) cm.add(q, y, x);
             }
         }
     }
-    if (mom) {
-        block_reduce_fixed<4>(m, red);
-        if (tid == 0) {
-            const double h2 = P.h * P.h;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) mom[i] = h2 * m[i];
-        }
-    }
+    if (mom) cm.finish(red, P.h, P.L, mom);
 }
 
 // elements of the f buffer; the P buffer follows it
@@ -812,7 +834,8 @@ __device__ __forceinline__ void run_cell(const PlanDev& P, int pb, int pe, const
             else                                                                                                  \
                 fftloss_body<T, KAHAN, NN, HH, NT, false>(P, pb, pe, f, q, mom, sm, red, do_loss, 0);             \
         } else {                                                                                                  \
-            fixed_body<T, KAHAN, NN, HH, NT>(P.pairs, P.pair_c, pb, pe, P.h, P.L, f, q, mom, sF, sP, red, jd);   \
+            fixed_body<T, KAHAN, NN, HH, NT>(P.pairs, P.pair_c, P.pair_c2f, pb, pe, P.h, P.L, f, q, mom, sF, sP, \
+                                             red, jd);                                                            \
         }                                                                                                         \
         return;                                                                                                   \
     }
@@ -823,7 +846,8 @@ __device__ __forceinline__ void run_cell(const PlanDev& P, int pb, int pe, const
 #undef QDVM_FIXED
     const int k = ppt_pick(NT, (P.N * P.N + NT - 1) / NT);
 #define QDVM_BODY(K)                                                                                          \
-    fused2d_body<T, KAHAN, K>(P.N, P.Ntilde, P.pairs, P.pair_c, pb, pe, P.h, P.L, f, q, mom, sF, sP, red, jd); \
+    fused2d_body<T, KAHAN, K>(P.N, P.Ntilde, P.pairs, P.pair_c, P.pair_c2f, pb, pe, P.h, P.L, f, q, mom, sF, sP, \
+                              red, jd);                                                                          \
     return
     if (NT == 256) {
         if (k == 1) { QDVM_BODY(1); }

@@ -279,6 +279,12 @@ __global__ void k_pair_scan(int n_pairs, int N, int H, int4* pairs, int4* scan) 
     scan[i] = make_int4(r0, s0, r1, s1);
 }
 
+// 2 c_e per pair rounded to FP32, the weight the FP32 evaluators apply.
+__global__ void k_pair_c2f(int n_pairs, const double* __restrict__ pair_c, float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_pairs) out[i] = (float)(2.0 * pair_c[i]);
+}
+
 // Size of e^perp ∩ [-Nt, Nt]^d \ {0} per line (one block per line).
 __global__ void k_plane_count(int d, int n_lines, const int4* lines, int Nt, int* counts) {
     const int4 e = lines[blockIdx.x];
@@ -424,6 +430,7 @@ static void plan_free(qdvm_plan_s* p) {
     cudaFree(p->d_pairs);
     cudaFree(p->d_pair_c);
     cudaFree(p->d_pair_scan);
+    cudaFree(p->d_pair_c2f);
     cudaFree(p->d_plane_start);
     cudaFree(p->d_plane);
     cudaFree(p->d_khat);
@@ -498,6 +505,9 @@ static qdvm_status build_tables(qdvm_plan_s* p) {
         if ((e = cudaMalloc(&p->d_pair_scan, np * sizeof(int4))) != cudaSuccess)
             return fail(qdvm_cuda_status(e, "pair scan table"));
         k_pair_scan<<<(np + 127) / 128, 128>>>(np, p->N, p->Ntilde, p->d_pairs, p->d_pair_scan);
+        if ((e = cudaMalloc(&p->d_pair_c2f, np * sizeof(float))) != cudaSuccess)
+            return fail(qdvm_cuda_status(e, "pair weights"));
+        k_pair_c2f<<<(np + 127) / 128, 128>>>(np, p->d_pair_c, p->d_pair_c2f);
         if ((e = cudaGetLastError()) != cudaSuccess) return fail(qdvm_cuda_status(e, "k_pair_scan"));
     }
     // plane lists e^perp ∩ [-Ntilde, Ntilde]^d \ {0} (in 2D: the segment along e^perp)

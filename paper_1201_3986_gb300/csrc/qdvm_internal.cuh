@@ -30,6 +30,7 @@ struct qdvm_plan_s {
     double* d_c;          // c_e
     int4* d_pairs;        // 2D: (e0, e1, J, S), one per pair
     double* d_pair_c;     // 2D: c_e (= c_{e^perp})
+    float* d_pair_c2f;    // 2D: 2 c_e rounded to FP32 (the FP32 kernels' pair weight)
     int4* d_pair_scan;    // 2D: unimodular complements of e and e^perp (scan engine; S in d_pairs[].w)
     int* d_plane_start;   // 3D: n_lines + 1 offsets into d_plane
     char4* d_plane;       // (l0, l1, l2, 0), l in e^perp, 0 < |l|_inf <= Ntilde
@@ -65,6 +66,7 @@ struct PlanDev {
     const double* c;
     const int4* pairs;
     const double* pair_c;
+    const float* pair_c2f;
     const int4* pair_scan;
     const int* plane_start;
     const char4* plane;
@@ -98,6 +100,7 @@ inline PlanDev plan_dev(const qdvm_plan_s* p) {
     v.c = p->d_c;
     v.pairs = p->d_pairs;
     v.pair_c = p->d_pair_c;
+    v.pair_c2f = p->d_pair_c2f;
     v.pair_scan = p->d_pair_scan;
     v.plane_start = p->d_plane_start;
     v.plane = p->d_plane;
