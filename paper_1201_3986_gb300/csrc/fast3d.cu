@@ -293,6 +293,14 @@ __device__ __forceinline__ T tree_sum(const T (&v)[K]) {
     else return tree_sum<LO, (LO + HI) / 2>(v) + tree_sum<(LO + HI) / 2, HI>(v);
 }
 
+// c_e of row-form line li in the kernel's type (FP32 kernels read the
+// plan's FP32 copy: no FP64 conversion per line).
+template <typename T>
+__device__ __forceinline__ T line_weight(const PlanDev& P, const int li) {
+    if constexpr (sizeof(T) == 4) return __ldg(P.rc_f + li);
+    else return __ldg(P.rc + li);
+}
+
 // Start of a row run in the class-coordinate cell: row offsets (dalpha,
 // dbeta, dgamma) from the unit at (a0, be, ga).
 template <int N, typename T>
@@ -372,14 +380,14 @@ __device__ void class_units(const PlanDev& P, const int (&Mm)[9], int ls, int le
 #pragma unroll
         for (int t = 0; t < 8; ++t) acc[t] = cmp[t] = T(0);
         int4 e = __ldg(P.rline + ls);
-        double cd = __ldg(P.rc + ls);
+        T cd = line_weight<T>(P, ls);
         int rs = __ldg(P.rrow_start + ls);
         for (int li = ls; li < lend; ++li) {
             const int re = __ldg(P.rrow_start + li + 1);
             // next line's descriptor in flight while this line is summed
             const int ln = min(li + 1, lend - 1);
             const int4 e_n = __ldg(P.rline + ln);
-            const double c_n = __ldg(P.rc + ln);
+            const T c_n = line_weight<T>(P, ln);
             T P0 = T(0), D[7], W[8];
 #pragma unroll
             for (int t = 0; t < 7; ++t) D[t] = T(0);
@@ -399,7 +407,7 @@ __device__ void class_units(const PlanDev& P, const int (&Mm)[9], int ls, int le
                     for (int t = 0; t < 8; ++t) W[t] += bp[t] + bm[t];
                 }
             }
-            const T c = (T)cd;
+            const T c = cd;
             T Pk = P0;
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
@@ -513,7 +521,7 @@ __device__ void vjp_class(const PlanDev& P, const int (&Mm)[9], const int (&Mi)[
         }
         __syncthreads();
         const int4 e = __ldg(P.rline + li);
-        const T c = (T)__ldg(P.rc + li);
+        const T c = line_weight<T>(P, li);
         for (int u = tid; u < NU; u += NT) {
             const int ga = u & M, be = (u / N) & M, a0 = (u / N2) * 8;
             T W[8];
@@ -533,7 +541,7 @@ __device__ void vjp_class(const PlanDev& P, const int (&Mm)[9], const int (&Mi)[
     // pass B: Y = g W_e(f) into shared memory, then Pi_e(Y)
     for (int li = ls; li < lend; ++li) {
         const int4 e = __ldg(P.rline + li);
-        const T c = (T)__ldg(P.rc + li);
+        const T c = line_weight<T>(P, li);
         for (int u = tid; u < NU; u += NT) {
             const int ga = u & M, be = (u / N) & M, a0 = (u / N2) * 8;
             T W[8], gv[8];

@@ -440,6 +440,7 @@ static void plan_free(qdvm_plan_s* p) {
     cudaFree(p->d_rclass);
     cudaFree(p->d_rline);
     cudaFree(p->d_rc);
+    cudaFree(p->d_rc_f);
     cudaFree(p->d_rrow_start);
     cudaFree(p->d_rrow);
     p->magic = 0;

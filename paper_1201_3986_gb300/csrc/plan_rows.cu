@@ -278,16 +278,20 @@ qdvm_status build_row_tables(qdvm_plan_s* p) {
         cd[19] = (int)hline.size();
     }
 
+    std::vector<float> hcf(hc.size());  // the FP32 kernels' copy of the weights
+    for (size_t i = 0; i < hc.size(); ++i) hcf[i] = (float)hc[i];
     cudaError_t e;
     if ((e = cudaMalloc(&p->d_rclass, hcls.size() * sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&p->d_rline, hline.size() * sizeof(int4))) != cudaSuccess ||
         (e = cudaMalloc(&p->d_rc, hc.size() * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_rc_f, hc.size() * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&p->d_rrow_start, hrs.size() * sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&p->d_rrow, hrow.size() * sizeof(uchar4))) != cudaSuccess)
         return qdvm_cuda_status(e, "row tables");
     if ((e = cudaMemcpy(p->d_rclass, hcls.data(), hcls.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(p->d_rline, hline.data(), hline.size() * sizeof(int4), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(p->d_rc, hc.data(), hc.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(p->d_rc_f, hcf.data(), hcf.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(p->d_rrow_start, hrs.data(), hrs.size() * sizeof(int), cudaMemcpyHostToDevice)) !=
             cudaSuccess ||
         (e = cudaMemcpy(p->d_rrow, hrow.data(), hrow.size() * sizeof(uchar4), cudaMemcpyHostToDevice)) != cudaSuccess)

@@ -50,6 +50,7 @@ struct qdvm_plan_s {
     int* d_rclass;         // per class: M (3x3, columns u, w2, w3), M^-1, first and end line
     int4* d_rline;         // per line: e in class coordinates (mod N), J
     double* d_rc;          // c_e
+    float* d_rc_f;         // c_e rounded to FP32 (the FP32 kernels' line weight)
     int* d_rrow_start;     // n_lines + 1 offsets into d_rrow
     uchar4* d_rrow;        // per row: start (alpha, beta, gamma) mod N, length
     // host copies
@@ -78,6 +79,7 @@ struct PlanDev {
     const int* rclass;
     const int4* rline;
     const double* rc;
+    const float* rc_f;
     const int* rrow_start;
     const uchar4* rrow;
 };
@@ -112,6 +114,7 @@ inline PlanDev plan_dev(const qdvm_plan_s* p) {
     v.rclass = p->d_rclass;
     v.rline = p->d_rline;
     v.rc = p->d_rc;
+    v.rc_f = p->d_rc_f;
     v.rrow_start = p->d_rrow_start;
     v.rrow = p->d_rrow;
     return v;
