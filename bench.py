@@ -86,27 +86,48 @@ def kernel_source_hash() -> str:
     return h.hexdigest()
 
 
+PROFILE_KEYS = ("source_sha256:", "dram_bytes_per_launch:", "smem_wavefronts_per_launch:", "launch_tuning:")
+
+
+def profiled_fields() -> dict:
+    """The key: value lines of the committed ncu summary of the evaluator, or
+    {} when the kernel sources changed since it was captured."""
+    if not os.path.exists(PROFILE):
+        return {}
+    vals = {}
+    for line in open(PROFILE):
+        t = line.strip().lstrip("-").strip().strip("`")
+        if t.startswith(PROFILE_KEYS):
+            k, v = t.split(":", 1)
+            vals[k.strip()] = v.split("`")[0].split("(")[0].strip()
+    return vals if vals.get("source_sha256") == kernel_source_hash() else {}
+
+
 def profiled_value(key: str):
     """A per-launch count of the evaluator from the committed ncu summary
     (dram_bytes_per_launch, smem_wavefronts_per_launch), or None when the
     kernel sources changed since it was captured."""
-    if not os.path.exists(PROFILE):
-        return None
-    vals = {}
-    for line in open(PROFILE):
-        t = line.strip().lstrip("-").strip().strip("`")
-        if t.startswith(("source_sha256:", "dram_bytes_per_launch:", "smem_wavefronts_per_launch:")):
-            k, v = t.split(":", 1)
-            vals[k.strip()] = v.split("`")[0].split("(")[0].strip()
-    if vals.get("source_sha256") != kernel_source_hash():
-        return None
     try:
-        return int(vals[key])
+        return int(profiled_fields()[key])
     except (KeyError, ValueError):
         return None
 
 
-def profiled_traffic():
+def profiled_tuning():
+    """(threads, direct_j, loss_fft, scan_j) of the profiled launch."""
+    try:
+        return tuple(int(v) for v in profiled_fields()["launch_tuning"].split(","))
+    except (KeyError, ValueError):
+        return None
+
+
+def profiled_traffic(tuning=None):
+    """DRAM bytes per launch of the profiled launch configuration (None for
+    another configuration or changed sources)."""
+    pt = profiled_tuning()
+    t = tuning or {}
+    if pt is None or (t.get("threads"), t.get("loss_fft"), t.get("scan_j")) != (pt[0], pt[2], pt[3]):
+        return None
     return profiled_value("dram_bytes_per_launch")
 
 
@@ -120,8 +141,9 @@ def smem_roofline(kernel_ms: float, clocks: dict, tuning: dict):
     wf = profiled_value("smem_wavefronts_per_launch")
     mhz = clocks.get("sm_mhz") or 2070.0
     t = tuning or {}
-    if wf is None or (t.get("threads"), t.get("loss_fft"), t.get("scan_j")) != (256, 1, 0) or NS != (16, 32, 48, 64) \
-            or NBAR != 8:
+    pt = profiled_tuning()
+    if wf is None or pt is None or (t.get("threads"), t.get("loss_fft"), t.get("scan_j")) != (pt[0], pt[2], pt[3]) \
+            or NS != (16, 32, 48, 64) or NBAR != 8:
         return None
     per_cycle = wf / (kernel_ms / 1e3 * 152 * mhz * 1e6)
     return {"bound": "smem", "achieved": per_cycle, "peak": 1.0, "unit": "wavefronts/cycle/SM",
@@ -454,7 +476,7 @@ def run_gpu(args):
                              "streams overlap step k", "serial_ms_per_step": e2e_serial_ms},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": sm_peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / sm_peak_tflops, "traffic": profiled_traffic(),
+                     "frac": achieved_tflops / sm_peak_tflops, "traffic": profiled_traffic(tuning),
                      "kernel": "k_fused2d_batched", "kernel_ms": kernel_ms,
                      "note": "FP32 peak = 152 SMs x 128 lanes x 2 x 2.07 GHz; algorithmic flops = 11 per point-pair"},
         "roofline_smem": smem_roofline(kernel_ms, clocks, tuning),

@@ -100,7 +100,13 @@ enum { QDVM_ENGINE_AUTO = 0, QDVM_ENGINE_DIRECT = 1, QDVM_ENGINE_SCAN = 2 };
  *               with the default truncation); the lines then only sum the
  *               gain.  Rounding differs from the direct sums (no longer
  *               bit-exact on integer data).  0: direct sums.
- *   scan_j      with loss_fft = 1 in the on-chip 2D evaluator (cells of 16,
+ *               2: as 1, and in the on-chip 2D evaluator with DIRECT
+ *               gathers (scan_j = 0 or above the cell's Ntilde) the same
+ *               inverse transform also returns the window sum W_(1,0) of
+ *               the axis pair {(1,0), (0,1)} (the spectrum is multiplied by
+ *               Ktilde + i D with D the window's real transform), so that
+ *               pair gathers only along (0,1).  Elsewhere 2 acts as 1.
+ *   scan_j      with loss_fft >= 1 in the on-chip 2D evaluator (cells of 16,
  *               32, 48 or 64 points per axis with the default truncation):
  *               pairs {e, e^perp} with J >= scan_j compute both windows with
  *               the SCAN engine, the others with DIRECT gathers; 0 = DIRECT

@@ -456,11 +456,13 @@ __device__ __forceinline__ void fixed_body(const int4* __restrict__ pairs, const
 // COLS), NS = product of the radices already applied.  Butterfly b works on
 // line b % N, so a warp touches consecutive lines (row stride LD = N + 1
 // complex: no bank conflicts on columns or rows).
-// KH: multiply each output by the real factor kh at its mode (row-major
-// N x N), used on the last forward pass to apply the loss kernel's transform.
-template <typename C, int N, int LD, int R, int NS, bool INV, bool COLS, bool KH = false>
+// KH = 1: multiply each output by the real factor kh at its mode (row-major
+// N x N), used on the last forward pass to apply the loss kernel's transform;
+// KH = 2: by the complex factor kh + i dw[row frequency] instead.
+template <typename C, int N, int LD, int R, int NS, bool INV, bool COLS, int KH = 0>
 __device__ __forceinline__ void fft_pass(const C* __restrict__ src, C* __restrict__ dst, const C* __restrict__ tw,
-                                         const decltype(C::x)* __restrict__ kh = nullptr) {
+                                         const decltype(C::x)* __restrict__ kh = nullptr,
+                                         const decltype(C::x)* __restrict__ dw = nullptr) {
     constexpr int NB = N / R;
     for (int b = threadIdx.x; b < N * NB; b += blockDim.x) {
         const int line = b % N, j = b / N;
@@ -482,34 +484,42 @@ __device__ __forceinline__ void fft_pass(const C* __restrict__ src, C* __restric
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int e = idxD + r * NS;
-            if constexpr (KH) {
+            if constexpr (KH == 1) {
                 const auto k = kh[COLS ? e * N + line : line * N + e];
                 v[r].x *= k;
                 v[r].y *= k;
+            } else if constexpr (KH == 2) {
+                const auto k = kh[COLS ? e * N + line : line * N + e];
+                const auto dd = dw[COLS ? e : line];
+                const auto re = v[r].x * k - v[r].y * dd;
+                v[r].y = v[r].x * dd + v[r].y * k;
+                v[r].x = re;
             }
             dst[COLS ? e * LD + line : line * LD + e] = v[r];
         }
     }
 }
 
-template <typename C, int N, int LD, bool INV, bool COLS, bool KH, int NS, int R, int... Rs>
-__device__ __forceinline__ C* fft_passes(C* a, C* b, const C* tw, const decltype(C::x)* kh) {
-    fft_pass<C, N, LD, R, NS, INV, COLS, KH && sizeof...(Rs) == 0>(a, b, tw, kh);
+template <typename C, int N, int LD, bool INV, bool COLS, int KH, int NS, int R, int... Rs>
+__device__ __forceinline__ C* fft_passes(C* a, C* b, const C* tw, const decltype(C::x)* kh,
+                                         const decltype(C::x)* dw) {
+    fft_pass<C, N, LD, R, NS, INV, COLS, sizeof...(Rs) == 0 ? KH : 0>(a, b, tw, kh, dw);
     __syncthreads();
     if constexpr (sizeof...(Rs) > 0)
-        return fft_passes<C, N, LD, INV, COLS, KH, NS * R, Rs...>(b, a, tw, kh);
+        return fft_passes<C, N, LD, INV, COLS, KH, NS * R, Rs...>(b, a, tw, kh, dw);
     else
         return b;
 }
 
 // All N line transforms of length N; returns the buffer holding the result.
-// KH: the last pass also multiplies by kh (see fft_pass).
-template <typename C, int N, int LD, bool INV, bool COLS, bool KH = false>
-__device__ __forceinline__ C* fft_lines(C* a, C* b, const C* tw, const decltype(C::x)* kh = nullptr) {
-    if constexpr (N == 64) return fft_passes<C, N, LD, INV, COLS, KH, 1, 8, 8>(a, b, tw, kh);
-    else if constexpr (N == 48) return fft_passes<C, N, LD, INV, COLS, KH, 1, 3, 4, 4>(a, b, tw, kh);
-    else if constexpr (N == 32) return fft_passes<C, N, LD, INV, COLS, KH, 1, 4, 8>(a, b, tw, kh);
-    else return fft_passes<C, N, LD, INV, COLS, KH, 1, 4, 4>(a, b, tw, kh);  // N == 16
+// KH: the last pass also multiplies by kh (1) or kh + i dw (2) (see fft_pass).
+template <typename C, int N, int LD, bool INV, bool COLS, int KH = 0>
+__device__ __forceinline__ C* fft_lines(C* a, C* b, const C* tw, const decltype(C::x)* kh = nullptr,
+                                        const decltype(C::x)* dw = nullptr) {
+    if constexpr (N == 64) return fft_passes<C, N, LD, INV, COLS, KH, 1, 8, 8>(a, b, tw, kh, dw);
+    else if constexpr (N == 48) return fft_passes<C, N, LD, INV, COLS, KH, 1, 3, 4, 4>(a, b, tw, kh, dw);
+    else if constexpr (N == 32) return fft_passes<C, N, LD, INV, COLS, KH, 1, 4, 8>(a, b, tw, kh, dw);
+    else return fft_passes<C, N, LD, INV, COLS, KH, 1, 4, 4>(a, b, tw, kh, dw);  // N == 16
 }
 
 // Layouts of the FFT body.  Without the SCAN engine: the cell with a
@@ -640,7 +650,7 @@ __device__ __forceinline__ void scan_walks(const T* __restrict__ sF, T* __restri
 template <typename T, bool KAHAN, int N, int H, int NT, bool SCAN>
 __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, const int pe, const T* __restrict__ fcell,
                                              T* __restrict__ qcell, double* __restrict__ mom, unsigned char* smem,
-                                             double* red, const bool do_loss, const int scan_j) {
+                                             double* red, const bool do_loss, const int scan_j, const bool wfft) {
     using C = typename Cplx<T>::type;
     using G = GeoF<N, H, SCAN>;
     constexpr int W = G::W, RS = G::RS, HW = G::HW, LD = G::LD;
@@ -695,10 +705,18 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
             if (k < PPT - 1 || last_ok) comp_add<T, KAHAN>(acc[k], cmp[k], c2 * w[k] * pp[k]);
     };
     // the loss -f (K * f) from the FFT buffers A, B (K's transform in kh);
-    // fk(k) gives f at the k-th owned point
-    auto loss_fft = [&](auto fk) {
+    // fk(k) gives f at the k-th owned point.  With dw (the axis window's
+    // transform, scaled by a power of two s to the size of Ktilde) the
+    // spectrum is multiplied by Ktilde + i s D instead, and the returned
+    // buffer holds K * f + i s W_(1,0): both are real, so one inverse
+    // transform carries the two, and with parts of one size the rounding of
+    // each stays relative to itself.
+    auto loss_fft = [&](auto fk, const T* dw) {
         C* r = fft_lines<C, N, LD, false, false>(A, B, tw);
-        r = fft_lines<C, N, LD, false, true, true>(r, r == A ? B : A, tw, kh);  // times Ktilde
+        if (dw)
+            r = fft_lines<C, N, LD, false, true, 2>(r, r == A ? B : A, tw, kh, dw);  // times Ktilde + i s D
+        else
+            r = fft_lines<C, N, LD, false, true, 1>(r, r == A ? B : A, tw, kh);  // times Ktilde
         r = fft_lines<C, N, LD, true, true>(r, r == A ? B : A, tw);
         r = fft_lines<C, N, LD, true, false>(r, r == A ? B : A, tw);
         if (active) {
@@ -710,6 +728,29 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
                 }
             }
         }
+        return static_cast<const C*>(r);
+    };
+    // the gain of the axis pair {(1,0), (0,1)} (J = H) with s W_(1,0) from
+    // the loss transform's imaginary part rw and W_(0,1) by direct gathers
+    // along the row; c2 arrives divided by s (exact: s is a power of two)
+    auto gain_axis = [&](const C* rw, const T c2) {
+        T w[PPT], pp[PPT];
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            w[k] = (k < PPT - 1 || last_ok) ? rw[(y0 + k * R) * LD + x].y : T(0);
+            pp[k] = T(0);
+        }
+        for (int j = 1; j <= H; ++j) {
+#pragma unroll
+            for (int k = 0; k < PPT; ++k)
+                if (k < PPT - 1 || last_ok) pp[k] += sF[a0 + k * DK + j];
+#pragma unroll
+            for (int k = 0; k < PPT; ++k)
+                if (k < PPT - 1 || last_ok) pp[k] += sF[a0 + k * DK - j];
+        }
+#pragma unroll
+        for (int k = 0; k < PPT; ++k)
+            if (k < PPT - 1 || last_ok) comp_add<T, KAHAN>(acc[k], cmp[k], c2 * w[k] * pp[k]);
     };
     // The cell copy with its periodic halo of width HW (2 HW < N, so a point
     // has at most one image per axis), and optionally the FFT input: the N^2
@@ -738,9 +779,24 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
             acc[k] = T(0);
             cmp[k] = T(0);
         }
-        if (do_loss) loss_fft([&](int k) { return sF[a0 + k * DK]; });
+        // the first pair is the axis pair (lines in order of |e|_inf): with
+        // wfft its W_(1,0) comes out of the loss transform
+        bool wax = false;
+        if (wfft && do_loss && pb < pe) {
+            const int4 e0 = P.pairs[pb];
+            wax = abs(e0.x) + abs(e0.y) == 1 && e0.z == H;
+        }
+        const T* dw = nullptr;
+        if (wax) {
+            if constexpr (sizeof(T) == 8) dw = P.dwin;
+            else dw = P.dwin_f;
+        }
+        const C* rw = nullptr;
+        if (do_loss) rw = loss_fft([&](int k) { return sF[a0 + k * DK]; }, dw);
         if (active) {
-            for (int pr = pb; pr < pe; ++pr) gain_direct(P.pairs[pr], pair_weight<T>(P.pair_c, P.pair_c2f, pr));
+            int pr = pb;
+            if (wax) gain_axis(rw, pair_weight<T>(P.pair_c, P.pair_c2f, pr++) * dw[N]);  // dw[N] = 1 / s
+            for (; pr < pe; ++pr) gain_direct(P.pairs[pr], pair_weight<T>(P.pair_c, P.pair_c2f, pr));
         }
     } else {
         // the FFT buffers occupy the cell's place: f at the owned points is
@@ -759,7 +815,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
         }
         __syncthreads();
         if (do_loss) {
-            loss_fft([&](int k) { return fh[k]; });
+            loss_fft([&](int k) { return fh[k]; }, nullptr);
             __syncthreads();
         }
         fill_cell(false);
@@ -830,9 +886,9 @@ __device__ __forceinline__ void run_cell(const PlanDev& P, int pb, int pe, const
         if (fft && P.khat) {                                                                                      \
             unsigned char* sm = reinterpret_cast<unsigned char*>(sF);                                             \
             if (sj > 0 && sj <= HH)                                                                               \
-                fftloss_body<T, KAHAN, NN, HH, NT, true>(P, pb, pe, f, q, mom, sm, red, do_loss, sj);             \
+                fftloss_body<T, KAHAN, NN, HH, NT, true>(P, pb, pe, f, q, mom, sm, red, do_loss, sj, false);      \
             else                                                                                                  \
-                fftloss_body<T, KAHAN, NN, HH, NT, false>(P, pb, pe, f, q, mom, sm, red, do_loss, 0);             \
+                fftloss_body<T, KAHAN, NN, HH, NT, false>(P, pb, pe, f, q, mom, sm, red, do_loss, 0, fft == 2);   \
         } else {                                                                                                  \
             fixed_body<T, KAHAN, NN, HH, NT>(P.pairs, P.pair_c, P.pair_c2f, pb, pe, P.h, P.L, f, q, mom, sF, sP, \
                                              red, jd);                                                            \

@@ -379,6 +379,27 @@ __global__ void k_twiddles(int N, double2* tw, float2* twf) {
     twf[t] = make_float2((float)c, (float)-s);
 }
 
+// The axis window's transform D(t) = 2 sum_{j=1..J} cos(2 pi j t / N) / N^2,
+// t < N, phases reduced exactly modulo N, times s = the power of two nearest
+// Ktilde(0) / D(0) (the two parts of one inverse transform then have one
+// size); entry N holds 1 / s.  One thread per t.
+__global__ void k_dwin(int N, int J, const double* kh, double* dw, float* dwf) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > N) return;
+    const double d0 = 2.0 * J / ((double)N * (double)N);
+    const int es = kh[0] > 0.0 ? (int)lround(log2(kh[0] / d0)) : 0;
+    double v;
+    if (t == N) {
+        v = ldexp(1.0, -es);
+    } else {
+        double acc = 0.0;
+        for (int j = 1; j <= J; ++j) acc += 2.0 * cospi(2.0 * ((j * t) % N) / N);
+        v = ldexp(acc / ((double)N * (double)N), es);
+    }
+    dw[t] = v;
+    dwf[t] = (float)v;
+}
+
 // Ktilde(xi) = sum_e c_e D_e(xi) Lambda_e(xi) / N^d with
 // D_e = 2 sum_{j=1..J_e} cos(2 pi j (e.xi) / N) (the line factor) and
 // Lambda_e = sum_{l in plane list} cos(2 pi (l.xi) / N) (the e^perp factor):
@@ -437,6 +458,8 @@ static void plan_free(qdvm_plan_s* p) {
     cudaFree(p->d_khat_f);
     cudaFree(p->d_tw);
     cudaFree(p->d_tw_f);
+    cudaFree(p->d_dwin);
+    cudaFree(p->d_dwin_f);
     cudaFree(p->d_rclass);
     cudaFree(p->d_rline);
     cudaFree(p->d_rc);
@@ -557,13 +580,16 @@ static qdvm_status build_tables(qdvm_plan_s* p) {
         if ((e = cudaMalloc(&p->d_khat, n2 * sizeof(double))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_khat_f, n2 * sizeof(float))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_tw, N * sizeof(double2))) != cudaSuccess ||
-            (e = cudaMalloc(&p->d_tw_f, N * sizeof(float2))) != cudaSuccess) {
+            (e = cudaMalloc(&p->d_tw_f, N * sizeof(float2))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_dwin, (N + 1) * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_dwin_f, (N + 1) * sizeof(float))) != cudaSuccess) {
             cudaFree(dK);
             return fail(qdvm_cuda_status(e, "loss kernel tables"));
         }
         k_loss_kernel2d<<<(n2 + 127) / 128, 128>>>(total, p->d_lines, p->d_c, p->d_plane_start, p->d_plane, N, dK);
         k_khat2d<<<(n2 + 127) / 128, 128>>>(N, dK, p->d_khat, p->d_khat_f);
         k_twiddles<<<(N + 63) / 64, 64>>>(N, p->d_tw, p->d_tw_f);
+        k_dwin<<<(N + 64) / 64, 64>>>(N, p->Ntilde, p->d_khat, p->d_dwin, p->d_dwin_f);
         e = cudaDeviceSynchronize();
         cudaFree(dK);
         if (e != cudaSuccess) return fail(qdvm_cuda_status(e, "loss kernel tables"));
@@ -674,7 +700,7 @@ extern "C" qdvm_status qdvm_plan_set_tuning(qdvm_plan_t p, const qdvm_tuning* t)
     if (t->threads != 256 && t->threads != 512) return qdvm_fail(QDVM_ERR_INVALID_ARG, "threads must be 256 or 512");
     if (t->direct_j < 0 || t->direct_j > 2) return qdvm_fail(QDVM_ERR_INVALID_ARG, "direct_j must be 0, 1 or 2");
     if (t->line_chunks < 0) return qdvm_fail(QDVM_ERR_INVALID_ARG, "line_chunks must be >= 0");
-    if (t->loss_fft != 0 && t->loss_fft != 1) return qdvm_fail(QDVM_ERR_INVALID_ARG, "loss_fft must be 0 or 1");
+    if (t->loss_fft < 0 || t->loss_fft > 2) return qdvm_fail(QDVM_ERR_INVALID_ARG, "loss_fft must be 0, 1 or 2");
     if (t->scan_j < 0 || t->scan_j > 64) return qdvm_fail(QDVM_ERR_INVALID_ARG, "scan_j must be in [0, 64]");
     p->tune = *t;
     return QDVM_OK;

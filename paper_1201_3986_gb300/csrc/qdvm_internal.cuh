@@ -42,6 +42,13 @@ struct qdvm_plan_s {
     float* d_khat_f;
     double2* d_tw;
     float2* d_tw_f;
+    // 2D with N <= 64: the transform of the axis window (j e, 0 < |j| <= J,
+    // e = (1, 0), J = Ntilde) at row frequency t < N,
+    // s D(t) = s sum_{0<|j|<=J} cos(2 pi j t / N) / N^2, so that one inverse
+    // FFT of fhat (Ktilde + i s D) returns the loss convolution and s W_(1,0);
+    // s is a power of two of the size of Ktilde(0) / D(0), entry N is 1 / s
+    double* d_dwin;
+    float* d_dwin_f;
     // 3D, N in {16, 32}, Ntilde <= 7: the plane polygons as rows along an
     // in-plane lattice vector u, lines grouped into classes of a common u
     // (plan_rows.cu).  Lines are listed class by class.
@@ -75,6 +82,8 @@ struct PlanDev {
     const float* khat_f;
     const double2* tw;
     const float2* tw_f;
+    const double* dwin;
+    const float* dwin_f;
     int n_rclass;
     const int* rclass;
     const int4* rline;
@@ -110,6 +119,8 @@ inline PlanDev plan_dev(const qdvm_plan_s* p) {
     v.khat_f = p->d_khat_f;
     v.tw = p->d_tw;
     v.tw_f = p->d_tw_f;
+    v.dwin = p->d_dwin;
+    v.dwin_f = p->d_dwin_f;
     v.n_rclass = p->n_rclass;
     v.rclass = p->d_rclass;
     v.rline = p->d_rline;

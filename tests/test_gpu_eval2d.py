@@ -217,13 +217,17 @@ def test_batched_empty_and_invalid_plan_index(q, torch):
     assert oracle.rel_linf(Qn[512:].reshape(16, 16), r["Q"], r["scale"]) <= 1e-5
 
 
-def test_batched_full_workload_sampled(q, torch):
-    """4096 cells, N uniform in {16,32,48,64}, Nbar = 8, FP32 + compensation:
-    the launch the benchmark times.  Sampled cells against the oracle, mass
+@pytest.mark.parametrize("loss_fft", [0, 1, 2])
+def test_batched_full_workload_sampled(q, torch, loss_fft):
+    """4096 cells, N uniform in {16,32,48,64}, Nbar = 8, FP32 + compensation,
+    with the loss by direct sums (0), by the FFT (1), or by the FFT that also
+    gives the axis window (2).  Sampled cells against the oracle, mass
     conservation on every cell."""
     Ns = (16, 32, 48, 64)
     b = synth.batch_2d(4096, Ns=Ns, L=8.0, seed=0)
     plans = [q.Plan(2, n, 8, 8.0, kernel="unit") for n in Ns]
+    for p in plans:
+        p.set_tuning(loss_fft=loss_fft)
     cp, co, f = _batch_tensors(torch, b, Ns, "f32_kahan")
     Q, mom = q.qdvm_eval_batched(plans, cp, co, f, "f32_kahan")
     Qn = Q.cpu().numpy().astype(np.float64)
@@ -244,6 +248,44 @@ def test_batched_full_workload_sampled(q, torch):
         fc = b.cell(c, fin)
         h2 = (16.0 / fc.shape[0]) ** 2
         assert abs(mom[c, 0]) <= 1e-6 * h2 * total_scale(fc, hist[fc.shape[0]])
+
+
+def test_benchmark_launch_full_workload(q, torch):
+    """The benchmark's own launch on its 4096-cell batch: the autotuner picks
+    the configuration, the evaluation is replayed from a captured CUDA graph.
+    Sampled cells against the oracle; on every cell the mass defect (FP32
+    bar) and the moments against an FP64 sum of the stored Q; the graph
+    replay equal bit for bit to a direct call with the same tuning."""
+    Ns = (16, 32, 48, 64)
+    b = synth.batch_2d(4096, Ns=Ns, L=8.0, seed=0)
+    plans = [q.Plan(2, n, 8, 8.0, kernel="unit") for n in Ns]
+    cp, co, f = _batch_tensors(torch, b, Ns, "f32_kahan")
+    ws = torch.empty(q.batched_workspace_bytes(plans, b.n_cells, "f32_kahan"), dtype=torch.uint8, device="cuda")
+    tuning = q.qdvm_tune_batched(plans, cp, co, f, "f32_kahan", workspace=ws)
+    assert all(p.tuning() == tuning for p in plans)
+    Q = torch.full_like(f, float("nan"))
+    mom = torch.full((b.n_cells, 4), float("nan"), dtype=torch.float64, device="cuda")
+    g = q.BatchedGraph(plans, cp, co, f, Q, mom, "f32_kahan", workspace=ws)
+    g.launch()
+    g.launch()
+    torch.cuda.synchronize()
+    Qd, momd = q.qdvm_eval_batched(plans, cp, co, f, "f32_kahan")
+    assert torch.equal(Q, Qd) and torch.equal(mom, momd)
+    Qn = Q.cpu().numpy().astype(np.float64)
+    fin = f.cpu().numpy().astype(np.float64)
+    mom = mom.cpu().numpy()
+    rng = np.random.default_rng(3)
+    for n in Ns:
+        for c in rng.choice(np.nonzero(b.Ns == n)[0], size=2, replace=False):
+            r = oracle.q(b.cell(int(c), fin), 8.0, 8)
+            assert oracle.rel_linf(b.cell(int(c), Qn), r["Q"], r["scale"]) <= 1e-5
+    hist = {n: displacement_histogram(n, 8) for n in Ns}
+    for c in range(b.n_cells):
+        fc, Qc = b.cell(c, fin), b.cell(c, Qn)
+        h2 = (16.0 / fc.shape[0]) ** 2
+        assert abs(mom[c, 0]) <= 1e-6 * h2 * total_scale(fc, hist[fc.shape[0]])
+        mref = oracle.moments(Qc, 8.0)
+        assert np.allclose(mom[c], mref, rtol=0, atol=1e-13 * h2 * np.sum(np.abs(Qc)) * 64)
 
 
 def displacement_histogram(N, Nbar):

@@ -53,14 +53,16 @@ def test_batched_2d_every_tuning(q, torch, threads, direct_j, prec):
 @pytest.mark.parametrize("threads", [256, 512])
 @pytest.mark.parametrize("prec", ["f64", "f32", "f32_kahan"])
 @pytest.mark.parametrize("kernel", ["unit", "hp"])
-def test_fft_loss_batched_every_cell(q, torch, threads, prec, kernel):
+@pytest.mark.parametrize("fft", [1, 2])
+def test_fft_loss_batched_every_cell(q, torch, threads, prec, kernel, fft):
     """Loss as one on-chip FFT convolution per cell (cells of 16/32/48/64
-    points with the default truncation; other sizes keep the direct sums)."""
+    points with the default truncation; other sizes keep the direct sums);
+    with fft = 2 the same transform also gives the axis window W_(1,0)."""
     Ns = (16, 20, 32, 48, 64)
     b = synth.batch_2d(15, Ns=Ns, L=8.0, seed=41)
     plans = [q.Plan(2, n, 8, 8.0, kernel=kernel) for n in Ns]
     for p in plans:
-        p.set_tuning(threads=threads, loss_fft=1)
+        p.set_tuning(threads=threads, loss_fft=fft)
     cp, co, f = _batch(torch, b, Ns, prec)
     Q, M = q.qdvm_eval_batched(plans, cp, co, f, prec)
     Qn = Q.cpu().numpy().astype(np.float64)
@@ -75,11 +77,12 @@ def test_fft_loss_batched_every_cell(q, torch, threads, prec, kernel):
 
 @pytest.mark.parametrize("N,Nbar", [(16, 16), (32, 8), (48, 8), (64, 4), (64, 16)])
 @pytest.mark.parametrize("prec", ["f64", "f32_kahan"])
-def test_fft_loss_single_cell(q, torch, N, Nbar, prec):
+@pytest.mark.parametrize("fft", [1, 2])
+def test_fft_loss_single_cell(q, torch, N, Nbar, prec, fft):
     f = synth.bkw_2d(N, 8.0) if N == 64 else synth.mixture(2, N, 8.0, np.random.default_rng(N))
     f = f if prec == "f64" else f.astype(np.float32).astype(np.float64)
     plan = q.Plan(2, N, Nbar, 8.0, kernel="hp")
-    plan.set_tuning(loss_fft=1)
+    plan.set_tuning(loss_fft=fft)
     Q = q.qdvm_eval(plan, torch.tensor(f, dtype=torch.float64 if prec == "f64" else torch.float32, device="cuda"),
                     prec).cpu().numpy().astype(np.float64)
     r = oracle.q(f, 8.0, Nbar, kernel="hp")
@@ -105,7 +108,7 @@ def test_tuning_rejects_bad_values(q):
     with pytest.raises(q.QdvmError):
         p.set_tuning(direct_j=3)
     with pytest.raises(q.QdvmError):
-        p.set_tuning(loss_fft=2)
+        p.set_tuning(loss_fft=3)
     with pytest.raises(q.QdvmError):
         p.set_tuning(scan_j=-1)
     assert p.tuning() == {"threads": 256, "direct_j": 2, "line_chunks": 0, "loss_fft": 0,
@@ -118,7 +121,7 @@ def test_autotuner_2d_then_parity(q, torch):
     plans = [q.Plan(2, n, 8, 8.0) for n in Ns]
     cp, co, f = _batch(torch, b, Ns, "f32_kahan")
     best = q.qdvm_tune_batched(plans, cp, co, f, "f32_kahan")
-    assert best["threads"] in (256, 512) and best["direct_j"] in (0, 1, 2) and best["loss_fft"] in (0, 1)
+    assert best["threads"] in (256, 512) and best["direct_j"] in (0, 1, 2) and best["loss_fft"] in (0, 1, 2)
     assert 0 <= best["scan_j"] <= 64
     assert all(p.tuning() == best for p in plans)
     Q, _ = q.qdvm_eval_batched(plans, cp, co, f, "f32_kahan")
