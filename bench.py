@@ -1019,9 +1019,10 @@ def main():
     ap.add_argument("--impl", default="qdvm", choices=["qdvm", "reference"])
     ap.add_argument("--ref-cells", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--loss-fft", type=int, default=None, choices=[0, 1],
+    ap.add_argument("--loss-fft", type=int, default=None, choices=[0, 1, 2],
                     help="single3d, jvp3d, vjp3d (default 1): loss as an FFT convolution with row-form gain, or the "
-                         "line engine (0); bkw (default 0): FFT loss in the single-cell 2D evaluator")
+                         "line engine (0); bkw (default 0): FFT loss in the single-cell 2D evaluator (2: the axis "
+                         "window from the same transform)")
     ap.add_argument("--workload", default="batch2d",
                     choices=["batch2d", "batch3d", "jvp3d", "vjp3d", "single3d", "rk2", "bkw", "adaptive", "dtr",
                              "spectral"])
