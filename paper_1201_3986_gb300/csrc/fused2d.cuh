@@ -522,6 +522,26 @@ __device__ __forceinline__ C* fft_lines(C* a, C* b, const C* tw, const decltype(
     else return fft_passes<C, N, LD, INV, COLS, KH, 1, 4, 4>(a, b, tw, kh, dw);  // N == 16
 }
 
+// The points a thread owns in the FFT body.  By default rows y0 + k R of
+// column x (R = NT / N rows per step, the last point predicated off where R
+// does not divide N).  For 48^2 cells on 256 threads, where that would leave
+// 16 threads idle and some warps one point short, each thread owns a 3 x 3
+// tile of points 16 apart instead: (y0 + 16 a, x + 16 b), y0, x < 16,
+// 256 x 9 = 48^2.  A warp then covers two rows of 16 consecutive points,
+// which with a row stride of 16 (mod 32) words hit distinct banks.
+template <int N, int NT>
+struct PointMap {
+    static constexpr bool TILE = N == 48 && NT == 256;
+    static constexpr int R = TILE ? 16 : ((NT / N < N) ? NT / N : N);
+    static constexpr int PPT = TILE ? 9 : (N + R - 1) / R;
+    static constexpr int ACT = TILE ? NT : R * N;  // threads that own points
+    static constexpr bool PARTIAL = !TILE && (N % R) != 0;
+    __host__ __device__ static constexpr int dy(int k) { return TILE ? (k / 3) * 16 : k * R; }
+    __host__ __device__ static constexpr int dx(int k) { return TILE ? (k % 3) * 16 : 0; }
+    __device__ static int x0(int tid) { return TILE ? tid % 16 : tid % N; }
+    __device__ static int y0(int tid) { return TILE ? tid / 16 : tid / N; }
+};
+
 // Layouts of the FFT body.  Without the SCAN engine: the cell with a
 // periodic halo of width H (all the direct gathers need), then two
 // N x (N+1) complex FFT buffers.  With it: a running-sum segment reaches
@@ -654,12 +674,8 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
     using C = typename Cplx<T>::type;
     using G = GeoF<N, H, SCAN>;
     constexpr int W = G::W, RS = G::RS, HW = G::HW, LD = G::LD;
-    constexpr int R = (NT / N < N) ? NT / N : N;
-    constexpr int PPT = (N + R - 1) / R;
-    constexpr int ACT = R * N;
-    constexpr int DK = R * RS;
-    constexpr int DH = R * N;  // address step between a thread's points in the window fields
-    constexpr bool PARTIAL = (N % R) != 0;
+    using PM = PointMap<N, NT>;
+    constexpr int PPT = PM::PPT;
     const int tid = threadIdx.x;
     T* sF = reinterpret_cast<T*>(smem);
     T* sRe = reinterpret_cast<T*>(smem + cell_bytes<T, N, H, SCAN>());
@@ -676,10 +692,10 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
         kh = reinterpret_cast<const T*>(P.khat_f);
     }
 
-    const bool active = tid < ACT;
-    const int x = tid % N, y0 = tid / N;
+    const bool active = tid < PM::ACT;
+    const int x = PM::x0(tid), y0 = PM::y0(tid);  // the thread's first point; point k at + (dy(k), dx(k))
     const int a0 = (y0 + HW) * RS + x + HW;
-    const bool last_ok = !PARTIAL || (y0 + (PPT - 1) * R < N);
+    const bool last_ok = !PM::PARTIAL || (y0 + PM::dy(PPT - 1) < N);
     T acc[PPT], cmp[PPT];
 
     // the direct gathers of the gain's two windows, 2 c_e W_e W_{e^perp}
@@ -693,7 +709,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
         for (int j = 1; j <= e.z; ++j) {
 #define QDVM_GATHER(arr, off)                                                                \
     b = sF + a0 + (off);                                                                     \
-    _Pragma("unroll") for (int k = 0; k < PPT; ++k) if (k < PPT - 1 || last_ok) arr[k] += b[k * DK];
+    _Pragma("unroll") for (int k = 0; k < PPT; ++k) if (k < PPT - 1 || last_ok) arr[k] += b[PM::dy(k) * RS + PM::dx(k)];
             QDVM_GATHER(w, j * se)
             QDVM_GATHER(w, -j * se)
             QDVM_GATHER(pp, j * sp)
@@ -722,10 +738,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
         if (active) {
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-                if (k < PPT - 1 || last_ok) {
-                    const int y = y0 + k * R;
-                    acc[k] = -fk(k) * r[y * LD + x].x;
-                }
+                if (k < PPT - 1 || last_ok) acc[k] = -fk(k) * r[(y0 + PM::dy(k)) * LD + x + PM::dx(k)].x;
             }
         }
         return static_cast<const C*>(r);
@@ -737,16 +750,16 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
         T w[PPT], pp[PPT];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-            w[k] = (k < PPT - 1 || last_ok) ? rw[(y0 + k * R) * LD + x].y : T(0);
+            w[k] = (k < PPT - 1 || last_ok) ? rw[(y0 + PM::dy(k)) * LD + x + PM::dx(k)].y : T(0);
             pp[k] = T(0);
         }
         for (int j = 1; j <= H; ++j) {
 #pragma unroll
             for (int k = 0; k < PPT; ++k)
-                if (k < PPT - 1 || last_ok) pp[k] += sF[a0 + k * DK + j];
+                if (k < PPT - 1 || last_ok) pp[k] += sF[a0 + PM::dy(k) * RS + PM::dx(k) + j];
 #pragma unroll
             for (int k = 0; k < PPT; ++k)
-                if (k < PPT - 1 || last_ok) pp[k] += sF[a0 + k * DK - j];
+                if (k < PPT - 1 || last_ok) pp[k] += sF[a0 + PM::dy(k) * RS + PM::dx(k) - j];
         }
 #pragma unroll
         for (int k = 0; k < PPT; ++k)
@@ -792,7 +805,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
             else dw = P.dwin_f;
         }
         const C* rw = nullptr;
-        if (do_loss) rw = loss_fft([&](int k) { return sF[a0 + k * DK]; }, dw);
+        if (do_loss) rw = loss_fft([&](int k) { return sF[a0 + PM::dy(k) * RS + PM::dx(k)]; }, dw);
         if (active) {
             int pr = pb;
             if (wax) gain_axis(rw, pair_weight<T>(P.pair_c, P.pair_c2f, pr++) * dw[N]);  // dw[N] = 1 / s
@@ -809,7 +822,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
         static_assert(2 * HW < N, "one periodic image per axis");
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-            fh[k] = (active && (k < PPT - 1 || last_ok)) ? fcell[(y0 + k * R) * N + x] : T(0);
+            fh[k] = (active && (k < PPT - 1 || last_ok)) ? fcell[(y0 + PM::dy(k)) * N + x + PM::dx(k)] : T(0);
             acc[k] = T(0);
             cmp[k] = T(0);
         }
@@ -832,7 +845,8 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
                         if (k < PPT - 1 || last_ok) {
-                            const T we = sRe[h0 + k * DH] - fh[k], wp = sRp[h0 + k * DH] - fh[k];
+                            const int hk = h0 + PM::dy(k) * N + PM::dx(k);
+                            const T we = sRe[hk] - fh[k], wp = sRp[hk] - fh[k];
                             comp_add<T, KAHAN>(acc[k], cmp[k], c2 * we * wp);
                         }
                     }
@@ -850,10 +864,10 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
             if (k < PPT - 1 || last_ok) {
-                const int y = y0 + k * R;
+                const int y = y0 + PM::dy(k), xk = x + PM::dx(k);
                 const T q = KAHAN ? acc[k] + cmp[k] : acc[k];
-                qcell[y * N + x] = q;
-                if (mom) cm.add(q, y, x);
+                qcell[y * N + xk] = q;
+                if (mom) cm.add(q, y, xk);
             }
         }
     }
