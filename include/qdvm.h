@@ -78,7 +78,10 @@ enum { QDVM_F64 = 0, QDVM_F32 = 1, QDVM_F32_KAHAN = 2 };
  * otherwise).  Measured on GB300: SCAN halves the shared-memory traffic of
  * a pair but adds integer work, so it pays for long windows (J >= 7) and in
  * the single-cell FP64 evaluation; batched FP32 evaluations with Nbar = 8 are
- * fastest with DIRECT. */
+ * fastest with DIRECT.  A third engine serves one window: with
+ * qdvm_tuning.loss_fft = 2 the axis window W_(1,0) is the convolution of f
+ * with its window, taken from the same inverse FFT as the loss (see
+ * qdvm_tuning). */
 enum { QDVM_ENGINE_AUTO = 0, QDVM_ENGINE_DIRECT = 1, QDVM_ENGINE_SCAN = 2 };
 #define QDVM_SCAN_J_DEFAULT 0
 
