@@ -65,9 +65,11 @@ __device__ __forceinline__ void block_reduce_fixed(double (&v)[NV], double* red 
 //   m_3 = h^2 (h^2 M3 - 2 L h (M1 + M2) + 2 L^2 M0).
 // A thread sums its points in the kernel's type.  In FP32 the sums are
 // compensated (each product split exactly by an fma, each sum by TwoSum),
-// which over a thread's few points is as accurate as FP64 arithmetic while
-// keeping off the FP64 pipe (1/64 of the FP32 rate on this part); the block
-// reduction and the combination above are FP64.
+// which is as accurate as FP64 arithmetic while keeping off the FP64 pipe
+// (1/64 of the FP32 rate on this part).  In FP32 the warps also combine
+// their lanes' (sum, compensation) pairs by TwoSum; one warp then adds the
+// warps' pairs in FP64, and the combination above is FP64.  In FP64 the
+// block reduction is a plain FP64 tree.
 template <typename T>
 struct CellMoments {
     T s[4], c[4];
@@ -94,9 +96,42 @@ struct CellMoments {
     }
     __device__ __forceinline__ void finish(double* red, const double h, const double L, double* mom) {
         double m[4];
+        if constexpr (sizeof(T) == 4) {
+            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) m[i] = (double)s[i] + (double)c[i];
-        block_reduce_fixed<4>(m, red);
+            for (int i = 0; i < 4; ++i) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float s2 = __shfl_down_sync(0xffffffffu, s[i], o);
+                    const float c2 = __shfl_down_sync(0xffffffffu, c[i], o);
+                    c[i] += c2;
+                    comp_add<float, true>(s[i], c[i], s2);
+                }
+            }
+            float* rf = reinterpret_cast<float*>(red);  // (sum, compensation) of warp w, moment i at 2 (4 w + i)
+            if (lane == 0) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    rf[2 * (4 * wid + i)] = s[i];
+                    rf[2 * (4 * wid + i) + 1] = c[i];
+                }
+            }
+            __syncthreads();
+            if (wid != 0) return;
+            // lane l takes the pairs 4 w + i = l and l + 32 (i = l % 4, up
+            // to 16 warps), then the lanes of one moment are added in FP64
+            double v = 0.0;
+            if (lane < 4 * nw) v = (double)rf[2 * lane] + (double)rf[2 * lane + 1];
+            if (lane + 32 < 4 * nw) v += (double)rf[2 * (lane + 32)] + (double)rf[2 * (lane + 32) + 1];
+#pragma unroll
+            for (int o = 16; o >= 4; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) m[i] = __shfl_sync(0xffffffffu, v, i);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) m[i] = (double)s[i] + (double)c[i];
+            block_reduce_fixed<4>(m, red);
+        }
         if (threadIdx.x == 0) {
             const double h2 = h * h;
             mom[0] = h2 * m[0];
