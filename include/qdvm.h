@@ -201,8 +201,8 @@ qdvm_status qdvm_eval(qdvm_plan_t plan, const void* f, void* Q, int prec, void* 
  *               h^d sum_i Q_i phi(v_i), phi = 1, v_0..v_{d-1}, |v|^2
  *               (Section 2.1), reduced from the stored Q with FP64
  *               accuracy (on-chip 2D evaluator in FP32: per-thread partials
- *               in compensated FP32, exact products by fma, then an FP64
- *               reduction over the cell).
+ *               in compensated FP32, exact products by fma, combined across
+ *               each warp by TwoSum, then added across the warps in FP64).
  * Cells are scheduled largest first through an atomic work counter kept in
  * the workspace (size from qdvm_batched_workspace); results do not depend on
  * the schedule.  Cells whose plan index is out of range are skipped (their
