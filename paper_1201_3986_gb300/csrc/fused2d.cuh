@@ -117,6 +117,8 @@ struct CellMoments {
                 }
             }
             __syncthreads();
+            // warp 0 alone reads red from here; every body runs barriers
+            // (the cell copy's) before it writes red again for its next cell
             if (wid != 0) return;
             // lane l takes the pairs 4 w + i = l and l + 32 (i = l % 4, up
             // to 16 warps), then the lanes of one moment are added in FP64
