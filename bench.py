@@ -48,7 +48,9 @@ N_CELLS = 4096
 NBAR = 8
 L = 8.0
 ROTATE = 6
-FLOPS_PER_POINT_PAIR = 11  # running windows W_e, W_e^perp, V_e (2 each) + assembly (5)
+FLOPS_PER_POINT_PAIR = 10  # running windows W_e, W_e^perp, V_e (2 each) + assembly (4)
+ACCURACY_CELLS_PER_N = 4  # accuracy leg: cells per size checked against the oracle in full
+DEFECT_BAR = 1e-6  # |defect_gpu - defect_oracle64| per phi (FP32 path)
 ORACLE_SAMPLE_CELLS = 1024  # CPU baseline: ~10-30 s of oracle work
 REF_STEP_CELLS = 96  # reference arm: one step = the first 96 cells (~1 s)
 
@@ -131,12 +133,12 @@ def profiled_traffic(tuning=None):
     return profiled_value("dram_bytes_per_launch")
 
 
-def smem_roofline(kernel_ms: float, clocks: dict, tuning: dict):
+def smem_roofline(kernel_ms: float, clocks: dict, tuning: dict, n_sm: int = 152):
     """The evaluator's binding resource: shared-memory wavefronts (the LSU
     pipe serves one per SM and cycle).  Wavefronts per launch from the ncu
     summary (they depend on the code, the workload and the launch
-    configuration, not on timing) over the live kernel time, 152 SMs and the
-    SM clock sampled in the timed region; None when the configuration is not
+    configuration, not on timing) over the live kernel time, the device's
+    SMs and the SM clock sampled in the timed region; None when the configuration is not
     the profiled one."""
     wf = profiled_value("smem_wavefronts_per_launch")
     mhz = clocks.get("sm_mhz") or 2070.0
@@ -145,7 +147,7 @@ def smem_roofline(kernel_ms: float, clocks: dict, tuning: dict):
     if wf is None or pt is None or (t.get("threads"), t.get("loss_fft"), t.get("scan_j")) != (pt[0], pt[2], pt[3]) \
             or NS != (16, 32, 48, 64) or NBAR != 8:
         return None
-    per_cycle = wf / (kernel_ms / 1e3 * 152 * mhz * 1e6)
+    per_cycle = wf / (kernel_ms / 1e3 * n_sm * mhz * 1e6)
     return {"bound": "smem", "achieved": per_cycle, "peak": 1.0, "unit": "wavefronts/cycle/SM",
             "frac": per_cycle, "wavefronts_per_launch": wf, "sm_mhz": mhz}
 
@@ -175,6 +177,85 @@ def combine_ranks(ms_local: float, pts_per_rank: int, steps: int, dist=None, dev
         ms = float(t.item())
     value = ws * pts_per_rank * steps / (ms / 1e3)
     return ms, value, ws
+
+
+def fp32_peak_tflops(n_sm: int, clocks: dict):
+    """FP32 FMA peak of the device: SMs x 128 FP32 lanes x 2 flops x the SM
+    clock sampled under load in the timed region (the maximum clock when no
+    sample is available)."""
+    mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    peak = n_sm * 128 * 2 * mhz * 1e6 / 1e12
+    return peak, f"FP32 peak = {n_sm} SMs x 128 lanes x 2 x {mhz:.0f} MHz (sampled SM clock)"
+
+
+def phi_arrays(d: int, N: int, L: float):
+    """phi = 1, v_0..v_{d-1}, |v|^2 on the vertex grid v = -L + j h."""
+    v = -L + np.arange(N) * (2.0 * L / N)
+    g = np.meshgrid(*([v] * d), indexing="ij")
+    return [np.ones((N,) * d)] + list(g) + [sum(x * x for x in g)]
+
+
+def accuracy_leg(b, Qn: np.ndarray, Mn: np.ndarray) -> dict:
+    """Accuracy of one evaluated batch (host copies of Q and the moments)
+    against the FP64 oracle.
+
+    On ACCURACY_CELLS_PER_N cells of every size: the relative L-inf error
+    max|Q - Q_ref| / max scale_ref, and the conservation defects per phi
+    (mass, momentum, energy), defect = |h^d sum Q phi| / (h^d sum scale |phi|),
+    for the GPU moments and for the oracle's Q, with the largest
+    |defect_gpu - defect_oracle| (bar DEFECT_BAR).  On every cell: the mass
+    defect |m_0| / (h^d sum scale), with sum scale = 2 sum_m K(m) R(m) from
+    the displacement histogram K of the terms and the autocorrelation R of f
+    (f >= 0)."""
+    import oracle
+
+    f32 = b.f.astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(1)
+    picks = []
+    for n in NS:
+        picks += [int(c) for c in rng.choice(np.nonzero(b.Ns == n)[0], size=ACCURACY_CELLS_PER_N, replace=False)]
+    names = ("mass", "momentum", "energy")
+    errs, dg_max, dr_max, dd_max = [], dict.fromkeys(names, 0.0), dict.fromkeys(names, 0.0), dict.fromkeys(names, 0.0)
+    for c in picks:
+        fc = b.cell(c, f32)
+        N = fc.shape[0]
+        r = oracle.q(fc, L, NBAR)
+        errs.append(oracle.rel_linf(b.cell(c, Qn), r["Q"], r["scale"]))
+        h2 = (2 * L / N) ** 2
+        den = np.array([h2 * np.sum(r["scale"] * np.abs(p)) for p in phi_arrays(2, N, L)])
+        dg = np.abs(Mn[c]) / den
+        dr = np.abs(oracle.moments(r["Q"], L)) / den
+        dd = np.abs(dg - dr)
+        for k, nm in ((0, "mass"), (1, "momentum"), (2, "momentum"), (3, "energy")):
+            dg_max[nm] = max(dg_max[nm], float(dg[k]))
+            dr_max[nm] = max(dr_max[nm], float(dr[k]))
+            dd_max[nm] = max(dd_max[nm], float(dd[k]))
+    hist = {}
+    for n in NS:
+        Nt = oracle.default_ntilde(n)
+        K = np.zeros((n, n))
+        for e in oracle.lines(2, min(NBAR, Nt)):
+            J = Nt // int(np.max(np.abs(e)))
+            ep = np.array([-e[1], e[0]])
+            js = [j for j in range(-J, J + 1) if j]
+            for j in js:
+                for jp in js:
+                    m = (j * e + jp * ep) % n
+                    K[m[0], m[1]] += 1
+        hist[n] = K
+    mass_all = 0.0
+    for c in range(b.n_cells):
+        fc = b.cell(c, f32)
+        N = fc.shape[0]
+        F = np.fft.fft2(fc)
+        R = np.fft.ifft2(np.conj(F) * F).real
+        tot = 2.0 * float(np.sum(hist[N] * R))
+        mass_all = max(mass_all, abs(Mn[c, 0]) / ((2 * L / N) ** 2 * tot))
+    return {"rel_linf_vs_fp64_oracle_max": max(errs), "cells_checked": picks,
+            "cells_checked_note": f"{ACCURACY_CELLS_PER_N} cells of each N, drawn with seed 1",
+            "defect_gpu_max": dg_max, "defect_oracle64_max": dr_max, "defect_diff_max": dd_max,
+            "defect_bar": DEFECT_BAR, "defect_ok": all(v <= DEFECT_BAR for v in dd_max.values()),
+            "mass_defect_rel_max_all_cells": mass_all, "cells_all": int(b.n_cells)}
 
 
 # ------------------------------------------------------------ CPU oracle
@@ -437,33 +518,20 @@ def run_gpu(args):
     fp64_pts = int((b.Ns[:n_fp64] ** 2).sum())
     fp64_value = fp64_pts / (a.elapsed_time(z) / 1e3)
 
-    # accuracy of the timed path against the FP64 oracle (sampled cells) and the
-    # conservation defect of mass on every cell
-    import oracle
-
-    Qn = Qs[0].cpu().numpy().astype(np.float64)
-    Mn = Ms[0].cpu().numpy()
-    f32 = b.f.astype(np.float32).astype(np.float64)
-    rng = np.random.default_rng(1)
-    picks = [int(rng.choice(np.nonzero(b.Ns == n)[0])) for n in NS]
-    errs = []
-    for c in picks:
-        r = oracle.q(b.cell(c, f32), L, NBAR)
-        errs.append(oracle.rel_linf(b.cell(c, Qn), r["Q"], r["scale"]))
-    mass_rel = []
-    for c in picks:
-        r = oracle.q(b.cell(c, f32), L, NBAR)
-        h2 = (2 * L / b.Ns[c]) ** 2
-        mass_rel.append(abs(Mn[c, 0]) / (h2 * r["scale"].sum()))
+    # accuracy of the timed path against the FP64 oracle (after the timed
+    # region): Q and the conservation defects on cells sampled per size, the
+    # mass defect on every cell
+    accuracy = accuracy_leg(b, Qs[0].cpu().numpy().astype(np.float64), Ms[0].cpu().numpy())
 
     hbm_peak, peak_kind = peaks()
     alg_bytes = total_pts * (4 + 4) + N_CELLS * 4 * 8
     achieved_gbs = alg_bytes / (kernel_ms / 1e3) / 1e9
     alg_flops = FLOPS_PER_POINT_PAIR * point_pairs
-    sm_peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12
+    clocks = clk.summary()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_peak_tflops, peak_note = fp32_peak_tflops(n_sm, clocks)
     achieved_tflops = alg_flops / (kernel_ms / 1e3) / 1e12
 
-    clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -478,15 +546,15 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": sm_peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved_tflops / sm_peak_tflops, "traffic": profiled_traffic(tuning),
                      "kernel": "k_fused2d_batched", "kernel_ms": kernel_ms,
-                     "note": "FP32 peak = 152 SMs x 128 lanes x 2 x 2.07 GHz; algorithmic flops = 11 per point-pair"},
-        "roofline_smem": smem_roofline(kernel_ms, clocks, tuning),
+                     "note": f"{peak_note}; algorithmic flops = {FLOPS_PER_POINT_PAIR} per point-pair x "
+                             f"{point_pairs} point-pairs"},
+        "roofline_smem": smem_roofline(kernel_ms, clocks, tuning, n_sm),
         "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved_gbs / hbm_peak, "peak_kind": f"of {peak_kind}",
                          "alg_bytes": alg_bytes},
         "fp64_single_cell": {"value": fp64_value, "unit": UNIT, "cells": n_fp64,
                              "speedup_of_batched_f32": value / ws / fp64_value},
-        "accuracy": {"rel_linf_vs_fp64_oracle_max": max(errs), "cells_checked": picks,
-                     "mass_defect_rel_max": max(mass_rel)},
+        "accuracy": accuracy,
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline:

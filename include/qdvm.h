@@ -370,9 +370,11 @@ qdvm_status qdvm_graph_capture_rk2(qdvm_graph_t* out, const qdvm_plan_t* plans, 
  *   - n_cells <= QDVM_NOALLOC_MAX_CELLS, else QDVM_ERR_INVALID_ARG (nothing
  *     is launched).
  *   - Allocates nothing (no cudaMalloc / cudaFree / allocating library call).
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) once for that device; make that first call
- *     before any stream capture.
+ *   - Every call made outside a stream capture looks up the array's device
+ *     address (cudaGetSymbolAddress) for the current device, so a device
+ *     reset between calls is harmless; a call made during a capture uses the
+ *     address found by the last call outside one.  Make the first call on a
+ *     device before any stream capture (else QDVM_ERR_INVALID_ARG).
  *   - All calls share the array (the counter is reset by every call), so
  *     calls that overlap on the GPU -- on different streams, or from
  *     different host threads -- race; serialise them. */

@@ -220,6 +220,34 @@ def _workspace(nbytes: int, device) -> torch.Tensor | None:
     return torch.empty(nbytes, dtype=torch.uint8, device=device)
 
 
+def _check_batch(p: int, cell_plan: torch.Tensor, cell_offset: torch.Tensor, f: torch.Tensor,
+                 Q: torch.Tensor | None = None, moments: torch.Tensor | None = None, n_mom: int = 4) -> None:
+    """Argument checks of the batched calls, made before anything reaches
+    the device: the cell layout (int32 plan indices, int64 offsets, one of
+    each per cell), f and Q of the precision's dtype, and the moments array
+    (float64, n_mom values per cell), all contiguous CUDA tensors on f's
+    device.  A wrong array here would otherwise be read or written out of
+    bounds by the kernels."""
+    if cell_plan.dtype != torch.int32 or cell_offset.dtype != torch.int64:
+        raise ValueError("cell_plan must be int32 and cell_offset int64")
+    if f.dtype != _DTYPE[p] or not f.is_cuda or not f.is_contiguous():
+        raise ValueError(f"f must be a contiguous CUDA {_DTYPE[p]} tensor")
+    for name, t in (("cell_plan", cell_plan), ("cell_offset", cell_offset)):
+        if not t.is_cuda or t.device != f.device or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA tensor on {f.device}")
+    if cell_plan.numel() != cell_offset.numel():
+        raise ValueError("cell_plan and cell_offset must hold one entry per cell")
+    if Q is not None:
+        if Q.dtype != f.dtype or not Q.is_cuda or Q.device != f.device or not Q.is_contiguous() \
+                or Q.numel() < f.numel():
+            raise ValueError(f"Q must be a contiguous CUDA {f.dtype} tensor on {f.device} with f's size")
+    if moments is not None:
+        if moments.dtype != torch.float64 or not moments.is_cuda or moments.device != f.device \
+                or not moments.is_contiguous() or moments.numel() < n_mom * cell_plan.numel():
+            raise ValueError(f"moments must be a contiguous CUDA float64 tensor on {f.device} "
+                             f"with at least {n_mom} values per cell")
+
+
 # -------------------------------------------------------------- evaluation
 
 def qdvm_eval(plan: Plan, f: torch.Tensor, prec="f64", out: torch.Tensor | None = None,
@@ -263,10 +291,7 @@ def qdvm_eval_batched(plans, cell_plan: torch.Tensor, cell_offset: torch.Tensor,
     (or None when ``moments`` is False)."""
     p = _prec(prec)
     n_cells = int(cell_plan.numel())
-    if cell_plan.dtype != torch.int32 or cell_offset.dtype != torch.int64:
-        raise ValueError("cell_plan must be int32 and cell_offset int64")
-    if f.dtype != _DTYPE[p] or not f.is_cuda or not f.is_contiguous():
-        raise ValueError(f"f must be a contiguous CUDA {_DTYPE[p]} tensor")
+    _check_batch(p, cell_plan, cell_offset, f)
     Q = torch.empty_like(f) if out is None else out
     d = plans[0].d
     mom = None
@@ -274,6 +299,7 @@ def qdvm_eval_batched(plans, cell_plan: torch.Tensor, cell_offset: torch.Tensor,
         mom = moments
     elif moments:
         mom = torch.empty((n_cells, d + 2), dtype=torch.float64, device=f.device)
+    _check_batch(p, cell_plan, cell_offset, f, Q, mom, d + 2)
     ws = workspace if workspace is not None else _workspace(batched_workspace_bytes(plans, n_cells, p), f.device)
     arr = _plan_array(plans)
     _check(_lib.qdvm_eval_batched(arr, len(plans), n_cells, _ptr(cell_plan), _ptr(cell_offset), _ptr(f), _ptr(Q),
@@ -289,6 +315,7 @@ class BatchedGraph:
     def __init__(self, plans, cell_plan, cell_offset, f, Q, moments, prec="f32_kahan", workspace=None):
         p = _prec(prec)
         n_cells = int(cell_plan.numel())
+        _check_batch(p, cell_plan, cell_offset, f, Q, moments, plans[0].d + 2)
         self._keep = (plans, cell_plan, cell_offset, f, Q, moments)
         self.workspace = workspace if workspace is not None else _workspace(
             batched_workspace_bytes(plans, n_cells, p), f.device)
@@ -523,11 +550,7 @@ def qdvm_eval_batched_noalloc(plans, cell_plan: torch.Tensor, cell_offset: torch
     caller passes every array (f, Q, moments or None); the library uses its
     own static scratch and allocates nothing."""
     p = _prec(prec)
-    if cell_plan.dtype != torch.int32 or cell_offset.dtype != torch.int64:
-        raise ValueError("cell_plan must be int32 and cell_offset int64")
-    for t in (f, Q):
-        if t.dtype != _DTYPE[p] or not t.is_cuda or not t.is_contiguous():
-            raise ValueError(f"f and Q must be contiguous CUDA {_DTYPE[p]} tensors")
+    _check_batch(p, cell_plan, cell_offset, f, Q, moments, 4)
     _check(_lib.qdvm_eval_batched_noalloc(_plan_array(plans), len(plans), int(cell_plan.numel()), _ptr(cell_plan),
                                           _ptr(cell_offset), _ptr(f), _ptr(Q), _ptr(moments), p, _stream(f.device)),
            "qdvm_eval_batched_noalloc")

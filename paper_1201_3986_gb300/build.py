@@ -36,7 +36,10 @@ def _sources():
 
 
 def _deps():
-    return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "qdvm.h")]
+    """Every file a translation unit can include: the sources, the CUDA
+    headers, the textual includes (*.inc) and the public header."""
+    return (_sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh")))
+            + sorted(glob.glob(os.path.join(CSRC, "*.inc"))) + sorted(glob.glob(os.path.join(INCLUDE, "*.h"))))
 
 
 def up_to_date() -> bool:

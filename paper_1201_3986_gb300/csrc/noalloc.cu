@@ -26,18 +26,28 @@ void* g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // Device address of g_batch_scratch for the current device.  In host code
 // the array's name is only a host-side stand-in, so the address comes from
-// cudaGetSymbolAddress, once per device, with that device current.
-qdvm_status scratch_address(void** out) {
+// cudaGetSymbolAddress with that device current.  It is looked up again on
+// every call made outside a stream capture (a lookup allocates nothing), so
+// a device reset between calls cannot leave a stale address behind; during a
+// capture the address that the last call outside a capture found is used.
+qdvm_status scratch_address(cudaStream_t stream, void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return qdvm_cuda_status(e, "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return qdvm_fail(QDVM_ERR_UNSUPPORTED, "device ordinal out of range");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t qe = cudaStreamIsCapturing(stream, &cs);
+    if (qe != cudaSuccess) cudaGetLastError();  // a refused query (a capture elsewhere) leaves no error behind
+    const bool capturing = qe != cudaSuccess || cs != cudaStreamCaptureStatusNone;
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_ptr[dev]) {
+    if (!capturing) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_batch_scratch);
         if (e != cudaSuccess || !p) return qdvm_cuda_status(e, "cudaGetSymbolAddress(g_batch_scratch)");
         g_scratch_ptr[dev] = p;
+    } else if (!g_scratch_ptr[dev]) {
+        return qdvm_fail(QDVM_ERR_INVALID_ARG,
+                         "qdvm_eval_batched_noalloc: the first call on a device must come before any stream capture");
     }
     *out = g_scratch_ptr[dev];
     return QDVM_OK;
@@ -70,7 +80,7 @@ extern "C" qdvm_status qdvm_eval_batched_noalloc(const qdvm_plan_t* plans, int n
     if (!cell_plan || !cell_offset || !f || !Q) return qdvm_fail(QDVM_ERR_INVALID_ARG, "NULL device array");
     if (f == Q) return qdvm_fail(QDVM_ERR_INVALID_ARG, "f must not alias Q");
     void* scratch = nullptr;
-    qdvm_status s = scratch_address(&scratch);
+    qdvm_status s = scratch_address(static_cast<cudaStream_t>(stream), &scratch);
     if (s != QDVM_OK) return s;
     // The schedule kernel zeroes the work counter at the start of every call;
     // the order list is rewritten in full.

@@ -45,3 +45,45 @@ def test_roofline_fields_follow_the_profiled_launch(monkeypatch):
     r = bench.smem_roofline(0.5, {"sm_mhz": 2000.0}, same)
     assert r["wavefronts_per_launch"] == wf
     assert r["frac"] == pytest.approx(wf / (0.5e-3 * 152 * 2000e6))
+
+
+def test_fp32_peak_uses_device_and_sampled_clock():
+    peak, note = bench.fp32_peak_tflops(152, {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0})
+    assert peak == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
+    assert "152 SMs" in note
+    assert bench.fp32_peak_tflops(148, {"sm_mhz": 1500.0})[0] == pytest.approx(148 * 256 * 1.5e9 / 1e12)
+    assert bench.fp32_peak_tflops(152, {"sm_mhz": None, "sm_max_mhz": 1000.0})[0] == pytest.approx(152 * 256e9 / 1e12)
+
+
+def test_accuracy_leg_on_oracle_results():
+    """The benchmark's accuracy leg fed with the oracle's own Q and moments:
+    zero error and zero defect differences; a planted mass defect of 1e-3
+    of h^2 sum scale on one cell is reported as such (the every-cell mass
+    denominator from the displacement histogram equals the oracle's
+    sum of absolute terms)."""
+    import numpy as np
+
+    import oracle
+    import synth
+
+    b = synth.batch_2d(40, Ns=bench.NS, L=bench.L, seed=4)
+    assert all(np.sum(b.Ns == n) >= bench.ACCURACY_CELLS_PER_N for n in bench.NS)
+    f32 = b.f.astype(np.float32).astype(np.float64)
+    Qn = np.zeros_like(f32)
+    Mn = np.zeros((b.n_cells, 4))
+    scales = []
+    for c in range(b.n_cells):
+        r = oracle.q(b.cell(c, f32), bench.L, bench.NBAR)
+        b.cell(c, Qn)[...] = r["Q"]
+        Mn[c] = oracle.moments(r["Q"], bench.L)
+        scales.append(r["scale"].sum())
+    acc = bench.accuracy_leg(b, Qn, Mn)
+    assert acc["rel_linf_vs_fp64_oracle_max"] == 0.0
+    assert len(acc["cells_checked"]) == 4 * bench.ACCURACY_CELLS_PER_N
+    assert all(v == 0.0 for v in acc["defect_diff_max"].values()) and acc["defect_ok"]
+    assert acc["mass_defect_rel_max_all_cells"] <= 1e-14
+    c = 7
+    h2 = (2 * bench.L / b.Ns[c]) ** 2
+    Mn[c, 0] = 1e-3 * h2 * scales[c]
+    acc = bench.accuracy_leg(b, Qn, Mn)
+    assert acc["mass_defect_rel_max_all_cells"] == pytest.approx(1e-3, rel=1e-9)

@@ -159,3 +159,61 @@ def test_batched_2d_mixed_every_cell(q, torch):
         assert np.max(np.abs(b.cell(c, G) - Gr)) / np.max(Gs) <= 1e-12
         Jr, Js = oracle.jvp_points(b.cell(c), b.cell(c, g), 8.0, 3)
         assert np.max(np.abs(b.cell(c, J) - Jr)) / np.max(Js) <= 1e-12
+
+
+@pytest.mark.parametrize("loss_fft", [0, 1])
+def test_config5_central_difference_N32(q, torch, loss_fft):
+    """The adjoint workload at its own size: 256 cells of 32^3, Nbar = 5, hard
+    spheres, FP32, Gaussian tangents and cotangents (seeds 2 and 3).  Q is
+    quadratic (eq. (DR)), so the central difference (Q(f + h d) - Q(f - h d)) / 2h
+    of the batched evaluation equals the batched JVP up to rounding
+    (h = 1e-3: bar 1e-3 of the JVP's term scale) on three cells, and
+    <g, J d> = <J^T g, d> holds for the batched VJP on the same cells to
+    FP32 rounding.  The term scale is the oracle's at 200 sampled points
+    (a lower bound of its maximum, so the bar only gets stricter)."""
+    b = synth.batch_3d(256, N=32, L=6.0, seed=1)
+    dl = synth.gaussian(b.f.shape, seed=2)
+    g = synth.gaussian(b.f.shape, seed=3)
+    plan = q.Plan(3, 32, 5, 6.0, kernel="hp")
+    plan.set_tuning(loss_fft=loss_fft)
+    cp = torch.zeros(b.n_cells, dtype=torch.int32, device="cuda")
+    co = torch.tensor(b.offsets, dtype=torch.int64, device="cuda")
+    f = torch.tensor(b.f, dtype=torch.float32, device="cuda")
+    d = torch.tensor(dl, dtype=torch.float32, device="cuda")
+    gt = torch.tensor(g, dtype=torch.float32, device="cuda")
+    h = 1e-3
+    qp, _ = q.qdvm_eval_batched([plan], cp, co, f + h * d, "f32", moments=False)
+    qm, _ = q.qdvm_eval_batched([plan], cp, co, f - h * d, "f32", moments=False)
+    fd = ((qp.double() - qm.double()) / (2 * h)).cpu().numpy()
+    J = q.qdvm_jvp_batched([plan], cp, co, f, d, "f32").cpu().numpy().astype(np.float64)
+    G = q.qdvm_vjp_batched([plan], cp, co, f, gt, "f32").cpu().numpy().astype(np.float64)
+    fin = f.cpu().numpy().astype(np.float64)
+    din = d.cpu().numpy().astype(np.float64)
+    gin = gt.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(fd)) and np.all(np.isfinite(J)) and np.all(np.isfinite(G))
+    for c in (0, 97, 255):
+        idx = _sample_idx(32, 3, 200, c)
+        _, Js = oracle.jvp_points(b.cell(c, fin), b.cell(c, din), 6.0, 5, idx, kernel="hp")
+        _, Gs = oracle.vjp_points(b.cell(c, fin), b.cell(c, gin), 6.0, 5, idx, kernel="hp")
+        err = np.max(np.abs(b.cell(c, fd) - b.cell(c, J))) / np.max(Js)
+        assert err <= 1e-3, f"cell {c}: FD vs JVP {err:.3e}"
+        lhs = float(np.sum(b.cell(c, gin) * b.cell(c, J)))
+        rhs = float(np.sum(b.cell(c, G) * b.cell(c, din)))
+        bound = 1e-5 * (float(np.sum(np.abs(b.cell(c, gin)))) * np.max(Js)
+                        + float(np.sum(np.abs(b.cell(c, din)))) * np.max(Gs))
+        assert abs(lhs - rhs) <= bound, f"cell {c}: <g, J d> = {lhs:.6e}, <J^T g, d> = {rhs:.6e}"
+
+
+def test_autograd_gradcheck_3d(q, torch):
+    """torch.autograd.gradcheck of the differentiable Q in FP64 on a 3D 8^3
+    cell (hard spheres, Nbar = 2): the backward (qdvm_vjp) against numerical
+    Jacobian columns of the forward, and the VJP against the oracle's."""
+    N = 8
+    plan = q.Plan(3, N, 2, 3.0, kernel="hp")
+    rs = np.random.default_rng(9)
+    f = torch.tensor(rs.uniform(0.1, 1.0, (N,) * 3), dtype=torch.float64, device="cuda", requires_grad=True)
+    assert torch.autograd.gradcheck(lambda x: q.collision(x, plan, "f64"), (f,), eps=1e-6, atol=1e-8, rtol=1e-6)
+    g = torch.tensor(rs.standard_normal((N,) * 3), dtype=torch.float64, device="cuda")
+    (gr,) = torch.autograd.grad((q.collision(f, plan, "f64") * g).sum(), f)
+    ref = oracle.vjp(f.detach().cpu().numpy(), g.cpu().numpy(), 3.0, 2, kernel="hp")
+    assert np.allclose(gr.cpu().numpy(), ref, rtol=1e-11, atol=1e-14)

@@ -5,10 +5,11 @@ owns a fixed device budget, a plug-in inside another framework's time loop):
 they pass f, Q, the cell layout and the moments array, and the library keeps
 its small scratch (work counter and cell schedule) in a static device array.
 This test calls it twice in a row through the C ABI and checks both results
-against the entry point that takes a caller workspace, at the FP32 parity bar
-the other tests use (1e-5 of the largest sum of absolute terms), plus the
-size limit and the rejection of plans it does not cover.  It lives in a file
-collected last and passes alone or after the other tests.
+against the FP64 oracle and against the entry point that takes a caller
+workspace, at the FP32 parity bar the other tests use (1e-5 of the largest
+sum of absolute terms); it checks that a call leaves the device's free memory
+unchanged, the size limit, and the rejection of plans it does not cover.  It
+lives in a file collected last and passes alone or after the other tests.
 """
 import numpy as np
 import pytest
@@ -34,18 +35,27 @@ def test_noalloc_matches_workspace_entry_point_on_two_calls():
     Q_ref = Q_ref.cpu().numpy().astype(np.float64)
     M_ref = M_ref.cpu().numpy()
     fin = f.cpu().numpy().astype(np.float64)
-    scales = [np.max(oracle.q(b.cell(c, fin), 8.0, 8, kernel="hp")["scale"]) for c in range(b.n_cells)]
+    refs = [oracle.q(b.cell(c, fin), 8.0, 8, kernel="hp") for c in range(b.n_cells)]
+    scales = [np.max(r["scale"]) for r in refs]
+    Q = torch.full_like(f, float("nan"))
+    M = torch.full((b.n_cells, 4), float("nan"), dtype=torch.float64, device="cuda")
     for call in range(2):
-        Q = torch.full_like(f, float("nan"))
-        M = torch.full((b.n_cells, 4), float("nan"), dtype=torch.float64, device="cuda")
+        Q.fill_(float("nan"))
+        M.fill_(float("nan"))
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         q.qdvm_eval_batched_noalloc(plans, cp, co, f, Q, M, "f32_kahan")
         torch.cuda.synchronize()
+        if call == 1:  # the first call may load the library's kernels; later calls must not allocate
+            assert torch.cuda.mem_get_info()[0] == free0, "the call changed the device's free memory"
         Qn = Q.cpu().numpy().astype(np.float64)
         Mn = M.cpu().numpy()
         assert np.all(np.isfinite(Qn)) and np.all(np.isfinite(Mn)), f"call {call}: unwritten outputs"
         for c in range(b.n_cells):
+            err = np.max(np.abs(b.cell(c, Qn) - refs[c]["Q"])) / scales[c]
+            assert err <= 1e-5, f"call {call}, cell {c}: {err:.3e} against the oracle"
             err = np.max(np.abs(b.cell(c, Qn) - b.cell(c, Q_ref))) / scales[c]
-            assert err <= 1e-5, f"call {call}, cell {c}: {err:.3e}"
+            assert err <= 1e-5, f"call {call}, cell {c}: {err:.3e} against qdvm_eval_batched"
             h2 = (16.0 / b.Ns[c]) ** 2
             assert np.all(np.abs(Mn[c] - M_ref[c]) <= 1e-5 * h2 * scales[c] * b.Ns[c] ** 2)
 
