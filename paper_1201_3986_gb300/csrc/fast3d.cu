@@ -348,6 +348,39 @@ __device__ __forceinline__ const T* row_dispatch(int len, const T* b, T& P0, T (
     }
 }
 
+// A run of LEN values from b added in the (first window, increments) form of
+// row_run: LEN + 7 loads.
+template <int LEN, typename T>
+__device__ __forceinline__ void run_acc(const T* __restrict__ b, T& P0, T (&D)[7]) {
+    T v[LEN + 7];
+#pragma unroll
+    for (int t = 0; t < LEN + 7; ++t) v[t] = b[t];
+    P0 += tree_sum<0, LEN>(v);
+#pragma unroll
+    for (int k = 1; k < 8; ++k) D[k - 1] += v[LEN - 1 + k] - v[k - 1];
+}
+
+// The central row of a class, {a u : 0 < |a| <= A} (the b = 0 row of every
+// line's polygon, u the class's alpha axis), for the unit (a0, be, ga): the
+// segments [-A, -1] and [1, A] along alpha, in the form of row_run.
+template <int N, typename T>
+__device__ __forceinline__ void central_rows(const int A, const T* g, const int be, const int ga, const int a0,
+                                             T& P0, T (&D)[7]) {
+    constexpr int M = N - 1, SA = rows_sa<N>();
+    const T* b = g + (be * N + ga) * SA;
+    const T* lo = b + ((a0 - A) & M);
+    const T* hi = b + ((a0 + 1) & M);
+    switch (A) {
+        case 1: run_acc<1>(lo, P0, D); run_acc<1>(hi, P0, D); break;
+        case 2: run_acc<2>(lo, P0, D); run_acc<2>(hi, P0, D); break;
+        case 3: run_acc<3>(lo, P0, D); run_acc<3>(hi, P0, D); break;
+        case 4: run_acc<4>(lo, P0, D); run_acc<4>(hi, P0, D); break;
+        case 5: run_acc<5>(lo, P0, D); run_acc<5>(hi, P0, D); break;
+        case 6: run_acc<6>(lo, P0, D); run_acc<6>(hi, P0, D); break;
+        default: run_acc<7>(lo, P0, D); run_acc<7>(hi, P0, D); break;
+    }
+}
+
 // Plane sums of one line, rows [rs, re), for the unit (a0, be, ga):
 // P0 and D as in row_run.  Row descriptors are fetched two rows ahead and
 // row starts one row ahead.
@@ -369,16 +402,23 @@ __device__ __forceinline__ void plane_rows(const uchar4* __restrict__ rows, int 
 // Sums over the lines [ls, lend) of one class for the thread's units of 8
 // consecutive alpha points and adds them at the points' cell indices
 // p = M q (mod N).  Plane sums come from the rows of g; line windows from g
-// (WG false) or from the global copy gw (WG true).
+// (WG false) or from the global copy gw (WG true).  With A > 0 the first nc
+// rows of every line are the class's central row {a u : 0 < |a| <= A}, summed
+// once per unit (central_rows) and taken as the start of each line's plane
+// sums.
 template <typename T, bool KAHAN, int N, bool WG>
-__device__ void class_units(const PlanDev& P, const int (&Mm)[9], int ls, int lend, const T* __restrict__ g,
-                            const T* gw, T* __restrict__ dst, T* __restrict__ comp) {
+__device__ void class_units(const PlanDev& P, const int (&Mm)[9], int ls, int lend, const int A, const int nc,
+                            const T* __restrict__ g, const T* gw, T* __restrict__ dst, T* __restrict__ comp) {
     constexpr int N2 = N * N, M = N - 1, SA = rows_sa<N>(), SW = rows_sw<N>(), NU = (N / 8) * N2;
     for (int u = threadIdx.x; u < NU; u += blockDim.x) {
         const int ga = u & M, be = (u / N) & M, a0 = (u / N2) * 8;
         T acc[8], cmp[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) acc[t] = cmp[t] = T(0);
+        T C0 = T(0), CD[7];
+#pragma unroll
+        for (int t = 0; t < 7; ++t) CD[t] = T(0);
+        if (A > 0) central_rows<N>(A, g, be, ga, a0, C0, CD);
         int4 e = __ldg(P.rline + ls);
         T cd = line_weight<T>(P, ls);
         int rs = __ldg(P.rrow_start + ls);
@@ -388,12 +428,12 @@ __device__ void class_units(const PlanDev& P, const int (&Mm)[9], int ls, int le
             const int ln = min(li + 1, lend - 1);
             const int4 e_n = __ldg(P.rline + ln);
             const T c_n = line_weight<T>(P, ln);
-            T P0 = T(0), D[7], W[8];
+            T P0 = C0, D[7], W[8];
 #pragma unroll
-            for (int t = 0; t < 7; ++t) D[t] = T(0);
+            for (int t = 0; t < 7; ++t) D[t] = CD[t];
 #pragma unroll
             for (int t = 0; t < 8; ++t) W[t] = T(0);
-            plane_rows<N>(P.rrow, rs, re, g, be, ga, a0, P0, D);
+            plane_rows<N>(P.rrow, rs + nc, re, g, be, ga, a0, P0, D);
             for (int j = 1; j <= e.w; ++j) {
                 if (WG) {
                     const T* bp = gw + (((be + j * e.y) & M) * SW + ((a0 + j * e.x) & M)) * N + ((ga + j * e.z) & M);
@@ -673,7 +713,10 @@ __device__ void rows3d_item(const PlanDev& P, const int lb, const int le, const 
             relayout_smem<T, N>(Mi, rsrc, g);
             if (MODE == F3_JVP) relayout_glob<T, N>(Mi, wsrc, gw);
             __syncthreads();
-            class_units<T, KAHAN, N, MODE == F3_JVP>(P, Mm, ls, lend, g, gw, dst, comp);
+            // the shared central row: A = floor(Ntilde / |u|_inf), u = (Mm[0], Mm[3], Mm[6])
+            const int un = max(abs(Mm[0]), max(abs(Mm[3]), abs(Mm[6])));
+            const int A = P.Ntilde / un;
+            class_units<T, KAHAN, N, MODE == F3_JVP>(P, Mm, ls, lend, A, A > 0 ? 2 : 0, g, gw, dst, comp);
             __syncthreads();
         }
     }

@@ -14,6 +14,11 @@
 //
 // u is chosen per line among short vectors to minimise the loads, allowing
 // 15% over the best choice so that few classes cover all lines (greedy).
+//
+// The row b = 0 of every line of a class is the same set {a u : 0 < |a| <= A},
+// A = floor(Ntilde / |u|_inf): the line window of u itself.  When A >= 1 each
+// line lists these two segments first, so that an evaluator may sum them
+// once per class (A follows from u, the first column of the class matrix).
 #include <algorithm>
 #include <array>
 #include <cstdlib>
@@ -250,6 +255,8 @@ qdvm_status build_row_tables(qdvm_plan_s* p) {
                 cd[9 + 3 * r + c] = Mi[r][c];
             }
         cd[18] = (int)hline.size();
+        // the central row b = 0 of every line: [-A, -1] and [1, A]
+        const int A = Nt / inf_norm(u);
         for (int i : cls_lines[k]) {
             const Option* o = nullptr;
             for (const Option& q : opts[i])
@@ -266,7 +273,16 @@ qdvm_status build_row_tables(qdvm_plan_s* p) {
             }
             hline.push_back(make_int4(mod(ep[0], N), mod(ep[1], N), mod(ep[2], N), q.w));
             hc.push_back(p->h_c[i]);
-            for (const Seg& s : o->segs) {
+            // central segments first, then the other rows in order of b
+            std::vector<Seg> segs;
+            for (const Seg& s : o->segs)
+                if (s.b == 0) segs.push_back(s);
+            const bool has_central = segs.size() == 2 && segs[0].a0 == -A && segs[0].a1 == -1 && segs[1].a0 == 1 &&
+                                     segs[1].a1 == A;
+            if (A >= 1 ? !has_central : !segs.empty()) return QDVM_OK;
+            for (const Seg& s : o->segs)
+                if (s.b != 0) segs.push_back(s);
+            for (const Seg& s : segs) {
                 const int len = s.a1 - s.a0 + 1;
                 if (len < 1 || len > QDVM_ROW_MAX) return QDVM_OK;
                 hrow.push_back(make_uchar4((unsigned char)mod(s.a0 + s.b * vp[0], N),
