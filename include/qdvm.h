@@ -103,17 +103,21 @@ enum { QDVM_ENGINE_AUTO = 0, QDVM_ENGINE_DIRECT = 1, QDVM_ENGINE_SCAN = 2 };
  *               with the default truncation); the lines then only sum the
  *               gain.  Rounding differs from the direct sums (no longer
  *               bit-exact on integer data).  0: direct sums.
- *               2: as 1, and in the on-chip 2D evaluator with DIRECT
- *               gathers (scan_j = 0 or above the cell's Ntilde) the same
- *               inverse transform also returns the window sum W_(1,0) of
- *               the axis pair {(1,0), (0,1)} (the spectrum is multiplied by
- *               Ktilde + i D with D the window's real transform), so that
- *               pair gathers only along (0,1).  Elsewhere 2 acts as 1.
+ *               2: as 1, and in the on-chip 2D evaluator the same inverse
+ *               transform also returns one window sum of the axis pair
+ *               {(1,0), (0,1)} (the spectrum is multiplied by Ktilde + i D
+ *               with D the window's real transform): W_(1,0) with DIRECT
+ *               gathers (scan_j = 0 or above the cell's Ntilde), so that
+ *               pair gathers only along (0,1); W_(0,1) with the SCAN engine,
+ *               which walks the other axis.  Elsewhere 2 acts as 1.
  *   scan_j      with loss_fft >= 1 in the on-chip 2D evaluator (cells of 16,
  *               32, 48 or 64 points per axis with the default truncation):
- *               pairs {e, e^perp} with J >= scan_j compute both windows with
- *               the SCAN engine, the others with DIRECT gathers; 0 = DIRECT
- *               for every pair.  0 <= scan_j <= 64.  Ignored elsewhere. */
+ *               pairs {e, e^perp} with J >= scan_j compute their windows
+ *               with the SCAN engine (running sums along strips of the
+ *               lattice lines; the horizontal window (0,1) is gathered, or
+ *               taken from the loss transform with loss_fft = 2), the others
+ *               with DIRECT gathers; 0 = DIRECT for every pair.
+ *               0 <= scan_j <= 64.  Ignored elsewhere. */
 typedef struct {
     int threads;
     int direct_j;

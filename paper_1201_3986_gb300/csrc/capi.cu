@@ -208,9 +208,12 @@ extern "C" qdvm_status qdvm_tune_batched(const qdvm_plan_t* plans, int n_plans, 
         for (int th : {256, 512})
             for (int sj : {0, 2, 3, 4, 5, 7})
                 cand.push_back(qdvm_tuning{th, saved.direct_j, saved.line_chunks, 1, sj});
-        // FFT loss carrying the axis window W_(1,0) too, the other windows by
-        // DIRECT gathers
-        for (int th : {256, 512}) cand.push_back(qdvm_tuning{th, saved.direct_j, saved.line_chunks, 2, 0});
+        // FFT loss carrying one axis window too: W_(1,0) with the other
+        // windows by DIRECT gathers (scan_j = 0), or W_(0,1) with the SCAN
+        // engine walking the pairs from window half-length scan_j up
+        for (int th : {256, 512})
+            for (int sj : {0, 5, 7, 10, 14})
+                cand.push_back(qdvm_tuning{th, saved.direct_j, saved.line_chunks, 2, sj});
     } else {
         const qdvm_tuning fft{saved.threads, saved.direct_j, 0, 1, saved.scan_j};
         const bool f3 = use_fast3d(QDVM_MODE_FWD, b, fft, prec);

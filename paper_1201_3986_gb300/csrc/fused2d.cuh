@@ -495,7 +495,8 @@ __device__ __forceinline__ void fixed_body(const int4* __restrict__ pairs, const
 // complex: no bank conflicts on columns or rows).
 // KH = 1: multiply each output by the real factor kh at its mode (row-major
 // N x N), used on the last forward pass to apply the loss kernel's transform;
-// KH = 2: by the complex factor kh + i dw[row frequency] instead.
+// KH = 2: by the complex factor kh + i dw[row frequency] instead; KH = 3: by
+// kh + i dw[column frequency].
 template <typename C, int N, int LD, int R, int NS, bool INV, bool COLS, int KH = 0>
 __device__ __forceinline__ void fft_pass(const C* __restrict__ src, C* __restrict__ dst, const C* __restrict__ tw,
                                          const decltype(C::x)* __restrict__ kh = nullptr,
@@ -525,9 +526,9 @@ __device__ __forceinline__ void fft_pass(const C* __restrict__ src, C* __restric
                 const auto k = kh[COLS ? e * N + line : line * N + e];
                 v[r].x *= k;
                 v[r].y *= k;
-            } else if constexpr (KH == 2) {
+            } else if constexpr (KH == 2 || KH == 3) {
                 const auto k = kh[COLS ? e * N + line : line * N + e];
-                const auto dd = dw[COLS ? e : line];
+                const auto dd = dw[(KH == 2) == COLS ? e : line];
                 const auto re = v[r].x * k - v[r].y * dd;
                 v[r].y = v[r].x * dd + v[r].y * k;
                 v[r].x = re;
@@ -549,7 +550,7 @@ __device__ __forceinline__ C* fft_passes(C* a, C* b, const C* tw, const decltype
 }
 
 // All N line transforms of length N; returns the buffer holding the result.
-// KH: the last pass also multiplies by kh (1) or kh + i dw (2) (see fft_pass).
+// KH: the last pass also multiplies by kh (1) or kh + i dw (2, 3) (see fft_pass).
 template <typename C, int N, int LD, bool INV, bool COLS, int KH = 0>
 __device__ __forceinline__ C* fft_lines(C* a, C* b, const C* tw, const decltype(C::x)* kh = nullptr,
                                         const decltype(C::x)* dw = nullptr) {
@@ -598,106 +599,57 @@ __host__ __device__ constexpr size_t cell_bytes() {
     return ((size_t)GeoF<N, H, SCAN>::W * GeoF<N, H, SCAN>::RS * sizeof(T) + 15) / 16 * 16;
 }
 
-// One running-sum segment in flight: read pointers, canonical write
-// position and the running value.
-template <typename T>
-struct ScanWalk {
-    const T* lead;
-    const T* trail;
-    T* out;
-    int yw, xw, vy, vx;
-    T R;
-};
+// floor(a / D) from the plan's magic number m = ceil(2^32 / D) (m = 0 for
+// D = 1), exact for the small non-negative a of the strip enumeration.
+__device__ __forceinline__ int strip_div(const int a, const unsigned m) {
+    return m ? (int)__umulhi((unsigned)a, m) : a;
+}
 
+// Scan engine, one piece of direction v = (v0, v1), v0 > 0 (plan table
+// pair_scan: da = (v0, v1, S, npg), db = (lo, ng, magic npg, magic v0)):
+// piece uu starts on row y (one of the first v0 rows of strip k, rows
+// [k S v0, (k + 1) S v0)) at column x = lo + (uu mod npg) and takes up to S
+// steps of v, carrying the running sum R = sum_{|j| <= J} f(. + j v) (the
+// window W_v plus the centre): the first sum costs 2J + 1 loads, each further
+// step one load ahead and one behind.  R is stored at the points of the
+// piece that lie in the cell (out, N x N row-major); the others, left or
+// right of the cell, only carry the sum.  Consecutive pieces start at
+// consecutive columns of one row, so a warp's loads and stores hit distinct
+// banks at every step.  The loads stay inside the cell's 2H halo because the
+// plan keeps (S - 1 + J)|v1| <= 2H and J v0 <= H.
 template <typename T, int N, int H>
-__device__ __forceinline__ ScanWalk<T> scan_start(const T* __restrict__ sF, T* sRe, T* sRp, const int4 e, const int4 w,
-                                                  const int u, const int nseg) {
+__device__ __forceinline__ void strip_walk(const T* __restrict__ sF, T* __restrict__ out, const int4 da,
+                                           const int4 db, const int J, const int uu) {
     using G = GeoF<N, H, true>;
-    constexpr int RS = G::RS, HF = G::HW;
-    const int J = e.z, S = e.w;
-    const bool perp = u >= nseg;
-    const int g = perp ? u - nseg : u;
-    ScanWalk<T> s;
-    s.vy = perp ? -e.y : e.x;
-    s.vx = perp ? e.x : e.y;
-    const int wy = perp ? w.z : w.x, wx = perp ? w.w : w.y;
-    const int beta = g % N, a = (g / N) * S;
-    int by = (a * s.vy + beta * wy) % N;
-    by += by < 0 ? N : 0;
-    int bx = (a * s.vx + beta * wx) % N;
-    bx += bx < 0 ? N : 0;
-    // steps t in [-J, S - 1 + J] are read
-    const int y0 = -J * s.vy, y1 = (S - 1 + J) * s.vy, x0 = -J * s.vx, x1 = (S - 1 + J) * s.vx;
-    int ry = by, rx = bx;
-    if (ry + max(y0, y1) > N + HF - 1) ry -= N;
-    else if (ry + min(y0, y1) < -HF) ry += N;
-    if (rx + max(x0, x1) > N + HF - 1) rx -= N;
-    else if (rx + min(x0, x1) < -HF) rx += N;
-    const int sv = s.vy * RS + s.vx;
-    const T* c = sF + (ry + HF) * RS + (rx + HF);
+    constexpr int RS = G::RS, HW = G::HW;
+    const int v0 = da.x, v1 = da.y, S = da.z, npg = da.w;
+    const int g = strip_div(uu, (unsigned)db.z);
+    const int k = strip_div(g, (unsigned)db.w);
+    const int y = k * S * v0 + (g - k * v0);
+    const int x = db.x + (uu - g * npg);
+    const int steps = min(S, strip_div(N - 1 - y, (unsigned)db.w) + 1);
+    const int sv = v0 * RS + v1, ov = v0 * N + v1;
+    const T* c = sF + (y + HW) * RS + (x + HW);
     T R0 = c[0], R1 = T(0);
 #pragma unroll 4
     for (int j = 1; j <= J; ++j) {
         R0 += c[j * sv];
         R1 += c[-j * sv];
     }
-    s.R = R0 + R1;
-    s.out = perp ? sRp : sRe;
-    s.yw = by;
-    s.xw = bx;
-    s.out[by * N + bx] = s.R;
-    s.lead = c + (J + 1) * sv;
-    s.trail = c - J * sv;
-    return s;
-}
-
-template <typename T, int N, int RS>
-__device__ __forceinline__ void scan_step(ScanWalk<T>& s) {
-    const int sv = s.vy * RS + s.vx;
-    s.R += *s.lead - *s.trail;
-    s.lead += sv;
-    s.trail += sv;
-    s.yw += s.vy;
-    s.yw -= s.yw >= N ? N : 0;
-    s.yw += s.yw < 0 ? N : 0;
-    s.xw += s.vx;
-    s.xw -= s.xw >= N ? N : 0;
-    s.xw += s.xw < 0 ? N : 0;
-    s.out[s.yw * N + s.xw] = s.R;
-}
-
-// Scan engine: R_v(i) = sum_{|j| <= J} f(i + j v) for v = e and v = e^perp
-// (the window W_v plus the centre) into sRe and sRp (N x N, row-major).
-// The torus is cut along each line into segments of S consecutive points:
-// with the complement w of v (det[v w] = 1), segment (k, beta) is
-// {(kS + t) v + beta w : 0 <= t < S}, and the N^2/S segments of v tile Z_N^2.
-// A thread takes a segment, sums its first window (2J + 1 loads), then
-// slides: R += f(i + (J+1) v) - f(i - J v).  The segment's base is placed
-// at the periodic image that keeps every load inside the 2H halo.
-// Consecutive threads take consecutive beta, whose bases differ by w; w has
-// an odd column component, so for N = 32, 64 (row strides = 0 mod 32) a
-// warp's loads and stores hit 32 distinct banks.  A thread advances two of
-// its segments side by side (two independent running sums).
-template <typename T, int N, int H, int NT>
-__device__ __forceinline__ void scan_walks(const T* __restrict__ sF, T* __restrict__ sRe, T* __restrict__ sRp,
-                                           const int4 e, const int4 w) {
-    constexpr int RS = GeoF<N, H, true>::RS;
-    const int S = e.w;
-    const int nseg = N * N / S, items = 2 * nseg;
-    int u = threadIdx.x;
-    for (; u + NT < items; u += 2 * NT) {
-        ScanWalk<T> a = scan_start<T, N, H>(sF, sRe, sRp, e, w, u, nseg);
-        ScanWalk<T> b = scan_start<T, N, H>(sF, sRe, sRp, e, w, u + NT, nseg);
-#pragma unroll 2
-        for (int t = 1; t < S; ++t) {
-            scan_step<T, N, RS>(a);
-            scan_step<T, N, RS>(b);
-        }
-    }
-    if (u < items) {
-        ScanWalk<T> a = scan_start<T, N, H>(sF, sRe, sRp, e, w, u, nseg);
+    T R = R0 + R1;
+    T* o = out + (y * N + x);
+    int xc = x;
+    if ((unsigned)xc < (unsigned)N) *o = R;
+    const T* lead = c + (J + 1) * sv;
+    const T* trail = c - J * sv;
 #pragma unroll 4
-        for (int t = 1; t < S; ++t) scan_step<T, N, RS>(a);
+    for (int t = 1; t < steps; ++t) {
+        R += *lead - *trail;
+        lead += sv;
+        trail += sv;
+        o += ov;
+        xc += v1;
+        if ((unsigned)xc < (unsigned)N) *o = R;
     }
 }
 
@@ -766,8 +718,8 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
     // each stays relative to itself.
     auto loss_fft = [&](auto fk, const T* dw) {
         C* r = fft_lines<C, N, LD, false, false>(A, B, tw);
-        if (dw)
-            r = fft_lines<C, N, LD, false, true, 2>(r, r == A ? B : A, tw, kh, dw);  // times Ktilde + i s D
+        if (dw)  // times Ktilde + i s D: D at the row frequency (W_(1,0)), with SCAN at the column one (W_(0,1))
+            r = fft_lines<C, N, LD, false, true, SCAN ? 3 : 2>(r, r == A ? B : A, tw, kh, dw);
         else
             r = fft_lines<C, N, LD, false, true, 1>(r, r == A ? B : A, tw, kh);  // times Ktilde
         r = fft_lines<C, N, LD, true, true>(r, r == A ? B : A, tw);
@@ -849,23 +801,45 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
             for (; pr < pe; ++pr) gain_direct(P.pairs[pr], pair_weight<T>(P.pair_c, P.pair_c2f, pr));
         }
     } else {
-        // the FFT buffers occupy the cell's place: f at the owned points is
-        // read before the FFT (the loss and the running sums' centres need
-        // it), the cell is copied after it
+        // the FFT buffers occupy the cell's place: the loss reads f at the
+        // owned points from global memory, the cell is copied after it
         const int h0 = y0 * N + x;
-        T fh[PPT];
         if (do_loss)
             for (int i = tid; i < N * N; i += NT) A[(i / N) * LD + (i % N)] = C{fcell[i], T(0)};
         static_assert(2 * HW < N, "one periodic image per axis");
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-            fh[k] = (active && (k < PPT - 1 || last_ok)) ? fcell[(y0 + PM::dy(k)) * N + x + PM::dx(k)] : T(0);
             acc[k] = T(0);
             cmp[k] = T(0);
         }
+        // the first pair is the axis pair (lines in order of |e|_inf): with
+        // wfft its horizontal window W_(0,1), which the strips do not walk,
+        // comes out of the loss transform (scaled by s); it waits in the
+        // window field of its own direction, which that pair leaves unused
+        bool wax = false;
+        if (wfft && do_loss && pb < pe) {
+            const int4 e0 = P.pairs[pb];
+            wax = abs(e0.x) + abs(e0.y) == 1 && e0.z == H;
+        }
+        const T* dw = nullptr;
+        if (wax) {
+            if constexpr (sizeof(T) == 8) dw = P.dwin;
+            else dw = P.dwin_f;
+        }
         __syncthreads();
         if (do_loss) {
-            loss_fft([&](int k) { return fh[k]; }, nullptr);
+            // the transform ping-pongs an even number of passes (four line
+            // transforms of equal pass count), so its result is in A, which
+            // ends before the window fields: the window moves there directly
+            static_assert((size_t)N * LD * sizeof(C) <= cell_bytes<T, N, H, true>(), "A below the window fields");
+            const C* r = loss_fft([&](int k) { return fcell[(y0 + PM::dy(k)) * N + x + PM::dx(k)]; }, dw);
+            if (wax && active) {
+                T* wf = (P.pairs[pb].w & 1) ? sRp : sRe;  // the unwalked direction's field
+#pragma unroll
+                for (int k = 0; k < PPT; ++k)
+                    if (k < PPT - 1 || last_ok)
+                        wf[h0 + PM::dy(k) * N + PM::dx(k)] = r[(y0 + PM::dy(k)) * LD + x + PM::dx(k)].y;
+            }
             __syncthreads();
         }
         fill_cell(false);
@@ -874,17 +848,44 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
         for (int pr = pb; pr < pe; ++pr) {
             const int4 e = P.pairs[pr];
             const T c2 = pair_weight<T>(P.pair_c, P.pair_c2f, pr);
-            if (e.z >= scan_j && e.w > 0) {
+            const int walked = e.z >= scan_j ? e.w : 0;  // bit d: direction d (e, e^perp) walked in strips
+            if (walked) {
                 if (pending) __syncthreads();
-                scan_walks<T, N, H, NT>(sF, sRe, sRp, e, P.pair_scan[pr]);
+                const int4* sd = P.pair_scan + 4 * pr;
+                const int n0 = (walked & 1) ? __ldg(&sd[1].y) * __ldg(&sd[0].w) : 0;
+                const int n1 = (walked & 2) ? __ldg(&sd[3].y) * __ldg(&sd[2].w) : 0;
+                for (int u = tid; u < n0 + n1; u += NT) {
+                    const int d = u >= n0;
+                    strip_walk<T, N, H>(sF, d ? sRp : sRe, __ldg(sd + 2 * d), __ldg(sd + 2 * d + 1), e.z,
+                                        d ? u - n0 : u);
+                }
                 __syncthreads();
                 if (active) {
+                    // the unwalked (horizontal) window: from the loss transform
+                    // for the axis pair with wax (c2 divided by s, exact), else
+                    // gathered along the row
+                    const bool from_fft = wax && pr == pb;
+                    const T cw = from_fft ? c2 * dw[N] : c2;
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
                         if (k < PPT - 1 || last_ok) {
+                            const int a = a0 + PM::dy(k) * RS + PM::dx(k);
                             const int hk = h0 + PM::dy(k) * N + PM::dx(k);
-                            const T we = sRe[hk] - fh[k], wp = sRp[hk] - fh[k];
-                            comp_add<T, KAHAN>(acc[k], cmp[k], c2 * we * wp);
+                            const T fk = sF[a];
+                            T wv[2];
+#pragma unroll
+                            for (int d = 0; d < 2; ++d) {
+                                if ((walked >> d) & 1) {
+                                    wv[d] = (d ? sRp : sRe)[hk] - fk;
+                                } else if (from_fft) {
+                                    wv[d] = (d ? sRp : sRe)[hk];
+                                } else {
+                                    T sum = T(0);
+                                    for (int j = 1; j <= e.z; ++j) sum += sF[a + j] + sF[a - j];
+                                    wv[d] = sum;
+                                }
+                            }
+                            comp_add<T, KAHAN>(acc[k], cmp[k], cw * wv[0] * wv[1]);
                         }
                     }
                 }
@@ -937,7 +938,7 @@ __device__ __forceinline__ void run_cell(const PlanDev& P, int pb, int pe, const
         if (fft && P.khat) {                                                                                      \
             unsigned char* sm = reinterpret_cast<unsigned char*>(sF);                                             \
             if (sj > 0 && sj <= HH)                                                                               \
-                fftloss_body<T, KAHAN, NN, HH, NT, true>(P, pb, pe, f, q, mom, sm, red, do_loss, sj, false);      \
+                fftloss_body<T, KAHAN, NN, HH, NT, true>(P, pb, pe, f, q, mom, sm, red, do_loss, sj, fft == 2);   \
             else                                                                                                  \
                 fftloss_body<T, KAHAN, NN, HH, NT, false>(P, pb, pe, f, q, mom, sm, red, do_loss, 0, fft == 2);   \
         } else {                                                                                                  \

@@ -210,73 +210,97 @@ __global__ void k_pairs(int n_lines, const int4* lines, const double* c, int4* p
     if (threadIdx.x == 0) *n_out = base;
 }
 
-// Unimodular complement of a primitive v = (p, q): w = (r, s) with
-// p s - q r = 1, so that (alpha, beta) -> alpha v + beta w is a bijection of
-// the torus Z_N^2 for every N.  Among the complements w + c v the one
-// returned has s odd (possible for every primitive v: if s is even, q r is
-// odd, so q is odd and s + q is odd).
-__device__ void unimodular_complement(int p, int q, int* r, int* s) {
-    int r0 = p, r1 = q, x0 = 1, x1 = 0, y0 = 0, y1 = 1;  // extended Euclid: p x + q y = +-1
-    while (r1 != 0) {
-        const int k = r0 / r1;
-        int t = r0 - k * r1;
-        r0 = r1;
-        r1 = t;
-        t = x0 - k * x1;
-        x0 = x1;
-        x1 = t;
-        t = y0 - k * y1;
-        y0 = y1;
-        y1 = t;
-    }
-    if (r0 < 0) {
-        x0 = -x0;
-        y0 = -y0;
-    }
-    int rr = -y0, ss = x0;
-    if ((ss & 1) == 0) {
-        rr += p;
-        ss += q;
-    }
-    *r = rr;
-    *s = ss;
+// Tables of the running-sum (scan) line-sum engine of the 2D evaluator, one
+// thread per pair {e, e^perp}.  A direction v = (v0, v1) with v0 != 0 (sign
+// chosen so that v0 > 0) is walked in strips of S v0 rows: a piece starts on
+// one of the first v0 rows of a strip, at any column x in [lo, lo + npg),
+// and advances S steps of v (fewer in the last strip, so that it ends inside
+// the cell), carrying the running window sum R = sum_{|j| <= J} f(. + j v).
+// Every point of the cell lies on exactly one piece; pieces that start left
+// of the cell (lo < 0) or leave it on the right write only their points
+// inside it.  Reads reach (S - 1 + J)|v1| columns beyond the cell, which the
+// evaluator's 2H halo allows when (S - 1 + J)|v1| <= 2H.  The horizontal
+// direction (v0 = 0) is not walked.
+//   scan[4 i + 2 d]     = (v0, v1, S, npg)      d = 0: v = e, d = 1: v = e^perp
+//   scan[4 i + 2 d + 1] = (lo, ng, magic(npg), magic(v0))
+// with ng the number of start rows and magic(D) = ceil(2^32 / D) (0 for
+// D = 1), so that floor(a / D) = umulhi(a, magic(D)) for the small a used.
+//   pairs[i].w = bit d set when direction d is walked.
+// S (at most 32 per direction) minimises a per-thread cost model of a
+// 256-thread CTA: the pieces of both directions dealt out to the threads in
+// rounds, a round costing the longest piece (its first window, 2J + 1 loads
+// and adds, a set-up, and about 10 instructions per further step).
+__host__ __device__ inline unsigned div_magic_of(int D) { return D <= 1 ? 0u : 0xFFFFFFFFu / (unsigned)D + 1u; }
+
+__device__ void strip_desc(int v0, int v1, int J, int N, int H, int S, int4* a, int4* b) {
+    const int m = abs(v1);
+    const int npg = N + (S - 1) * m;
+    const int kf = N / (S * v0);
+    const int ng = kf * v0 + min(v0, N - kf * S * v0);
+    *a = make_int4(v0, v1, S, npg);
+    *b = make_int4(v1 > 0 ? -(S - 1) * v1 : 0, ng, (int)div_magic_of(npg), (int)div_magic_of(v0));
 }
 
-// Tables of the running-sum (scan) line-sum engine of the 2D evaluator, one
-// thread per pair {e, e^perp}:
-//   scan[i] = (complement of e, complement of e^perp), each as (row, column);
-//   pairs[i].w = S, the segment length of the running sums.  A segment is S
-//   consecutive points of an e-orbit; its loads span (S - 1 + 2J) steps of
-//   |e|_inf, which must fit in the 4H rows/columns of the on-chip halo.
-//   Among the divisors of N allowed by that (at most 32), S minimises a
-//   per-thread cost model of a 256-thread CTA: rounds of segments times
-//   (2J + 1 first-window loads + 3 shared-memory accesses per further step
-//   + a fixed set-up).
 __global__ void k_pair_scan(int n_pairs, int N, int H, int4* pairs, int4* scan) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_pairs) return;
     int4 e = pairs[i];
-    const int p = e.x, q = e.y, J = e.z;
-    const int n = max(abs(p), abs(q));
-    const int smax = min(32, (4 * H) / n - 2 * J + 1);
-    int best = 0;
-    long long best_cost = 0;
-    for (int S = 1; S <= smax; ++S) {
-        if (N % S) continue;
-        const long long items = 2LL * N * N / S;
-        const long long rounds = (items + 255) / 256;
-        const long long cost = rounds * (2 * J + 1 + 3 * (S - 1) + 12);
-        if (best == 0 || cost <= best_cost) {
-            best = S;
-            best_cost = cost;
+    const int J = e.z;
+    int v[2][2] = {{e.x, e.y}, {-e.y, e.x}};
+    int smax[2];
+    for (int d = 0; d < 2; ++d) {
+        if (v[d][0] < 0) {
+            v[d][0] = -v[d][0];
+            v[d][1] = -v[d][1];
         }
+        const int m = abs(v[d][1]);
+        smax[d] = 0;
+        if (v[d][0] == 0 || J < 1 || J * v[d][0] > H) continue;  // horizontal: not walked
+        const int s = m ? (2 * H) / m - J + 1 : 32;
+        smax[d] = max(0, min(s, min(32, (N + v[d][0] - 1) / v[d][0])));
     }
-    int r0, s0, r1, s1;
-    unimodular_complement(p, q, &r0, &s0);
-    unimodular_complement(-q, p, &r1, &s1);
-    e.w = best;
+    // cost of direction d with S steps: (pieces, per-piece cost)
+    auto pieces = [&](int d, int S) -> long long {
+        int4 a, b;
+        strip_desc(v[d][0], v[d][1], J, N, H, S, &a, &b);
+        return (long long)a.w * b.y;
+    };
+    int best[2] = {0, 0};
+    double best_cost = -1.0;
+    for (int s0 = (smax[0] ? 1 : 0); s0 <= smax[0]; ++s0)
+        for (int s1 = (smax[1] ? 1 : 0); s1 <= smax[1]; ++s1) {
+            double work = 0.0, cmax = 0.0;
+            long long np = 0;
+            const int ss[2] = {s0, s1};
+            for (int d = 0; d < 2; ++d) {
+                if (!ss[d]) continue;
+                const double c = 4 * J + 20 + 10.0 * ss[d];  // first window, set-up, steps
+                const long long n = pieces(d, ss[d]);
+                np += n;
+                work += (double)n * c;
+                cmax = fmax(cmax, c);
+            }
+            // rounds of pieces over the threads times the longest piece, the
+            // total work breaking ties
+            const double cost = (double)((np + 255) / 256) * cmax + 1e-3 * work;
+            if (best_cost < 0.0 || cost < best_cost) {
+                best_cost = cost;
+                best[0] = s0;
+                best[1] = s1;
+            }
+        }
+    int mask = 0;
+    for (int d = 0; d < 2; ++d) {
+        int4 a = make_int4(0, 0, 0, 0), b = make_int4(0, 0, 0, 0);
+        if (best[d]) {
+            strip_desc(v[d][0], v[d][1], J, N, H, best[d], &a, &b);
+            mask |= 1 << d;
+        }
+        scan[4 * i + 2 * d] = a;
+        scan[4 * i + 2 * d + 1] = b;
+    }
+    e.w = mask;
     pairs[i] = e;
-    scan[i] = make_int4(r0, s0, r1, s1);
 }
 
 // 2 c_e per pair rounded to FP32, the weight the FP32 evaluators apply.
@@ -526,7 +550,7 @@ static qdvm_status build_tables(qdvm_plan_s* p) {
         p->n_pairs = np;
         cudaFree(d_tmp);
         d_tmp = nullptr;
-        if ((e = cudaMalloc(&p->d_pair_scan, np * sizeof(int4))) != cudaSuccess)
+        if ((e = cudaMalloc(&p->d_pair_scan, 4 * np * sizeof(int4))) != cudaSuccess)
             return fail(qdvm_cuda_status(e, "pair scan table"));
         k_pair_scan<<<(np + 127) / 128, 128>>>(np, p->N, p->Ntilde, p->d_pairs, p->d_pair_scan);
         if ((e = cudaMalloc(&p->d_pair_c2f, np * sizeof(float))) != cudaSuccess)

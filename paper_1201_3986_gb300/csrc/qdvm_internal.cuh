@@ -31,7 +31,7 @@ struct qdvm_plan_s {
     int4* d_pairs;        // 2D: (e0, e1, J, S), one per pair
     double* d_pair_c;     // 2D: c_e (= c_{e^perp})
     float* d_pair_c2f;    // 2D: 2 c_e rounded to FP32 (the FP32 kernels' pair weight)
-    int4* d_pair_scan;    // 2D: unimodular complements of e and e^perp (scan engine; S in d_pairs[].w)
+    int4* d_pair_scan;    // 2D: strip descriptors of e and e^perp, 4 per pair (scan engine; walked directions in d_pairs[].w)
     int* d_plane_start;   // 3D: n_lines + 1 offsets into d_plane
     char4* d_plane;       // (l0, l1, l2, 0), l in e^perp, 0 < |l|_inf <= Ntilde
     // 2D with N <= 64 and 3D with N <= 32: the loss as one convolution,

@@ -1,14 +1,15 @@
 """The running-sum (SCAN) line-sum engine of the on-chip 2D evaluator.
 
-With the loss as one FFT convolution per cell (tuning loss_fft = 1), each pair
-{e, e^perp} with window half-length J >= scan_j sums its two windows
-W_e, W_{e^perp} (the alpha_p factors of eq. (decDVM)) as segmented running
-sums along the orbits of e and e^perp on the torus instead of gathering 2J
-values per point.  The set of terms is the same, so:
+With the loss as one FFT convolution per cell (tuning loss_fft >= 1), each
+pair {e, e^perp} with window half-length J >= scan_j sums its windows
+W_e, W_{e^perp} (the alpha_p factors of eq. (decDVM)) as running sums along
+strips of the lattice lines instead of gathering 2J values per point; the
+horizontal window (0,1) is gathered, or with loss_fft = 2 taken from the
+loss transform.  The set of terms is the same, so:
   - against the FP64 oracle the bars are those of every other evaluator;
-  - on integer data every window is an exact integer in both engines, so
-    SCAN and DIRECT give bit-identical Q (same FFT loss, same accumulation
-    order of the same values).
+  - on integer data (loss_fft = 1) every window is an exact integer in both
+    engines, so SCAN and DIRECT give bit-identical Q (same FFT loss, same
+    accumulation order of the same values).
 """
 import numpy as np
 import pytest
@@ -45,15 +46,15 @@ def _batch(torch, b, Ns, prec):
     return cp, co, f
 
 
-@pytest.mark.parametrize("scan_j", [1, 2, 3, 5])
+@pytest.mark.parametrize("scan_j,loss_fft", [(1, 1), (2, 1), (3, 1), (5, 1), (1, 2), (5, 2), (7, 2), (10, 2)])
 @pytest.mark.parametrize("threads", [256, 512])
 @pytest.mark.parametrize("prec", ["f64", "f32", "f32_kahan"])
 @pytest.mark.parametrize("kernel", ["unit", "hp"])
-def test_batched_scan_matches_oracle(q, torch, scan_j, threads, prec, kernel):
+def test_batched_scan_matches_oracle(q, torch, scan_j, loss_fft, threads, prec, kernel):
     b = synth.batch_2d(12, Ns=NS, L=8.0, seed=71 + scan_j)
     plans = [q.Plan(2, n, 8, 8.0, kernel=kernel) for n in NS]
     for p in plans:
-        p.set_tuning(threads=threads, loss_fft=1, scan_j=scan_j)
+        p.set_tuning(threads=threads, loss_fft=loss_fft, scan_j=scan_j)
     cp, co, f = _batch(torch, b, NS, prec)
     Q, M = q.qdvm_eval_batched(plans, cp, co, f, prec)
     Qn = Q.cpu().numpy().astype(np.float64)
@@ -98,13 +99,15 @@ def test_scan_bit_identical_to_direct_on_integer_data(q, torch, threads, prec):
     assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[3])
 
 
-def test_batched_scan_full_workload_sampled(q, torch):
+@pytest.mark.parametrize("scan_j,loss_fft", [(1, 1), (7, 2)])
+def test_batched_scan_full_workload_sampled(q, torch, scan_j, loss_fft):
     """The 4096-cell mixed-size batch with N̄ = 8 in FP32 with compensation,
-    every pair on the SCAN engine; sampled cells against the oracle."""
+    every pair on the SCAN engine, or the long windows (J >= 7) with the
+    axis window from the loss transform; sampled cells against the oracle."""
     b = synth.batch_2d(4096, Ns=NS, L=8.0, seed=0)
     plans = [q.Plan(2, n, 8, 8.0) for n in NS]
     for p in plans:
-        p.set_tuning(loss_fft=1, scan_j=1)
+        p.set_tuning(loss_fft=loss_fft, scan_j=scan_j)
     cp, co, f = _batch(torch, b, NS, "f32_kahan")
     Q, M = q.qdvm_eval_batched(plans, cp, co, f, "f32_kahan")
     Qn = Q.cpu().numpy().astype(np.float64)
