@@ -115,41 +115,61 @@ def profiled_value(key: str):
         return None
 
 
+def tuning_key(tunings: dict) -> str:
+    """The launch configuration of a batched 2D call as one string: per cell
+    size N, the plan's threads,direct_j,loss_fft,scan_j (each cell runs with
+    its own plan's parameters)."""
+    return " ".join(f"{n}={t['threads']},{t['direct_j']},{t['loss_fft']},{t['scan_j']}"
+                    for n, t in sorted(tunings.items()))
+
+
 def profiled_tuning():
-    """(threads, direct_j, loss_fft, scan_j) of the profiled launch."""
-    try:
-        return tuple(int(v) for v in profiled_fields()["launch_tuning"].split(","))
-    except (KeyError, ValueError):
-        return None
+    """The launch configuration (tuning_key) of the profiled launch, or None."""
+    return profiled_fields().get("launch_tuning")
 
 
-def profiled_traffic(tuning=None):
+def profiled_traffic(key=None):
     """DRAM bytes per launch of the profiled launch configuration (None for
     another configuration or changed sources)."""
     pt = profiled_tuning()
-    t = tuning or {}
-    if pt is None or (t.get("threads"), t.get("loss_fft"), t.get("scan_j")) != (pt[0], pt[2], pt[3]):
+    if pt is None or key != pt:
         return None
     return profiled_value("dram_bytes_per_launch")
 
 
-def smem_roofline(kernel_ms: float, clocks: dict, tuning: dict, n_sm: int = 152):
+def smem_roofline(kernel_ms: float, clocks: dict, key, n_sm: int = 152):
     """The evaluator's binding resource: shared-memory wavefronts (the LSU
     pipe serves one per SM and cycle).  Wavefronts per launch from the ncu
     summary (they depend on the code, the workload and the launch
     configuration, not on timing) over the live kernel time, the device's
-    SMs and the SM clock sampled in the timed region; None when the configuration is not
-    the profiled one."""
+    SMs and the SM clock sampled in the timed region; None when the
+    configuration is not the profiled one."""
     wf = profiled_value("smem_wavefronts_per_launch")
     mhz = clocks.get("sm_mhz") or 2070.0
-    t = tuning or {}
     pt = profiled_tuning()
-    if wf is None or pt is None or (t.get("threads"), t.get("loss_fft"), t.get("scan_j")) != (pt[0], pt[2], pt[3]) \
-            or NS != (16, 32, 48, 64) or NBAR != 8:
+    if wf is None or pt is None or key != pt or NS != (16, 32, 48, 64) or NBAR != 8:
         return None
     per_cycle = wf / (kernel_ms / 1e3 * n_sm * mhz * 1e6)
     return {"bound": "smem", "achieved": per_cycle, "peak": 1.0, "unit": "wavefronts/cycle/SM",
             "frac": per_cycle, "wavefronts_per_launch": wf, "sm_mhz": mhz}
+
+
+def set_tunings(plans, spec: str) -> None:
+    """Pin the launch configuration from the command line: one
+    threads,direct_j,loss_fft[,scan_j] for every plan, or per cell size
+    N=threads,direct_j,loss_fft,scan_j entries separated by spaces or ';'."""
+    entries = spec.replace(";", " ").split()
+    per = {}
+    for ent in entries:
+        if "=" in ent:
+            n, v = ent.split("=", 1)
+            per[int(n)] = v
+    for p in plans:
+        v = per.get(p.N, entries[0] if not per else None)
+        if v is None:
+            continue
+        vals = [int(x) for x in v.split(",")]
+        p.set_tuning(threads=vals[0], direct_j=vals[1], loss_fft=vals[2], scan_j=vals[3] if len(vals) > 3 else None)
 
 
 def peaks():
@@ -390,13 +410,11 @@ def run_gpu(args):
     # the library's autotuner picks the launch configuration on this batch;
     # each rotating buffer set is then captured once into a CUDA graph
     if args.tuning:
-        vals = [int(v) for v in args.tuning.split(",")]
-        th, dj, fft = vals[:3]
-        for p in plans:
-            p.set_tuning(threads=th, direct_j=dj, loss_fft=fft, scan_j=vals[3] if len(vals) > 3 else None)
-        tuning = plans[0].tuning()
+        set_tunings(plans, args.tuning)
     else:
-        tuning = q.qdvm_tune_batched(plans, cp, co, fs[0], "f32_kahan", workspace=wss)
+        q.qdvm_tune_batched(plans, cp, co, fs[0], "f32_kahan", workspace=wss)
+    tunings = {int(n): p.tuning() for n, p in zip(NS, plans)}
+    key = tuning_key(tunings)
     graphs = [q.BatchedGraph(plans, cp, co, fs[k], Qs[k], Ms[k], "f32_kahan", workspace=wss) for k in range(ROTATE)]
 
     for g in graphs:  # first replay of a graph uploads it; keep that out of the timed region
@@ -537,18 +555,18 @@ def run_gpu(args):
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": workload_config({"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                                   "tuning": tuning, "launch": "CUDA graph (schedule + persistent evaluator)"}),
+                                   "tuning": key, "launch": "CUDA graph (schedule + persistent evaluator)"}),
         "e2e": {"value": total_pts / (e2e_ms / 1e3) * ws, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
                 "pipelined": "two device buffer sets; copy-in of step k+1 and copy-out of step k-1 on their own "
                              "streams overlap step k", "serial_ms_per_step": e2e_serial_ms},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": sm_peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / sm_peak_tflops, "traffic": profiled_traffic(tuning),
+                     "frac": achieved_tflops / sm_peak_tflops, "traffic": profiled_traffic(key),
                      "kernel": "k_fused2d_batched", "kernel_ms": kernel_ms,
                      "note": f"{peak_note}; algorithmic flops = {FLOPS_PER_POINT_PAIR} per point-pair x "
                              f"{point_pairs} point-pairs"},
-        "roofline_smem": smem_roofline(kernel_ms, clocks, tuning, n_sm),
+        "roofline_smem": smem_roofline(kernel_ms, clocks, key, n_sm),
         "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved_gbs / hbm_peak, "peak_kind": f"of {peak_kind}",
                          "alg_bytes": alg_bytes},
@@ -588,9 +606,10 @@ def run_rk2_workload(args):
     co = torch.tensor(b.offsets, dtype=torch.int64, device=dev)
     f_host = torch.from_numpy(b.f.astype(np.float32))
     fs = [f_host.to(dev) for _ in range(ROTATE)]
-    tuning = q.qdvm_tune_batched(plans, cp, co, fs[0], "f32_kahan",
-                                 workspace=torch.empty(q.batched_workspace_bytes(plans, N_CELLS, "f32_kahan"),
-                                                       dtype=torch.uint8, device=dev))
+    q.qdvm_tune_batched(plans, cp, co, fs[0], "f32_kahan",
+                        workspace=torch.empty(q.batched_workspace_bytes(plans, N_CELLS, "f32_kahan"),
+                                              dtype=torch.uint8, device=dev))
+    tuning = tuning_key({p.N: p.tuning() for p in plans})
     wsb = q.rk2_workspace_bytes(plans, N_CELLS, b.total, "f32_kahan")
     wss = [torch.empty(wsb, dtype=torch.uint8, device=dev) for _ in range(ROTATE)]
     Ms = [torch.empty((N_CELLS, 4), dtype=torch.float64, device=dev) for _ in range(ROTATE)]
@@ -674,7 +693,8 @@ def run_adaptive_workload(args):
     q.select_levels(eps[0], cb, thr, level_plan, out=cps[0])
     wsb = q.batched_workspace_bytes(plans, N_CELLS, "f32_kahan")
     ws = [torch.empty(wsb, dtype=torch.uint8, device=dev) for _ in range(ROTATE)]
-    tuning = q.qdvm_tune_batched(plans, cps[0], co, fs[0], "f32_kahan", workspace=ws[0])
+    q.qdvm_tune_batched(plans, cps[0], co, fs[0], "f32_kahan", workspace=ws[0])
+    tuning = [p.tuning() for p in plans]  # per plan: cell size x level
     # fixed Nbar = 8 on the same batch (level 2 for every cell)
     cp8 = (cb * len(nbars) + 2).to(torch.int32)
 
@@ -1101,7 +1121,8 @@ def main():
     ap.add_argument("--ns", default=None, help="batch2d: comma-separated cell sizes (default 16,32,48,64)")
     ap.add_argument("--cells", type=int, default=256, help="batch3d / jvp3d / vjp3d: number of 32^3 cells; dtr: 2D cells")
     ap.add_argument("--tuning", default=None,
-                    help="pin the launch configuration instead of autotuning: batch2d threads,direct_j,loss_fft[,scan_j]; "
+                    help="pin the launch configuration instead of autotuning: batch2d threads,direct_j,loss_fft[,scan_j] "
+                         "for every plan, or per cell size 'N=threads,direct_j,loss_fft,scan_j ...'; "
                          "batch3d threads,direct_j,loss_fft,line_chunks")
     args = ap.parse_args()
     if args.warmup < 3:

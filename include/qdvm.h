@@ -109,7 +109,15 @@ enum { QDVM_ENGINE_AUTO = 0, QDVM_ENGINE_DIRECT = 1, QDVM_ENGINE_SCAN = 2 };
  *               with D the window's real transform): W_(1,0) with DIRECT
  *               gathers (scan_j = 0 or above the cell's Ntilde), so that
  *               pair gathers only along (0,1); W_(0,1) with the SCAN engine,
- *               which walks the other axis.  Elsewhere 2 acts as 1.
+ *               which walks the other axis.
+ *               3: as 1, and in the on-chip 2D evaluator the pairs with
+ *               J >= scan_j take their windows from the FFT window engine:
+ *               the cell's spectrum fhat stays on chip and each such pair
+ *               takes one inverse transform of fhat (D_J(e.xi) +
+ *               i D_J(e^perp.xi)), which returns W_e + i W_{e^perp}
+ *               (Section 3.2, eq. (decDVM): each direction term as a
+ *               convolution); the other pairs gather directly (scan_j = 0:
+ *               DIRECT for every pair).  Elsewhere 2 and 3 act as 1.
  *   scan_j      with loss_fft >= 1 in the on-chip 2D evaluator (cells of 16,
  *               32, 48 or 64 points per axis with the default truncation):
  *               pairs {e, e^perp} with J >= scan_j compute their windows
@@ -211,17 +219,23 @@ qdvm_status qdvm_eval(qdvm_plan_t plan, const void* f, void* Q, int prec, void* 
  * the workspace (size from qdvm_batched_workspace); results do not depend on
  * the schedule.  Cells whose plan index is out of range are skipped (their
  * outputs are left untouched).  Overlapping calls that share a workspace
- * race.  n_cells == 0 is a no-op. */
+ * race.  n_cells == 0 is a no-op.  Launch parameters: in the on-chip 2D
+ * evaluator every cell runs with its own plan's direct_j, loss_fft and
+ * scan_j, and the block size is plans[0]'s; elsewhere plans[0]'s tuning
+ * applies to the whole batch. */
 qdvm_status qdvm_eval_batched(const qdvm_plan_t* plans, int n_plans, int n_cells, const int* cell_plan,
                               const int64_t* cell_offset, const void* f, void* Q, double* moments,
                               int prec, void* workspace, size_t workspace_bytes, void* stream);
 
 /* Autotuner: time every candidate launch configuration of
  * qdvm_eval_batched on this batch (CUDA events on `stream`, synchronises the
- * host; not for a hot path), keep the fastest in every plan of the batch and
- * return it in *best (may be NULL).  Arguments as for qdvm_eval_batched; Q
- * is overwritten.  Candidates that would need more workspace than given are
- * skipped. */
+ * host; not for a hot path) and keep the fastest in every plan of the batch.
+ * For the on-chip 2D evaluator with several plans, the block size chosen,
+ * each plan in turn then tries the candidates with that block size while
+ * the others keep their best so far, so plans may end with different
+ * direct_j, loss_fft and scan_j.  *best (may be NULL) receives plans[0]'s
+ * tuning.  Arguments as for qdvm_eval_batched; Q is overwritten.
+ * Candidates that would need more workspace than given are skipped. */
 qdvm_status qdvm_tune_batched(const qdvm_plan_t* plans, int n_plans, int n_cells, const int* cell_plan,
                               const int64_t* cell_offset, const void* f, void* Q, int prec, void* workspace,
                               size_t workspace_bytes, void* stream, qdvm_tuning* best);

@@ -214,6 +214,11 @@ extern "C" qdvm_status qdvm_tune_batched(const qdvm_plan_t* plans, int n_plans, 
         for (int th : {256, 512})
             for (int sj : {0, 5, 7, 10, 14})
                 cand.push_back(qdvm_tuning{th, saved.direct_j, saved.line_chunks, 2, sj});
+        // FFT loss and the FFT window engine for the pairs from window
+        // half-length scan_j up, the other windows by DIRECT gathers
+        for (int th : {256, 512})
+            for (int sj : {5, 7, 10, 14})
+                cand.push_back(qdvm_tuning{th, saved.direct_j, saved.line_chunks, 3, sj});
     } else {
         const qdvm_tuning fft{saved.threads, saved.direct_j, 0, 1, saved.scan_j};
         const bool f3 = use_fast3d(QDVM_MODE_FWD, b, fft, prec);
@@ -233,12 +238,11 @@ extern "C" qdvm_status qdvm_tune_batched(const qdvm_plan_t* plans, int n_plans, 
         cudaEventDestroy(e0);
         return qdvm_cuda_status(ce, "cudaEventCreate");
     }
-    float best_ms = 1e30f;
-    qdvm_tuning best_t = saved;
     qdvm_status rs = QDVM_OK;
-    for (const qdvm_tuning& t : cand) {
-        for (int i = 0; i < n_plans; ++i) plans[i]->tune = t;
-        float times[3];
+    // median of three timed runs after a warm-up, with the plans' current
+    // tunings; rs records a failure
+    auto time_batch = [&]() -> float {
+        float times[3] = {0.f, 0.f, 0.f};
         for (int rep = 0; rep < 4 && rs == QDVM_OK; ++rep) {
             cudaEventRecord(e0, st);
             rs = qdvm_eval_batched(plans, n_plans, n_cells, cell_plan, cell_offset, f, Q, nullptr, prec, ws, ws_bytes,
@@ -254,17 +258,45 @@ extern "C" qdvm_status qdvm_tune_batched(const qdvm_plan_t* plans, int n_plans, 
             cudaEventElapsedTime(&ms, e0, e1);
             if (rep > 0) times[rep - 1] = ms;  // first run warms up
         }
-        if (rs != QDVM_OK) break;
         std::sort(times, times + 3);
-        if (times[1] < best_ms) {
-            best_ms = times[1];
+        return times[1];
+    };
+    float best_ms = 1e30f;
+    qdvm_tuning best_t = saved;
+    for (const qdvm_tuning& t : cand) {
+        for (int i = 0; i < n_plans; ++i) plans[i]->tune = t;
+        const float ms = time_batch();
+        if (rs != QDVM_OK) break;
+        if (ms < best_ms) {
+            best_ms = ms;
             best_t = t;
+        }
+    }
+    // per-plan refinement of the 2D launch parameters: each cell runs with
+    // its plan's direct_j, loss_fft and scan_j (the block size is plans[0]'s),
+    // so, the block size fixed, every plan in turn tries the candidates of
+    // that size with the others at their best so far
+    std::vector<qdvm_tuning> per(n_plans, best_t);
+    if (rs == QDVM_OK && n_plans > 1 && all_fused2d(plans, n_plans, d, prec)) {
+        for (int i = 0; i < n_plans; ++i) {
+            for (int k = 0; k < n_plans; ++k) plans[k]->tune = per[k];
+            for (const qdvm_tuning& t : cand) {
+                if (t.threads != best_t.threads) continue;
+                plans[i]->tune = t;
+                const float ms = time_batch();
+                if (rs != QDVM_OK) break;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    per[i] = t;
+                }
+            }
+            if (rs != QDVM_OK) break;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    for (int i = 0; i < n_plans; ++i) plans[i]->tune = rs == QDVM_OK ? best_t : saved;
+    for (int i = 0; i < n_plans; ++i) plans[i]->tune = rs == QDVM_OK ? per[i] : saved;
     if (rs != QDVM_OK) return rs;
-    if (best) *best = best_t;
+    if (best) *best = per[0];
     return QDVM_OK;
 }

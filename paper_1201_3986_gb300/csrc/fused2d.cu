@@ -59,9 +59,11 @@ qdvm_status fused2d_eval_batched(const BatchDev& b, const qdvm_tuning& tu, int n
     int* order = reinterpret_cast<int*>(static_cast<char*>(ws) + 256);
     qdvm_status s = schedule_launch(b, n_cells, cell_plan, order, counter, st);
     if (s != QDVM_OK) return s;
+    // each cell runs with its plan's own launch parameters (PlanDev); the
+    // block size is tu's
     size_t smem = 0;
     for (int i = 0; i < b.n_plans; ++i)
-        smem = std::max(smem, fused2d_smem_bytes(b.p[i].N, b.p[i].Ntilde, prec, tu.loss_fft));
+        smem = std::max(smem, fused2d_smem_bytes(b.p[i].N, b.p[i].Ntilde, prec, b.p[i].tfft));
     switch (prec) {
         case QDVM_F64:
             return fused2d_batched_f64(b, tu, n_cells, cell_plan, cell_offset, order, counter, f, Q, moments, smem,

@@ -560,24 +560,76 @@ __device__ __forceinline__ C* fft_lines(C* a, C* b, const C* tw, const decltype(
     else return fft_passes<C, N, LD, INV, COLS, KH, 1, 4, 4>(a, b, tw, kh, dw);  // N == 16
 }
 
+// The first pass (NS = 1, no twiddles) of a transform that reads a stored
+// spectrum src and multiplies each input by mul(row frequency, column
+// frequency) before the butterflies; dst receives the pass's output.
+template <typename C, int N, int LD, int R, bool INV, bool COLS, typename Mul>
+__device__ __forceinline__ void fft_pass_mul(const C* __restrict__ src, C* __restrict__ dst, Mul mul) {
+    constexpr int NB = N / R;
+    for (int b = threadIdx.x; b < N * NB; b += blockDim.x) {
+        const int line = b % N, j = b / N;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int e = j + r * NB;
+            v[r] = cmul(src[COLS ? e * LD + line : line * LD + e], COLS ? mul(e, line) : mul(line, e));
+        }
+        dft_small<R, INV>(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int e = j * R + r;
+            dst[COLS ? e * LD + line : line * LD + e] = v[r];
+        }
+    }
+}
+
+template <typename C, int N, int LD, int R, int... Rs, typename Mul>
+__device__ __forceinline__ C* icols_from(const C* F, C* A, C* B, const C* tw, Mul mul) {
+    fft_pass_mul<C, N, LD, R, true, true>(F, A, mul);
+    __syncthreads();
+    if constexpr (sizeof...(Rs) > 0)
+        return fft_passes<C, N, LD, true, true, 0, R, Rs...>(A, B, tw, nullptr, nullptr);
+    else
+        return A;
+}
+
+// The inverse 2D transform of mul(xi) * F (F a stored spectrum, left
+// unchanged) through the buffers A and B: the first column pass reads F
+// and writes A, the other passes ping-pong.  With an even number of passes
+// in all, the result is always in B.
+template <typename C, int N, int LD, typename Mul>
+__device__ __forceinline__ C* ifft2_from(const C* F, C* A, C* B, const C* tw, Mul mul) {
+    C* r;
+    if constexpr (N == 64) r = icols_from<C, N, LD, 8, 8>(F, A, B, tw, mul);
+    else if constexpr (N == 48) r = icols_from<C, N, LD, 3, 4, 4>(F, A, B, tw, mul);
+    else if constexpr (N == 32) r = icols_from<C, N, LD, 4, 8>(F, A, B, tw, mul);
+    else r = icols_from<C, N, LD, 4, 4>(F, A, B, tw, mul);  // N == 16
+    return fft_lines<C, N, LD, true, false>(r, r == A ? B : A, tw);
+}
+
 // The points a thread owns in the FFT body.  By default rows y0 + k R of
 // column x (R = NT / N rows per step, the last point predicated off where R
 // does not divide N).  For 48^2 cells on 256 threads, where that would leave
 // 16 threads idle and some warps one point short, each thread owns a 3 x 3
 // tile of points 16 apart instead: (y0 + 16 a, x + 16 b), y0, x < 16,
 // 256 x 9 = 48^2.  A warp then covers two rows of 16 consecutive points,
-// which with a row stride of 16 (mod 32) words hit distinct banks.
-template <int N, int NT>
+// which with a row stride of 16 (mod 32) words hit distinct banks.  With VEC
+// (FP32 cells of 32^2 and 64^2) a thread owns pairs of neighbouring points
+// (y0 + m R, x + c), x even, c = 0, 1 (point k = 2 m + c), so that every
+// gather reads the two values of a pair with one 8-byte load; a warp's 32
+// pairs are 64 consecutive points of a row, or two rows of 32.
+template <int N, int NT, bool VEC = false>
 struct PointMap {
-    static constexpr bool TILE = N == 48 && NT == 256;
-    static constexpr int R = TILE ? 16 : ((NT / N < N) ? NT / N : N);
-    static constexpr int PPT = TILE ? 9 : (N + R - 1) / R;
-    static constexpr int ACT = TILE ? NT : R * N;  // threads that own points
+    static constexpr bool TILE = !VEC && N == 48 && NT == 256;
+    static constexpr int XW = VEC ? N / 2 : N;  // threads per row
+    static constexpr int R = TILE ? 16 : ((NT / XW < N) ? NT / XW : N);
+    static constexpr int PPT = TILE ? 9 : (VEC ? 2 : 1) * ((N + R - 1) / R);
+    static constexpr int ACT = TILE ? NT : R * XW;  // threads that own points
     static constexpr bool PARTIAL = !TILE && (N % R) != 0;
-    __host__ __device__ static constexpr int dy(int k) { return TILE ? (k / 3) * 16 : k * R; }
-    __host__ __device__ static constexpr int dx(int k) { return TILE ? (k % 3) * 16 : 0; }
-    __device__ static int x0(int tid) { return TILE ? tid % 16 : tid % N; }
-    __device__ static int y0(int tid) { return TILE ? tid / 16 : tid / N; }
+    __host__ __device__ static constexpr int dy(int k) { return TILE ? (k / 3) * 16 : (VEC ? (k / 2) * R : k * R); }
+    __host__ __device__ static constexpr int dx(int k) { return TILE ? (k % 3) * 16 : (VEC ? k % 2 : 0); }
+    __device__ static int x0(int tid) { return TILE ? tid % 16 : (VEC ? 2 * (tid % XW) : tid % N); }
+    __device__ static int y0(int tid) { return TILE ? tid / 16 : tid / XW; }
 };
 
 // Layouts of the FFT body.  Without the SCAN engine: the cell with a
@@ -656,14 +708,24 @@ __device__ __forceinline__ void strip_walk(const T* __restrict__ sF, T* __restri
 // SCAN: pairs with J >= scan_j take the SCAN engine (the caller instantiates
 // SCAN = true only when some pair of the cell does); the others, and every
 // pair when !SCAN, gather their windows directly.
+// FWIN (without SCAN): the FFT window engine.  The spectrum fhat of the cell
+// stays in the cell's place while every pair with J >= scan_j takes one
+// inverse transform of fhat (D_J(e.xi) + i D_J(e^perp.xi)), which returns
+// W_e + i W_{e^perp} (both real: f is real and the window transforms even),
+// and the loss takes one of fhat Ktilde; the cell is copied afterwards for
+// the direct gathers of the remaining pairs.
 template <typename T, bool KAHAN, int N, int H, int NT, bool SCAN>
 __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, const int pe, const T* __restrict__ fcell,
                                              T* __restrict__ qcell, double* __restrict__ mom, unsigned char* smem,
-                                             double* red, const bool do_loss, const int scan_j, const bool wfft) {
+                                             double* red, const bool do_loss, const int scan_j, const bool wfft,
+                                             const bool fwin = false) {
     using C = typename Cplx<T>::type;
     using G = GeoF<N, H, SCAN>;
     constexpr int W = G::W, RS = G::RS, HW = G::HW, LD = G::LD;
-    using PM = PointMap<N, NT>;
+    // FP32 cells of 32^2 and 64^2 without SCAN: pairs of neighbouring points
+    // per thread, gathered with 8-byte loads (PointMap)
+    constexpr bool VEC = !SCAN && sizeof(T) == 4 && (N == 32 || N == 64);
+    using PM = PointMap<N, NT, VEC>;
     constexpr int PPT = PM::PPT;
     const int tid = threadIdx.x;
     T* sF = reinterpret_cast<T*>(smem);
@@ -671,6 +733,13 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
     T* sRp = sRe + N * N;
     C* A = reinterpret_cast<C*>(SCAN ? smem : smem + cell_bytes<T, N, H, SCAN>());
     C* B = A + N * LD;
+    // with VEC: the cell shifted by one word, sS[i] = sF[i + 1], built in the
+    // FFT buffers once the loss transform is done, so that a pair of points
+    // whose gather address is odd loads its two values with one aligned
+    // 8-byte load from sS
+    T* sS = reinterpret_cast<T*>(A);
+    static_assert(!VEC || W * RS <= 4 * N * LD, "the shifted cell fits in the FFT buffers");
+    static_assert(!VEC || (RS % 2 == 0 && (PM::R * RS) % 2 == 0), "even strides keep pairs aligned");
     const C* tw;
     const T* kh;
     if constexpr (sizeof(T) == 8) {
@@ -687,6 +756,24 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
     const bool last_ok = !PM::PARTIAL || (y0 + PM::dy(PPT - 1) < N);
     T acc[PPT], cmp[PPT];
 
+    // VEC: add the values at +-off from every owned pair to arr.  The
+    // address a0 + off has the parity of HW + off (x and the strides are
+    // even): even, an aligned 8-byte load from the cell; odd, from sS.
+    auto vgather = [&](T (&arr)[PPT], const int off) {
+        if constexpr (VEC) {
+            const bool al = ((HW + off) & 1) == 0;
+            const T* bp = al ? sF + a0 + off : sS + a0 + off - 1;
+            const T* bm = al ? sF + a0 - off : sS + a0 - off - 1;
+#pragma unroll
+            for (int m = 0; m < PPT / 2; ++m) {
+                const C u = *reinterpret_cast<const C*>(bp + m * PM::R * RS);
+                const C v = *reinterpret_cast<const C*>(bm + m * PM::R * RS);
+                arr[2 * m] += u.x + v.x;
+                arr[2 * m + 1] += u.y + v.y;
+            }
+        }
+    };
+
     // the direct gathers of the gain's two windows, 2 c_e W_e W_{e^perp}
     auto gain_direct = [&](const int4 e, const T c2) {
         const int se = e.x * RS + e.y;
@@ -694,16 +781,23 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
         T w[PPT], pp[PPT];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) w[k] = pp[k] = T(0);
-        const T* b;
-        for (int j = 1; j <= e.z; ++j) {
+        if constexpr (VEC) {
+            for (int j = 1; j <= e.z; ++j) {
+                vgather(w, j * se);
+                vgather(pp, j * sp);
+            }
+        } else {
+            const T* b;
+            for (int j = 1; j <= e.z; ++j) {
 #define QDVM_GATHER(arr, off)                                                                \
     b = sF + a0 + (off);                                                                     \
     _Pragma("unroll") for (int k = 0; k < PPT; ++k) if (k < PPT - 1 || last_ok) arr[k] += b[PM::dy(k) * RS + PM::dx(k)];
-            QDVM_GATHER(w, j * se)
-            QDVM_GATHER(w, -j * se)
-            QDVM_GATHER(pp, j * sp)
-            QDVM_GATHER(pp, -j * sp)
+                QDVM_GATHER(w, j * se)
+                QDVM_GATHER(w, -j * se)
+                QDVM_GATHER(pp, j * sp)
+                QDVM_GATHER(pp, -j * sp)
 #undef QDVM_GATHER
+            }
         }
 #pragma unroll
         for (int k = 0; k < PPT; ++k)
@@ -774,6 +868,71 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
     };
 
     if constexpr (!SCAN) {
+        if (fwin) {
+            // fhat: f into A, forward transform (an even number of passes:
+            // the result is in A), then into the cell's place F
+            const T* djt;
+            if constexpr (sizeof(T) == 8) djt = P.dj;
+            else djt = P.dj_f;
+            C* F = reinterpret_cast<C*>(smem);
+            static_assert((size_t)N * LD * sizeof(C) <= cell_bytes<T, N, H, false>(), "fhat fits in the cell's place");
+            for (int i = tid; i < N * N; i += NT) A[(i / N) * LD + (i % N)] = C{fcell[i], T(0)};
+            __syncthreads();
+            C* r = fft_lines<C, N, LD, false, false>(A, B, tw);
+            r = fft_lines<C, N, LD, false, true>(r, r == A ? B : A, tw);
+            for (int i = tid; i < N * LD; i += NT) F[i] = r[i];
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                acc[k] = T(0);
+                cmp[k] = T(0);
+            }
+            for (int pr = pb; pr < pe; ++pr) {
+                const int4 e = P.pairs[pr];
+                if (e.z < scan_j) continue;
+                const T c2 = pair_weight<T>(P.pair_c, P.pair_c2f, pr);
+                const T* dje = djt + e.z * N;
+                // e and e^perp = (-e1, e0) reduced to [0, N): every product below is non-negative
+                const int e0 = (e.x % N + N) % N, e1 = (e.y % N + N) % N, n1 = (N - e1) % N;
+                const C* q = ifft2_from<C, N, LD>(F, A, B, tw, [&](const int ky, const int kx) {
+                    return C{dje[(e0 * ky + e1 * kx) % N], dje[(n1 * ky + e0 * kx) % N]};
+                });
+                if (active) {
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) {
+                        if (k < PPT - 1 || last_ok) {
+                            const C w = q[(y0 + PM::dy(k)) * LD + x + PM::dx(k)];
+                            comp_add<T, KAHAN>(acc[k], cmp[k], c2 * w.x * w.y);
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+            // the loss, then the cell in F's place for the other pairs
+            const C* q = nullptr;
+            if (do_loss)
+                q = ifft2_from<C, N, LD>(F, A, B, tw,
+                                         [&](const int ky, const int kx) { return C{kh[ky * N + kx], T(0)}; });
+            fill_cell(false);
+            __syncthreads();
+            if (do_loss && active) {
+#pragma unroll
+                for (int k = 0; k < PPT; ++k)
+                    if (k < PPT - 1 || last_ok)
+                        comp_add<T, KAHAN>(acc[k], cmp[k],
+                                           -sF[a0 + PM::dy(k) * RS + PM::dx(k)] * q[(y0 + PM::dy(k)) * LD + x + PM::dx(k)].x);
+            }
+            if constexpr (VEC) {
+                __syncthreads();  // the loss result is read: the FFT buffers take the shifted cell
+                for (int i = tid; i < W * RS - 1; i += NT) sS[i] = sF[i + 1];
+                __syncthreads();
+            }
+            if (active)
+                for (int pr = pb; pr < pe; ++pr) {
+                    const int4 e = P.pairs[pr];
+                    if (e.z < scan_j) gain_direct(e, pair_weight<T>(P.pair_c, P.pair_c2f, pr));
+                }
+        } else {
         fill_cell(do_loss);
         __syncthreads();
 #pragma unroll
@@ -795,10 +954,32 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
         }
         const C* rw = nullptr;
         if (do_loss) rw = loss_fft([&](int k) { return sF[a0 + PM::dy(k) * RS + PM::dx(k)]; }, dw);
-        if (active) {
+        if constexpr (VEC) {
+            // s W_(1,0) leaves the FFT buffers before they take the shifted cell
+            T wx[PPT];
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) wx[k] = (wax && active) ? rw[(y0 + PM::dy(k)) * LD + x + PM::dx(k)].y : T(0);
+            __syncthreads();
+            for (int i = tid; i < W * RS - 1; i += NT) sS[i] = sF[i + 1];
+            __syncthreads();
+            if (active) {
+                int pr = pb;
+                if (wax) {
+                    const T c2 = pair_weight<T>(P.pair_c, P.pair_c2f, pr++) * dw[N];  // dw[N] = 1 / s
+                    T pp[PPT];
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) pp[k] = T(0);
+                    for (int j = 1; j <= H; ++j) vgather(pp, j);  // W_(0,1), along the row
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) comp_add<T, KAHAN>(acc[k], cmp[k], c2 * wx[k] * pp[k]);
+                }
+                for (; pr < pe; ++pr) gain_direct(P.pairs[pr], pair_weight<T>(P.pair_c, P.pair_c2f, pr));
+            }
+        } else if (active) {
             int pr = pb;
             if (wax) gain_axis(rw, pair_weight<T>(P.pair_c, P.pair_c2f, pr++) * dw[N]);  // dw[N] = 1 / s
             for (; pr < pe; ++pr) gain_direct(P.pairs[pr], pair_weight<T>(P.pair_c, P.pair_c2f, pr));
+        }
         }
     } else {
         // the FFT buffers occupy the cell's place: the loss reads f at the
@@ -937,7 +1118,10 @@ __device__ __forceinline__ void run_cell(const PlanDev& P, int pb, int pe, const
     if (P.N == NN && P.Ntilde == HH) {                                                                            \
         if (fft && P.khat) {                                                                                      \
             unsigned char* sm = reinterpret_cast<unsigned char*>(sF);                                             \
-            if (sj > 0 && sj <= HH)                                                                               \
+            if (fft == 3)                                                                                         \
+                fftloss_body<T, KAHAN, NN, HH, NT, false>(P, pb, pe, f, q, mom, sm, red, do_loss, sj > 0 ? sj : 65, \
+                                                          false, true);                                           \
+            else if (sj > 0 && sj <= HH)                                                                          \
                 fftloss_body<T, KAHAN, NN, HH, NT, true>(P, pb, pe, f, q, mom, sm, red, do_loss, sj, fft == 2);   \
             else                                                                                                  \
                 fftloss_body<T, KAHAN, NN, HH, NT, false>(P, pb, pe, f, q, mom, sm, red, do_loss, 0, fft == 2);   \
@@ -1001,7 +1185,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused2d_batched(BatchDev B, int n_cel
                                                            const int64_t* __restrict__ cell_offset,
                                                            const int* __restrict__ order, int* counter,
                                                            const T* __restrict__ f, T* __restrict__ Q,
-                                                           double* __restrict__ moments, int jd, int fft, int sj) {
+                                                           double* __restrict__ moments) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32 * 4];
     __shared__ int s_cell;
@@ -1024,8 +1208,9 @@ __global__ void __launch_bounds__(NT, 2) k_fused2d_batched(BatchDev B, int n_cel
         const int64_t off = cell_offset[cell];
         T* sF = reinterpret_cast<T*>(smem_raw);
         T* sP = sF + buf_f_elems(P.N, P.Ntilde);
+        // the cell's plan's own direct_j, loss_fft and scan_j
         run_cell<T, KAHAN, NT>(P, 0, P.n_pairs, f + off, Q + off, moments ? moments + (size_t)cell * 4 : nullptr, sF,
-                               sP, red, jd, fft, sj, true);
+                               sP, red, P.tjd, P.tfft, P.tsj, true);
         __syncthreads();
     }
 }
@@ -1067,15 +1252,15 @@ inline void split_pairs(int n_pairs, int max_ctas, int* S, int* ppc) {
 
 template <typename T, bool KAHAN, int NT>
 qdvm_status launch_batched_t(const BatchDev& b, int n_cells, const int* cell_plan, const int64_t* cell_offset,
-                             const int* order, int* counter, const T* f, T* Q, double* moments, size_t smem, int jd,
-                             int fft, int sj, cudaStream_t st) {
+                             const int* order, int* counter, const T* f, T* Q, double* moments, size_t smem,
+                             cudaStream_t st) {
     auto k = k_fused2d_batched<T, KAHAN, NT>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem);
     per_sm = std::max(per_sm, 1);
     const int grid = std::max(1, std::min(n_cells, per_sm * qdvm_num_sms()));
-    k<<<grid, NT, smem, st>>>(b, n_cells, cell_plan, cell_offset, order, counter, f, Q, moments, jd, fft, sj);
+    k<<<grid, NT, smem, st>>>(b, n_cells, cell_plan, cell_offset, order, counter, f, Q, moments);
     QDVM_LAUNCH_CHECK("fused2d batched launch");
     return QDVM_OK;
 }
@@ -1088,9 +1273,9 @@ qdvm_status dispatch_batched(const BatchDev& b, const qdvm_tuning& tu, int n_cel
     T* qo = static_cast<T*>(Q);
     if (tu.threads == 512)
         return launch_batched_t<T, KAHAN, 512>(b, n_cells, cell_plan, cell_offset, order, counter, fi, qo, moments,
-                                               smem, tu.direct_j, tu.loss_fft, tu.scan_j, st);
+                                               smem, st);
     return launch_batched_t<T, KAHAN, 256>(b, n_cells, cell_plan, cell_offset, order, counter, fi, qo, moments, smem,
-                                           tu.direct_j, tu.loss_fft, tu.scan_j, st);
+                                           st);
 }
 
 

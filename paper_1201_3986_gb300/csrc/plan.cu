@@ -424,6 +424,23 @@ __global__ void k_dwin(int N, int J, const double* kh, double* dw, float* dwf) {
     dwf[t] = (float)v;
 }
 
+// Transforms of the line windows for the FFT window engine of the 2D
+// evaluator: dj[J N + t] = sum_{0<|j|<=J} cos(2 pi j t / N) / N^2 for
+// J = 0..H, t < N (row 0 zero), phases reduced exactly modulo N.  With
+// m = e.xi mod N, fhat(xi) dj[J N + m] is the transform of W_e (the window
+// of half-length J along e) including the inverse transform's 1 / N^2.
+// One thread per (J, t).
+__global__ void k_djtab(int N, int H, double* dj, float* djf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (H + 1) * N) return;
+    const int J = i / N, t = i - J * N;
+    double acc = 0.0;
+    for (int j = 1; j <= J; ++j) acc += 2.0 * cospi(2.0 * ((j * t) % N) / N);
+    const double v = acc / ((double)N * (double)N);
+    dj[i] = v;
+    djf[i] = (float)v;
+}
+
 // Ktilde(xi) = sum_e c_e D_e(xi) Lambda_e(xi) / N^d with
 // D_e = 2 sum_{j=1..J_e} cos(2 pi j (e.xi) / N) (the line factor) and
 // Lambda_e = sum_{l in plane list} cos(2 pi (l.xi) / N) (the e^perp factor):
@@ -484,6 +501,8 @@ static void plan_free(qdvm_plan_s* p) {
     cudaFree(p->d_tw_f);
     cudaFree(p->d_dwin);
     cudaFree(p->d_dwin_f);
+    cudaFree(p->d_dj);
+    cudaFree(p->d_dj_f);
     cudaFree(p->d_rclass);
     cudaFree(p->d_rline);
     cudaFree(p->d_rc);
@@ -606,7 +625,9 @@ static qdvm_status build_tables(qdvm_plan_s* p) {
             (e = cudaMalloc(&p->d_tw, N * sizeof(double2))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_tw_f, N * sizeof(float2))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_dwin, (N + 1) * sizeof(double))) != cudaSuccess ||
-            (e = cudaMalloc(&p->d_dwin_f, (N + 1) * sizeof(float))) != cudaSuccess) {
+            (e = cudaMalloc(&p->d_dwin_f, (N + 1) * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_dj, (p->Ntilde + 1) * N * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_dj_f, (p->Ntilde + 1) * N * sizeof(float))) != cudaSuccess) {
             cudaFree(dK);
             return fail(qdvm_cuda_status(e, "loss kernel tables"));
         }
@@ -614,6 +635,7 @@ static qdvm_status build_tables(qdvm_plan_s* p) {
         k_khat2d<<<(n2 + 127) / 128, 128>>>(N, dK, p->d_khat, p->d_khat_f);
         k_twiddles<<<(N + 63) / 64, 64>>>(N, p->d_tw, p->d_tw_f);
         k_dwin<<<(N + 64) / 64, 64>>>(N, p->Ntilde, p->d_khat, p->d_dwin, p->d_dwin_f);
+        k_djtab<<<((p->Ntilde + 1) * N + 127) / 128, 128>>>(N, p->Ntilde, p->d_dj, p->d_dj_f);
         e = cudaDeviceSynchronize();
         cudaFree(dK);
         if (e != cudaSuccess) return fail(qdvm_cuda_status(e, "loss kernel tables"));
@@ -724,7 +746,7 @@ extern "C" qdvm_status qdvm_plan_set_tuning(qdvm_plan_t p, const qdvm_tuning* t)
     if (t->threads != 256 && t->threads != 512) return qdvm_fail(QDVM_ERR_INVALID_ARG, "threads must be 256 or 512");
     if (t->direct_j < 0 || t->direct_j > 2) return qdvm_fail(QDVM_ERR_INVALID_ARG, "direct_j must be 0, 1 or 2");
     if (t->line_chunks < 0) return qdvm_fail(QDVM_ERR_INVALID_ARG, "line_chunks must be >= 0");
-    if (t->loss_fft < 0 || t->loss_fft > 2) return qdvm_fail(QDVM_ERR_INVALID_ARG, "loss_fft must be 0, 1 or 2");
+    if (t->loss_fft < 0 || t->loss_fft > 3) return qdvm_fail(QDVM_ERR_INVALID_ARG, "loss_fft must be 0, 1, 2 or 3");
     if (t->scan_j < 0 || t->scan_j > 64) return qdvm_fail(QDVM_ERR_INVALID_ARG, "scan_j must be in [0, 64]");
     p->tune = *t;
     return QDVM_OK;

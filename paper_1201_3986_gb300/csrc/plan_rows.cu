@@ -12,8 +12,9 @@
 // run along alpha and a thread that owns 8 consecutive alpha points reads a
 // row of length n once (n + 7 loads) instead of 8 n times.
 //
-// u is chosen per line among short vectors to minimise the loads, allowing
-// 15% over the best choice so that few classes cover all lines (greedy).
+// u is chosen per line among short vectors to minimise the loads of its
+// rows other than the central one (see below), allowing 15% over the best
+// choice so that few classes cover all lines (greedy).
 //
 // The row b = 0 of every line of a class is the same set {a u : 0 < |a| <= A},
 // A = floor(Ntilde / |u|_inf): the line window of u itself.  When A >= 1 each
@@ -121,7 +122,8 @@ bool rows_for(const V3& e, const V3& u, const std::vector<V3>& pts, Option* o) {
             size_t j = i;
             while (j + 1 < aa.size() && aa[j + 1] == aa[j] + 1) ++j;
             o->segs.push_back(Seg{kv.first, aa[i], aa[j]});
-            o->cost += (aa[j] - aa[i] + 1) + 7 + 10;
+            // the central row b = 0 is summed once per class, not per line
+            if (kv.first != 0) o->cost += (aa[j] - aa[i] + 1) + 7 + 10;
             i = j + 1;
         }
     }

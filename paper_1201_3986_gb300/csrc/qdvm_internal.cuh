@@ -49,6 +49,11 @@ struct qdvm_plan_s {
     // s is a power of two of the size of Ktilde(0) / D(0), entry N is 1 / s
     double* d_dwin;
     float* d_dwin_f;
+    // 2D with N <= 64: the window transforms of every half-length J <= Ntilde,
+    // dj[J N + t] = sum_{0<|j|<=J} cos(2 pi j t / N) / N^2 (the FFT window
+    // engine multiplies fhat by dj[J N + (e.xi mod N)] + i dj[J N + (e^perp.xi mod N)])
+    double* d_dj;
+    float* d_dj_f;
     // 3D, N in {16, 32}, Ntilde <= 7: the plane polygons as rows along an
     // in-plane lattice vector u, lines grouped into classes of a common u
     // (plan_rows.cu).  Lines are listed class by class.
@@ -84,6 +89,8 @@ struct PlanDev {
     const float2* tw_f;
     const double* dwin;
     const float* dwin_f;
+    const double* dj;
+    const float* dj_f;
     int n_rclass;
     const int* rclass;
     const int4* rline;
@@ -91,6 +98,9 @@ struct PlanDev {
     const float* rc_f;
     const int* rrow_start;
     const uchar4* rrow;
+    // the plan's own launch parameters (direct_j, loss_fft, scan_j): a
+    // batched 2D launch takes them per cell from the cell's plan
+    int tjd, tfft, tsj;
 };
 
 struct BatchDev {
@@ -121,6 +131,8 @@ inline PlanDev plan_dev(const qdvm_plan_s* p) {
     v.tw_f = p->d_tw_f;
     v.dwin = p->d_dwin;
     v.dwin_f = p->d_dwin_f;
+    v.dj = p->d_dj;
+    v.dj_f = p->d_dj_f;
     v.n_rclass = p->n_rclass;
     v.rclass = p->d_rclass;
     v.rline = p->d_rline;
@@ -128,6 +140,9 @@ inline PlanDev plan_dev(const qdvm_plan_s* p) {
     v.rc_f = p->d_rc_f;
     v.rrow_start = p->d_rrow_start;
     v.rrow = p->d_rrow;
+    v.tjd = p->tune.direct_j;
+    v.tfft = p->tune.loss_fft;
+    v.tsj = p->tune.scan_j;
     return v;
 }
 

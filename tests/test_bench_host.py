@@ -19,8 +19,10 @@ def test_profile_summary_is_well_formed():
     assert len(vals["source_sha256"]) == 64
     assert int(vals["dram_bytes_per_launch"]) > 0
     assert int(vals["smem_wavefronts_per_launch"]) > 0
-    tu = tuple(int(v) for v in vals["launch_tuning"].split(","))
-    assert len(tu) == 4 and tu[0] in (256, 512) and tu[2] in (0, 1, 2)
+    for ent in vals["launch_tuning"].split():
+        n, v = ent.split("=")
+        tu = tuple(int(x) for x in v.split(","))
+        assert int(n) in bench.NS and len(tu) == 4 and tu[0] in (256, 512) and tu[2] in (0, 1, 2, 3)
 
 
 def test_fields_dropped_when_sources_change(monkeypatch):
@@ -28,16 +30,16 @@ def test_fields_dropped_when_sources_change(monkeypatch):
     assert bench.profiled_fields() == {}
     assert bench.profiled_value("dram_bytes_per_launch") is None
     assert bench.profiled_tuning() is None
-    assert bench.profiled_traffic({"threads": 256, "loss_fft": 2, "scan_j": 0}) is None
-    assert bench.smem_roofline(0.6, {"sm_mhz": 2070.0}, {"threads": 256, "loss_fft": 2, "scan_j": 0}) is None
+    key = bench.tuning_key({n: {"threads": 256, "direct_j": 2, "loss_fft": 2, "scan_j": 0} for n in bench.NS})
+    assert bench.profiled_traffic(key) is None
+    assert bench.smem_roofline(0.6, {"sm_mhz": 2070.0}, key) is None
 
 
 def test_roofline_fields_follow_the_profiled_launch(monkeypatch):
     sha = open(bench.PROFILE).read().split("source_sha256:")[1].split("`")[0].strip()
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: sha)
-    th, dj, fft, sj = bench.profiled_tuning()
-    same = {"threads": th, "direct_j": dj, "loss_fft": fft, "scan_j": sj}
-    other = dict(same, loss_fft=(fft + 1) % 3)
+    same = bench.profiled_tuning()
+    other = same.replace("=256,", "=512,") if "=256," in same else same.replace("=512,", "=256,")
     wf = bench.profiled_value("smem_wavefronts_per_launch")
     assert bench.profiled_traffic(same) == bench.profiled_value("dram_bytes_per_launch")
     assert bench.profiled_traffic(other) is None

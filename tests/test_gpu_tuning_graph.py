@@ -108,7 +108,7 @@ def test_tuning_rejects_bad_values(q):
     with pytest.raises(q.QdvmError):
         p.set_tuning(direct_j=3)
     with pytest.raises(q.QdvmError):
-        p.set_tuning(loss_fft=3)
+        p.set_tuning(loss_fft=4)
     with pytest.raises(q.QdvmError):
         p.set_tuning(scan_j=-1)
     assert p.tuning() == {"threads": 256, "direct_j": 2, "line_chunks": 0, "loss_fft": 0,
@@ -121,9 +121,12 @@ def test_autotuner_2d_then_parity(q, torch):
     plans = [q.Plan(2, n, 8, 8.0) for n in Ns]
     cp, co, f = _batch(torch, b, Ns, "f32_kahan")
     best = q.qdvm_tune_batched(plans, cp, co, f, "f32_kahan")
-    assert best["threads"] in (256, 512) and best["direct_j"] in (0, 1, 2) and best["loss_fft"] in (0, 1, 2)
+    assert best["threads"] in (256, 512) and best["direct_j"] in (0, 1, 2) and best["loss_fft"] in (0, 1, 2, 3)
     assert 0 <= best["scan_j"] <= 64
-    assert all(p.tuning() == best for p in plans)
+    assert plans[0].tuning() == best
+    for p in plans:  # per-plan launch parameters, one block size
+        t = p.tuning()
+        assert t["threads"] == best["threads"] and t["loss_fft"] in (0, 1, 2, 3) and 0 <= t["scan_j"] <= 64
     Q, _ = q.qdvm_eval_batched(plans, cp, co, f, "f32_kahan")
     Qn = Q.cpu().numpy().astype(np.float64)
     fin = f.cpu().numpy().astype(np.float64)
@@ -182,3 +185,31 @@ def test_graph_replay_matches_direct_call(q, torch, d):
         g.launch()
         torch.cuda.synchronize()
         assert torch.equal(Q, Qd) and torch.equal(M, Md)
+
+
+def test_per_plan_launch_parameters_in_one_batch(q, torch):
+    """Each cell of a batched 2D call runs with its own plan's loss_fft and
+    scan_j: a batch whose plans carry four different engines (direct loss,
+    FFT loss + axis window, SCAN, FFT windows) against the oracle, and each
+    cell equal bit for bit to the same cell evaluated in a batch of its own
+    plan alone."""
+    Ns = (16, 32, 48, 64)
+    b = synth.batch_2d(16, Ns=Ns, L=8.0, seed=44)
+    plans = [q.Plan(2, n, 8, 8.0) for n in Ns]
+    settings = [dict(loss_fft=0, scan_j=0), dict(loss_fft=2, scan_j=0), dict(loss_fft=1, scan_j=3),
+                dict(loss_fft=3, scan_j=7)]
+    for p, st in zip(plans, settings):
+        p.set_tuning(**st)
+    cp, co, f = _batch(torch, b, Ns, "f32_kahan")
+    Q, _ = q.qdvm_eval_batched(plans, cp, co, f, "f32_kahan")
+    Qn = Q.cpu().numpy()
+    fin = f.cpu().numpy().astype(np.float64)
+    for c in range(b.n_cells):
+        r = oracle.q(b.cell(c, fin), 8.0, 8)
+        assert oracle.rel_linf(b.cell(c, Qn).astype(np.float64), r["Q"], r["scale"]) <= 1e-5
+        i = Ns.index(int(b.Ns[c]))
+        one = torch.zeros(1, dtype=torch.int32, device="cuda")
+        off = torch.zeros(1, dtype=torch.int64, device="cuda")
+        fc = torch.tensor(b.cell(c, fin).ravel(), dtype=torch.float32, device="cuda")
+        Qc, _ = q.qdvm_eval_batched([plans[i]], one, off, fc, "f32_kahan")
+        assert np.array_equal(Qc.cpu().numpy(), b.cell(c, Qn).ravel())
