@@ -348,39 +348,6 @@ __device__ __forceinline__ const T* row_dispatch(int len, const T* b, T& P0, T (
     }
 }
 
-// A run of LEN values from b added in the (first window, increments) form of
-// row_run: LEN + 7 loads.
-template <int LEN, typename T>
-__device__ __forceinline__ void run_acc(const T* __restrict__ b, T& P0, T (&D)[7]) {
-    T v[LEN + 7];
-#pragma unroll
-    for (int t = 0; t < LEN + 7; ++t) v[t] = b[t];
-    P0 += tree_sum<0, LEN>(v);
-#pragma unroll
-    for (int k = 1; k < 8; ++k) D[k - 1] += v[LEN - 1 + k] - v[k - 1];
-}
-
-// The central row of a class, {a u : 0 < |a| <= A} (the b = 0 row of every
-// line's polygon, u the class's alpha axis), for the unit (a0, be, ga): the
-// segments [-A, -1] and [1, A] along alpha, in the form of row_run.
-template <int N, typename T>
-__device__ __forceinline__ void central_rows(const int A, const T* g, const int be, const int ga, const int a0,
-                                             T& P0, T (&D)[7]) {
-    constexpr int M = N - 1, SA = rows_sa<N>();
-    const T* b = g + (be * N + ga) * SA;
-    const T* lo = b + ((a0 - A) & M);
-    const T* hi = b + ((a0 + 1) & M);
-    switch (A) {
-        case 1: run_acc<1>(lo, P0, D); run_acc<1>(hi, P0, D); break;
-        case 2: run_acc<2>(lo, P0, D); run_acc<2>(hi, P0, D); break;
-        case 3: run_acc<3>(lo, P0, D); run_acc<3>(hi, P0, D); break;
-        case 4: run_acc<4>(lo, P0, D); run_acc<4>(hi, P0, D); break;
-        case 5: run_acc<5>(lo, P0, D); run_acc<5>(hi, P0, D); break;
-        case 6: run_acc<6>(lo, P0, D); run_acc<6>(hi, P0, D); break;
-        default: run_acc<7>(lo, P0, D); run_acc<7>(hi, P0, D); break;
-    }
-}
-
 // Plane sums of one line, rows [rs, re), for the unit (a0, be, ga):
 // P0 and D as in row_run.  Row descriptors are fetched two rows ahead and
 // row starts one row ahead.
@@ -399,41 +366,102 @@ __device__ __forceinline__ void plane_rows(const uchar4* __restrict__ rows, int 
     }
 }
 
-// Sums over the lines [ls, lend) of one class for the thread's units of 8
-// consecutive alpha points and adds them at the points' cell indices
-// p = M q (mod N).  Plane sums come from the rows of g; line windows from g
-// (WG false) or from the global copy gw (WG true).  With A > 0 the first nc
-// rows of every line are the class's central row {a u : 0 < |a| <= A}, summed
-// once per unit (central_rows) and taken as the start of each line's plane
-// sums.
+// Prefix form of the class-coordinate cell (forward and JVP): for every
+// (beta, gamma) line, S[(beta N + gamma) SP + a] = sum_{t < a} g_t with g_t
+// the cell value at alpha = t mod N, a <= SP - 1.  A run of LEN points
+// starting at alpha = s sums to S[s + LEN] - S[s], whatever LEN, so the 8
+// windows of a unit (a0 .. a0 + 7) of one row cost 16 loads and no dispatch
+// on the length.  SP is odd (a warp's lanes, consecutive gamma, hit distinct
+// banks) and covers s <= N - 1, LEN <= QDVM_ROW_MAX, plus the 7 further
+// points of a unit.
+template <int N>
+__host__ __device__ constexpr int rows_sp() {
+    return (N + QDVM_ROW_MAX + 8) | 1;
+}
+
+// The cell src in prefix form: the class-coordinate values at a + 1 for
+// every a < SP - 1 with a = alpha (mod N), then one thread per (beta, gamma)
+// line accumulates them in place (S[0] = 0).  Ends with a barrier.
+template <typename T, int N>
+__device__ __forceinline__ void relayout_prefix(const int (&Mi)[9], const T* __restrict__ src, T* __restrict__ S) {
+    constexpr int N2 = N * N, N3 = N2 * N, M = N - 1, SP = rows_sp<N>();
+    for (int p = threadIdx.x; p < N3; p += blockDim.x) {
+        const int p0 = p / N2, p1 = (p / N) & M, p2 = p & M;
+        const int al = (Mi[0] * p0 + Mi[1] * p1 + Mi[2] * p2) & M;
+        const int be = (Mi[3] * p0 + Mi[4] * p1 + Mi[5] * p2) & M;
+        const int ga = (Mi[6] * p0 + Mi[7] * p1 + Mi[8] * p2) & M;
+        const T v = src[p];
+        T* d = S + (be * N + ga) * SP + 1;
+        for (int a = al; a < SP - 1; a += N) d[a] = v;
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < N2; l += blockDim.x) {
+        T* d = S + l * SP;
+        T run = T(0);
+        d[0] = run;
+#pragma unroll 8
+        for (int a = 1; a < SP; ++a) {
+            run += d[a];
+            d[a] = run;
+        }
+    }
+    __syncthreads();
+}
+
+// One row (dalpha, dbeta, dgamma, LEN) of the unit (a0, be, ga) in prefix
+// form: P[k] += S[lo + k + LEN] - S[lo + k].
+template <int N, typename T>
+__device__ __forceinline__ void prefix_row(const T* S, const int be, const int ga, const int a0, const uchar4 w,
+                                           T (&P)[8]) {
+    constexpr int M = N - 1, SP = rows_sp<N>();
+    const T* lo = S + (((be + w.y) & M) * N + ((ga + w.z) & M)) * SP + ((a0 + w.x) & M);
+    const T* hi = lo + w.w;
+    T a[8], b[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        a[k] = lo[k];
+        b[k] = hi[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) P[k] += b[k] - a[k];
+}
+
+// The forward and JVP sums over the lines [ls, lend) of one class for the
+// thread's units of 8 consecutive alpha points, added at the points' cell
+// indices p = M q (mod N).  Plane sums come from the rows of S in prefix
+// form; the first nc rows of every line are the class's central row
+// {a u : 0 < |a| <= A} (A > 0), summed once per unit and taken as the start
+// of each line's plane sums.  Line windows come from S (WG false: a value is
+// the difference of neighbouring prefix entries) or from the global copy gw
+// (WG true).
 template <typename T, bool KAHAN, int N, bool WG>
-__device__ void class_units(const PlanDev& P, const int (&Mm)[9], int ls, int lend, const int A, const int nc,
-                            const T* __restrict__ g, const T* gw, T* __restrict__ dst, T* __restrict__ comp) {
-    constexpr int N2 = N * N, M = N - 1, SA = rows_sa<N>(), SW = rows_sw<N>(), NU = (N / 8) * N2;
+__device__ void class_units_prefix(const PlanDev& P, const int (&Mm)[9], int ls, int lend, const int A, const int nc,
+                                   const T* __restrict__ S, const T* gw, T* __restrict__ dst, T* __restrict__ comp) {
+    constexpr int N2 = N * N, M = N - 1, SP = rows_sp<N>(), SW = rows_sw<N>(), NU = (N / 8) * N2;
     for (int u = threadIdx.x; u < NU; u += blockDim.x) {
         const int ga = u & M, be = (u / N) & M, a0 = (u / N2) * 8;
-        T acc[8], cmp[8];
+        T acc[8], cmp[8], C[8];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) acc[t] = cmp[t] = T(0);
-        T C0 = T(0), CD[7];
-#pragma unroll
-        for (int t = 0; t < 7; ++t) CD[t] = T(0);
-        if (A > 0) central_rows<N>(A, g, be, ga, a0, C0, CD);
+        for (int t = 0; t < 8; ++t) acc[t] = cmp[t] = C[t] = T(0);
+        if (A > 0) {  // the central row {a u : 0 < |a| <= A}: [-A, -1] and [1, A] along alpha
+            prefix_row<N>(S, be, ga, a0, make_uchar4((unsigned char)((N - A) & M), 0, 0, (unsigned char)A), C);
+            prefix_row<N>(S, be, ga, a0, make_uchar4(1, 0, 0, (unsigned char)A), C);
+        }
         int4 e = __ldg(P.rline + ls);
         T cd = line_weight<T>(P, ls);
         int rs = __ldg(P.rrow_start + ls);
         for (int li = ls; li < lend; ++li) {
             const int re = __ldg(P.rrow_start + li + 1);
-            // next line's descriptor in flight while this line is summed
             const int ln = min(li + 1, lend - 1);
             const int4 e_n = __ldg(P.rline + ln);
             const T c_n = line_weight<T>(P, ln);
-            T P0 = C0, D[7], W[8];
+            T Pk[8], W[8];
 #pragma unroll
-            for (int t = 0; t < 7; ++t) D[t] = CD[t];
-#pragma unroll
-            for (int t = 0; t < 8; ++t) W[t] = T(0);
-            plane_rows<N>(P.rrow, rs + nc, re, g, be, ga, a0, P0, D);
+            for (int t = 0; t < 8; ++t) {
+                Pk[t] = C[t];
+                W[t] = T(0);
+            }
+            for (int r = rs + nc; r < re; ++r) prefix_row<N>(S, be, ga, a0, __ldg(P.rrow + r), Pk);
             for (int j = 1; j <= e.w; ++j) {
                 if (WG) {
                     const T* bp = gw + (((be + j * e.y) & M) * SW + ((a0 + j * e.x) & M)) * N + ((ga + j * e.z) & M);
@@ -441,19 +469,21 @@ __device__ void class_units(const PlanDev& P, const int (&Mm)[9], int ls, int le
 #pragma unroll
                     for (int t = 0; t < 8; ++t) W[t] += bp[t * N] + bm[t * N];
                 } else {
-                    const T* bp = g + (((be + j * e.y) & M) * N + ((ga + j * e.z) & M)) * SA + ((a0 + j * e.x) & M);
-                    const T* bm = g + (((be - j * e.y) & M) * N + ((ga - j * e.z) & M)) * SA + ((a0 - j * e.x) & M);
+                    const T* bp = S + (((be + j * e.y) & M) * N + ((ga + j * e.z) & M)) * SP + ((a0 + j * e.x) & M);
+                    const T* bm = S + (((be - j * e.y) & M) * N + ((ga - j * e.z) & M)) * SP + ((a0 - j * e.x) & M);
+                    T xp[9], xm[9];
 #pragma unroll
-                    for (int t = 0; t < 8; ++t) W[t] += bp[t] + bm[t];
+                    for (int t = 0; t < 9; ++t) {
+                        xp[t] = bp[t];
+                        xm[t] = bm[t];
+                    }
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) W[t] += (xp[t + 1] - xp[t]) + (xm[t + 1] - xm[t]);
                 }
             }
             const T c = cd;
-            T Pk = P0;
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                if (t > 0) Pk += D[t - 1];
-                comp_add<T, KAHAN>(acc[t], cmp[t], c * W[t] * Pk);
-            }
+            for (int t = 0; t < 8; ++t) comp_add<T, KAHAN>(acc[t], cmp[t], c * W[t] * Pk[t]);
             e = e_n;
             cd = c_n;
             rs = re;
@@ -710,13 +740,12 @@ __device__ void rows3d_item(const PlanDev& P, const int lb, const int le, const 
                 Mm[t] = __ldg(cdp + t);
                 Mi[t] = __ldg(cdp + 9 + t);
             }
-            relayout_smem<T, N>(Mi, rsrc, g);
             if (MODE == F3_JVP) relayout_glob<T, N>(Mi, wsrc, gw);
-            __syncthreads();
+            relayout_prefix<T, N>(Mi, rsrc, g);  // ends with a barrier
             // the shared central row: A = floor(Ntilde / |u|_inf), u = (Mm[0], Mm[3], Mm[6])
             const int un = max(abs(Mm[0]), max(abs(Mm[3]), abs(Mm[6])));
             const int A = P.Ntilde / un;
-            class_units<T, KAHAN, N, MODE == F3_JVP>(P, Mm, ls, lend, A, A > 0 ? 2 : 0, g, gw, dst, comp);
+            class_units_prefix<T, KAHAN, N, MODE == F3_JVP>(P, Mm, ls, lend, A, A > 0 ? 2 : 0, g, gw, dst, comp);
             __syncthreads();
         }
     }
@@ -840,7 +869,8 @@ int f3_size(const BatchDev& b, int prec, int mode, size_t* smem, bool* rows) {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t sa = (size_t)(N == 32 ? rows_sa<32>() : rows_sa<16>());
+    // the VJP's row layout (stride rows_sa) and the forward / JVP prefix form (rows_sp)
+    const size_t sa = (size_t)(N == 32 ? std::max(rows_sa<32>(), rows_sp<32>()) : std::max(rows_sa<16>(), rows_sp<16>()));
     const size_t s_rows = (size_t)N * N * sa * es, s_dir = (size_t)(N + 2 * H) * N * N * es;
     r = r && s_rows + 1024 <= (size_t)optin;
     if (mode != F3_FWD && !r) return 0;
