@@ -250,23 +250,6 @@ __host__ __device__ constexpr int rows_sw() {
     return N + 7;
 }
 
-// The cell src in class coordinates q = M^-1 p (mod N), in shared memory:
-// g[(beta N + gamma) SA + alpha].  Neighbouring p (last axis) map to
-// neighbouring gamma when w3 is the last axis.
-template <typename T, int N>
-__device__ __forceinline__ void relayout_smem(const int (&Mi)[9], const T* __restrict__ src, T* __restrict__ g) {
-    constexpr int N2 = N * N, N3 = N2 * N, M = N - 1, SA = rows_sa<N>();
-    for (int p = threadIdx.x; p < N3; p += blockDim.x) {
-        const int p0 = p / N2, p1 = (p / N) & M, p2 = p & M;
-        const int al = (Mi[0] * p0 + Mi[1] * p1 + Mi[2] * p2) & M;
-        const int be = (Mi[3] * p0 + Mi[4] * p1 + Mi[5] * p2) & M;
-        const int ga = (Mi[6] * p0 + Mi[7] * p1 + Mi[8] * p2) & M;
-        const T v = src[p];
-        T* d = g + (be * N + ga) * SA;
-        for (int a = al; a < SA; a += N) d[a] = v;  // alpha and its repeats below SA
-    }
-}
-
 // The same in the CTA's global scratch for line-window taps, gamma fastest
 // (a warp's 32 gammas share cache lines): gw[(beta SW + alpha) N + gamma],
 // alpha < 7 repeated after N - 1.  Read back with plain loads after a CTA
@@ -561,30 +544,29 @@ __device__ void vjp_class(const PlanDev& P, const int (&Mm)[9], const int (&Mi)[
                           T* gC, T* accC, T* cmpC, T* __restrict__ dst, T* __restrict__ comp) {
     constexpr int N2 = N * N, N3 = N2 * N, M = N - 1, SA = rows_sa<N>(), SW = rows_sw<N>(), NU = (N / 8) * N2;
     const int NT = blockDim.x, tid = threadIdx.x;
-    relayout_smem<T, N>(Mi, fcell, g);
     relayout_glob<T, N>(Mi, fcell, gwf);
     relayout_compact<T, N>(Mi, gcell, gC);
     for (int i = tid; i < N3; i += NT) {
         accC[i] = T(0);
         if (KAHAN) cmpC[i] = T(0);
     }
-    __syncthreads();
+    // pass A reads the plane rows of f from its prefix form (one per class);
+    // pass B writes each line's product Y in the direct row layout over it
+    relayout_prefix<T, N>(Mi, fcell, g);  // ends with a barrier
     // pass A: X = g P_e(f), then Omega_e(X)
     for (int li = ls; li < lend; ++li) {
         const int rs = __ldg(P.rrow_start + li), re = __ldg(P.rrow_start + li + 1);
         for (int u = tid; u < NU; u += NT) {
             const int ga = u & M, be = (u / N) & M, a0 = (u / N2) * 8;
-            T P0 = T(0), D[7], gv[8];
+            T Pk[8], gv[8];
 #pragma unroll
-            for (int t = 0; t < 7; ++t) D[t] = T(0);
-            plane_rows<N>(P.rrow, rs, re, g, be, ga, a0, P0, D);
+            for (int t = 0; t < 8; ++t) Pk[t] = T(0);
+            for (int r = rs; r < re; ++r) prefix_row<N>(g, be, ga, a0, __ldg(P.rrow + r), Pk);
             load8<N>(gC + (be * N + a0) * N + ga, gv);
-            T Pk = P0;
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
-                if (t > 0) Pk += D[t - 1];
                 T* xp = X + (be * SW + a0 + t) * N + ga;
-                const T x = gv[t] * Pk;
+                const T x = gv[t] * Pk[t];
                 xp[0] = x;
                 if (a0 + t < SW - N) xp[N2] = x;
             }
