@@ -94,10 +94,17 @@ struct CellMoments {
             s[3] += q * (double)(y * y + x * x);
         }
     }
-    __device__ __forceinline__ void finish(double* red, const double h, const double L, double* mom) {
+    // SUB > 0: the block holds several cells, SUB threads each; red is the
+    // group's own part of the reduction buffer and only a group with store
+    // writes mom (every group reaches the barrier).
+    template <int SUB = 0>
+    __device__ __forceinline__ void finish(double* red, const double h, const double L, double* mom,
+                                           const bool store = true) {
         double m[4];
+        static_assert(SUB == 0 || sizeof(T) == 4, "sub-block moments in FP32 only");
+        const int tl = SUB ? (int)(threadIdx.x % SUB) : (int)threadIdx.x;
         if constexpr (sizeof(T) == 4) {
-            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+            const int lane = tl & 31, wid = tl >> 5, nw = (SUB ? SUB : (int)blockDim.x) >> 5;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
 #pragma unroll
@@ -134,7 +141,7 @@ struct CellMoments {
             for (int i = 0; i < 4; ++i) m[i] = (double)s[i] + (double)c[i];
             block_reduce_fixed<4>(m, red);
         }
-        if (threadIdx.x == 0) {
+        if (tl == 0 && store) {
             const double h2 = h * h;
             mom[0] = h2 * m[0];
             mom[1] = h2 * (h * m[1] - L * m[0]);
@@ -497,12 +504,16 @@ __device__ __forceinline__ void fixed_body(const int4* __restrict__ pairs, const
 // N x N), used on the last forward pass to apply the loss kernel's transform;
 // KH = 2: by the complex factor kh + i dw[row frequency] instead; KH = 3: by
 // kh + i dw[column frequency].
-template <typename C, int N, int LD, int R, int NS, bool INV, bool COLS, int KH = 0>
+// SUB > 0: the block works on several cells at once, SUB threads per cell;
+// each group transforms its own buffers (the barriers stay block-wide).
+template <typename C, int N, int LD, int R, int NS, bool INV, bool COLS, int KH = 0, int SUB = 0>
 __device__ __forceinline__ void fft_pass(const C* __restrict__ src, C* __restrict__ dst, const C* __restrict__ tw,
                                          const decltype(C::x)* __restrict__ kh = nullptr,
                                          const decltype(C::x)* __restrict__ dw = nullptr) {
     constexpr int NB = N / R;
-    for (int b = threadIdx.x; b < N * NB; b += blockDim.x) {
+    const int t0 = SUB ? (int)(threadIdx.x % SUB) : (int)threadIdx.x;
+    const int nt = SUB ? SUB : (int)blockDim.x;
+    for (int b = t0; b < N * NB; b += nt) {
         const int line = b % N, j = b / N;
         C v[R];
 #pragma unroll
@@ -538,26 +549,26 @@ __device__ __forceinline__ void fft_pass(const C* __restrict__ src, C* __restric
     }
 }
 
-template <typename C, int N, int LD, bool INV, bool COLS, int KH, int NS, int R, int... Rs>
+template <typename C, int N, int LD, bool INV, bool COLS, int KH, int SUB, int NS, int R, int... Rs>
 __device__ __forceinline__ C* fft_passes(C* a, C* b, const C* tw, const decltype(C::x)* kh,
                                          const decltype(C::x)* dw) {
-    fft_pass<C, N, LD, R, NS, INV, COLS, sizeof...(Rs) == 0 ? KH : 0>(a, b, tw, kh, dw);
+    fft_pass<C, N, LD, R, NS, INV, COLS, sizeof...(Rs) == 0 ? KH : 0, SUB>(a, b, tw, kh, dw);
     __syncthreads();
     if constexpr (sizeof...(Rs) > 0)
-        return fft_passes<C, N, LD, INV, COLS, KH, NS * R, Rs...>(b, a, tw, kh, dw);
+        return fft_passes<C, N, LD, INV, COLS, KH, SUB, NS * R, Rs...>(b, a, tw, kh, dw);
     else
         return b;
 }
 
 // All N line transforms of length N; returns the buffer holding the result.
 // KH: the last pass also multiplies by kh (1) or kh + i dw (2, 3) (see fft_pass).
-template <typename C, int N, int LD, bool INV, bool COLS, int KH = 0>
+template <typename C, int N, int LD, bool INV, bool COLS, int KH = 0, int SUB = 0>
 __device__ __forceinline__ C* fft_lines(C* a, C* b, const C* tw, const decltype(C::x)* kh = nullptr,
                                         const decltype(C::x)* dw = nullptr) {
-    if constexpr (N == 64) return fft_passes<C, N, LD, INV, COLS, KH, 1, 8, 8>(a, b, tw, kh, dw);
-    else if constexpr (N == 48) return fft_passes<C, N, LD, INV, COLS, KH, 1, 3, 4, 4>(a, b, tw, kh, dw);
-    else if constexpr (N == 32) return fft_passes<C, N, LD, INV, COLS, KH, 1, 4, 8>(a, b, tw, kh, dw);
-    else return fft_passes<C, N, LD, INV, COLS, KH, 1, 4, 4>(a, b, tw, kh, dw);  // N == 16
+    if constexpr (N == 64) return fft_passes<C, N, LD, INV, COLS, KH, SUB, 1, 8, 8>(a, b, tw, kh, dw);
+    else if constexpr (N == 48) return fft_passes<C, N, LD, INV, COLS, KH, SUB, 1, 3, 4, 4>(a, b, tw, kh, dw);
+    else if constexpr (N == 32) return fft_passes<C, N, LD, INV, COLS, KH, SUB, 1, 4, 8>(a, b, tw, kh, dw);
+    else return fft_passes<C, N, LD, INV, COLS, KH, SUB, 1, 4, 4>(a, b, tw, kh, dw);  // N == 16
 }
 
 // The first pass (NS = 1, no twiddles) of a transform that reads a stored
@@ -588,7 +599,7 @@ __device__ __forceinline__ C* icols_from(const C* F, C* A, C* B, const C* tw, Mu
     fft_pass_mul<C, N, LD, R, true, true>(F, A, mul);
     __syncthreads();
     if constexpr (sizeof...(Rs) > 0)
-        return fft_passes<C, N, LD, true, true, 0, R, Rs...>(A, B, tw, nullptr, nullptr);
+        return fft_passes<C, N, LD, true, true, 0, 0, R, Rs...>(A, B, tw, nullptr, nullptr);
     else
         return A;
 }
@@ -714,11 +725,15 @@ __device__ __forceinline__ void strip_walk(const T* __restrict__ sF, T* __restri
 // W_e + i W_{e^perp} (both real: f is real and the window transforms even),
 // and the loss takes one of fhat Ktilde; the cell is copied afterwards for
 // the direct gathers of the remaining pairs.
-template <typename T, bool KAHAN, int N, int H, int NT, bool SCAN>
+// SUB > 0 (16^2 FP32 cells, see quad16): the block evaluates several cells
+// at once, SUB = NT threads each with their own shared memory; store is
+// false for a group without a cell of its own (it runs on another group's
+// data so that every barrier is reached, and writes nothing).
+template <typename T, bool KAHAN, int N, int H, int NT, bool SCAN, int SUB = 0>
 __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, const int pe, const T* __restrict__ fcell,
                                              T* __restrict__ qcell, double* __restrict__ mom, unsigned char* smem,
                                              double* red, const bool do_loss, const int scan_j, const bool wfft,
-                                             const bool fwin = false) {
+                                             const bool fwin = false, const bool store = true) {
     using C = typename Cplx<T>::type;
     using G = GeoF<N, H, SCAN>;
     constexpr int W = G::W, RS = G::RS, HW = G::HW, LD = G::LD;
@@ -727,7 +742,8 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
     constexpr bool VEC = !SCAN && sizeof(T) == 4 && (N == 32 || N == 64);
     using PM = PointMap<N, NT, VEC>;
     constexpr int PPT = PM::PPT;
-    const int tid = threadIdx.x;
+    static_assert(SUB == 0 || (SUB == NT && !SCAN && !VEC), "a sub-block body is the plain FFT body");
+    const int tid = SUB ? (int)(threadIdx.x % SUB) : (int)threadIdx.x;
     T* sF = reinterpret_cast<T*>(smem);
     T* sRe = reinterpret_cast<T*>(smem + cell_bytes<T, N, H, SCAN>());
     T* sRp = sRe + N * N;
@@ -811,13 +827,13 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
     // transform carries the two, and with parts of one size the rounding of
     // each stays relative to itself.
     auto loss_fft = [&](auto fk, const T* dw) {
-        C* r = fft_lines<C, N, LD, false, false>(A, B, tw);
+        C* r = fft_lines<C, N, LD, false, false, 0, SUB>(A, B, tw);
         if (dw)  // times Ktilde + i s D: D at the row frequency (W_(1,0)), with SCAN at the column one (W_(0,1))
-            r = fft_lines<C, N, LD, false, true, SCAN ? 3 : 2>(r, r == A ? B : A, tw, kh, dw);
+            r = fft_lines<C, N, LD, false, true, SCAN ? 3 : 2, SUB>(r, r == A ? B : A, tw, kh, dw);
         else
-            r = fft_lines<C, N, LD, false, true, 1>(r, r == A ? B : A, tw, kh);  // times Ktilde
-        r = fft_lines<C, N, LD, true, true>(r, r == A ? B : A, tw);
-        r = fft_lines<C, N, LD, true, false>(r, r == A ? B : A, tw);
+            r = fft_lines<C, N, LD, false, true, 1, SUB>(r, r == A ? B : A, tw, kh);  // times Ktilde
+        r = fft_lines<C, N, LD, true, true, 0, SUB>(r, r == A ? B : A, tw);
+        r = fft_lines<C, N, LD, true, false, 0, SUB>(r, r == A ? B : A, tw);
         if (active) {
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
@@ -868,7 +884,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
     };
 
     if constexpr (!SCAN) {
-        if (fwin) {
+        if (SUB == 0 && fwin) {
             // fhat: f into A, forward transform (an even number of passes:
             // the result is in A), then into the cell's place F
             const T* djt;
@@ -1085,12 +1101,12 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
             if (k < PPT - 1 || last_ok) {
                 const int y = y0 + PM::dy(k), xk = x + PM::dx(k);
                 const T q = KAHAN ? acc[k] + cmp[k] : acc[k];
-                qcell[y * N + xk] = q;
+                if (store) qcell[y * N + xk] = q;
                 if (mom) cm.add(q, y, xk);
             }
         }
     }
-    if (mom) cm.finish(red, P.h, P.L, mom);
+    if (mom) cm.template finish<SUB>(red, P.h, P.L, mom, store);
 }
 
 // elements of the f buffer; the P buffer follows it
@@ -1180,6 +1196,21 @@ __global__ void k_reduce_partials(const T* __restrict__ part, int S, int n, T* _
     Q[i] = KAHAN ? s + c : s;
 }
 
+// 16^2 cells in FP32 with the plain FFT body (loss_fft 1 or 2, no SCAN) on
+// 256 threads go four at a time, 64 threads per cell (quad16): the FFT passes
+// of a lone 16^2 cell keep only 64 of 256 threads busy and each of its ~13
+// barriers serves one cell; four cells share them.
+template <typename T, int NT>
+__host__ __device__ constexpr bool quad16_eligible(const int N, const int Nt, const bool khat, const int fft,
+                                                   const int sj) {
+    return NT == 256 && sizeof(T) == 4 && N == 16 && Nt == 3 && khat && (fft == 1 || fft == 2) &&
+           !(sj > 0 && sj <= 3);
+}
+template <typename T>
+__host__ __device__ constexpr size_t quad16_bytes() {  // shared memory of one 16^2 cell, 128-byte aligned
+    return (cell_bytes<T, 16, 3, false>() + 2 * 16 * 17 * sizeof(typename Cplx<T>::type) + 127) / 128 * 128;
+}
+
 template <typename T, bool KAHAN, int NT>
 __global__ void __launch_bounds__(NT, 2) k_fused2d_batched(BatchDev B, int n_cells, const int* __restrict__ cell_plan,
                                                            const int64_t* __restrict__ cell_offset,
@@ -1188,23 +1219,69 @@ __global__ void __launch_bounds__(NT, 2) k_fused2d_batched(BatchDev B, int n_cel
                                                            double* __restrict__ moments) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32 * 4];
-    __shared__ int s_cell;
+    __shared__ int s_cell, s_pi, s_more[3];
     __shared__ PlanDev s_plan;
     for (;;) {
         if (threadIdx.x == 0) {
             const int c = atomicAdd(counter, 1);
             s_cell = c < n_cells ? order[c] : -1;
+            s_more[0] = s_more[1] = s_more[2] = -1;
             if (s_cell >= 0) {
                 const int pi = cell_plan[s_cell];
+                s_pi = pi;
 #pragma unroll
                 for (int q = 0; q < QDVM_MAX_BATCH_PLANS; ++q)
                     if (q == pi) s_plan = B.p[q];
+                // the schedule lists cells plan by plan, so the next three
+                // entries are almost always cells of the same 16^2 plan
+                if (quad16_eligible<T, NT>(s_plan.N, s_plan.Ntilde, s_plan.khat != nullptr, s_plan.tfft,
+                                           s_plan.tsj)) {
+                    const int c2 = atomicAdd(counter, 3);
+                    for (int k = 0; k < 3; ++k) s_more[k] = c2 + k < n_cells ? order[c2 + k] : -1;
+                }
             }
         }
         __syncthreads();
         const int cell = s_cell;
         if (cell < 0) break;
         const PlanDev P = s_plan;
+        if constexpr (quad16_eligible<T, NT>(16, 3, true, 1, 0)) {
+            if (quad16_eligible<T, NT>(P.N, P.Ntilde, P.khat != nullptr, P.tfft, P.tsj)) {
+                // group g (64 threads) takes cell g: the first cell, then the
+                // three more ones of the same plan; a group without one runs
+                // on the first cell's data and stores nothing
+                const int g = threadIdx.x / 64;
+                const int cg = g == 0 ? cell : s_more[g - 1];
+                const bool mine = cg >= 0 && cell_plan[cg] == s_pi;
+                const int src = mine ? cg : cell;
+                const int64_t offg = cell_offset[src];
+                fftloss_body<T, KAHAN, 16, 3, 64, false, 64>(
+                    P, 0, P.n_pairs, f + offg, Q + offg, moments ? moments + (size_t)src * 4 : nullptr,
+                    smem_raw + g * quad16_bytes<T>(), red + g * 32, true, 0, P.tfft == 2, false, mine);
+                __syncthreads();
+                // drawn cells of another plan, one at a time
+                for (int k = 0; k < 3; ++k) {
+                    const int ck = s_more[k];
+                    if (ck < 0 || cell_plan[ck] == s_pi) continue;
+                    if (threadIdx.x == 0) {
+                        const int pk = cell_plan[ck];
+#pragma unroll
+                        for (int q = 0; q < QDVM_MAX_BATCH_PLANS; ++q)
+                            if (q == pk) s_plan = B.p[q];
+                    }
+                    __syncthreads();
+                    const PlanDev Pk = s_plan;
+                    const int64_t offk = cell_offset[ck];
+                    T* sFk = reinterpret_cast<T*>(smem_raw);
+                    T* sPk = sFk + buf_f_elems(Pk.N, Pk.Ntilde);
+                    run_cell<T, KAHAN, NT>(Pk, 0, Pk.n_pairs, f + offk, Q + offk,
+                                           moments ? moments + (size_t)ck * 4 : nullptr, sFk, sPk, red, Pk.tjd,
+                                           Pk.tfft, Pk.tsj, true);
+                    __syncthreads();
+                }
+                continue;
+            }
+        }
         const int64_t off = cell_offset[cell];
         T* sF = reinterpret_cast<T*>(smem_raw);
         T* sP = sF + buf_f_elems(P.N, P.Ntilde);

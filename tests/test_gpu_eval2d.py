@@ -312,3 +312,38 @@ def total_scale(f, K):
     F = np.fft.fft2(f)
     R = np.fft.ifft2(np.conj(F) * F).real
     return 2.0 * float(np.sum(K * R))
+
+
+@pytest.mark.parametrize("n16,n12", [(1, 0), (5, 0), (7, 3), (4, 1), (9, 6)])
+@pytest.mark.parametrize("loss_fft", [1, 2])
+def test_quad16_tails_and_other_plans(q, torch, n16, n12, loss_fft):
+    """16^2 FP32 cells go four to a CTA (64 threads each): batches whose
+    count of 16^2 cells is not a multiple of four, and 12^2 cells drawn
+    along with them (the schedule lists the cheaper 12^2 plan right after),
+    against the oracle cell by cell, Q and moments."""
+    b16 = synth.batch_2d(n16, Ns=(16,), L=8.0, seed=60 + n16)
+    b12 = synth.batch_2d(max(n12, 1), Ns=(12,), L=8.0, seed=70 + n12)
+    Ns = np.concatenate([b16.Ns, b12.Ns[:n12]])
+    fs = np.concatenate([b16.f, b12.f[: n12 * 144]])
+    order = np.random.default_rng(n16 + 10 * n12).permutation(len(Ns))
+    cells = [fs[int(sum(Ns[:i] ** 2)):int(sum(Ns[:i + 1] ** 2))] for i in range(len(Ns))]
+    Ns = Ns[order]
+    fcat = np.concatenate([cells[i] for i in order])
+    b = synth.Batch(2, 8.0, Ns, fcat)
+    plans = [q.Plan(2, 16, 3, 8.0), q.Plan(2, 12, 3, 8.0)]
+    for p in plans:
+        p.set_tuning(threads=256, loss_fft=loss_fft, scan_j=0)
+    cp = torch.tensor([0 if n == 16 else 1 for n in b.Ns], dtype=torch.int32, device="cuda")
+    co = torch.tensor(b.offsets, dtype=torch.int64, device="cuda")
+    f = torch.tensor(b.f, dtype=torch.float32, device="cuda")
+    Q = torch.full_like(f, float("nan"))
+    Q, M = q.qdvm_eval_batched(plans, cp, co, f, "f32_kahan", out=Q)
+    Qn = Q.cpu().numpy().astype(np.float64)
+    Mn = M.cpu().numpy()
+    fin = f.cpu().numpy().astype(np.float64)
+    for c in range(b.n_cells):
+        r = oracle.q(b.cell(c, fin), 8.0, 3)
+        assert oracle.rel_linf(b.cell(c, Qn), r["Q"], r["scale"]) <= 1e-5, f"cell {c} (N={b.Ns[c]})"
+        mref = oracle.moments(b.cell(c, Qn), 8.0)
+        h2 = (16.0 / b.Ns[c]) ** 2
+        assert np.allclose(Mn[c], mref, rtol=0, atol=1e-12 * h2 * np.sum(np.abs(b.cell(c, Qn))) * 64)
