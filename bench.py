@@ -115,12 +115,27 @@ def profiled_value(key: str):
         return None
 
 
-def tuning_key(tunings: dict) -> str:
+def effective_tuning(t: dict, ntilde: int) -> tuple:
+    """(threads, direct_j, loss_fft, scan_j) with the parameters that select
+    no different code for this plan set to their neutral values: direct_j
+    only matters with the direct loss (loss_fft 0), scan_j only when it
+    reaches a pair of the cell (1 <= scan_j <= Ntilde) and the loss is an FFT."""
+    fft = t["loss_fft"]
+    dj = t["direct_j"] if fft == 0 else 2
+    sj = t["scan_j"] if fft > 0 and 1 <= t["scan_j"] <= ntilde else 0
+    return t["threads"], dj, fft, sj
+
+
+def tuning_key(tunings: dict, ntildes: dict | None = None) -> str:
     """The launch configuration of a batched 2D call as one string: per cell
     size N, the plan's threads,direct_j,loss_fft,scan_j (each cell runs with
-    its own plan's parameters)."""
-    return " ".join(f"{n}={t['threads']},{t['direct_j']},{t['loss_fft']},{t['scan_j']}"
-                    for n, t in sorted(tunings.items()))
+    its own plan's parameters), normalised by effective_tuning when the
+    plans' Ntilde are given."""
+    out = []
+    for n, t in sorted(tunings.items()):
+        v = effective_tuning(t, ntildes[n]) if ntildes else (t["threads"], t["direct_j"], t["loss_fft"], t["scan_j"])
+        out.append(f"{n}=" + ",".join(str(x) for x in v))
+    return " ".join(out)
 
 
 def profiled_tuning():
@@ -414,7 +429,7 @@ def run_gpu(args):
     else:
         q.qdvm_tune_batched(plans, cp, co, fs[0], "f32_kahan", workspace=wss)
     tunings = {int(n): p.tuning() for n, p in zip(NS, plans)}
-    key = tuning_key(tunings)
+    key = tuning_key(tunings, {int(n): p.Ntilde for n, p in zip(NS, plans)})
     graphs = [q.BatchedGraph(plans, cp, co, fs[k], Qs[k], Ms[k], "f32_kahan", workspace=wss) for k in range(ROTATE)]
 
     for g in graphs:  # first replay of a graph uploads it; keep that out of the timed region

@@ -89,3 +89,13 @@ def test_accuracy_leg_on_oracle_results():
     Mn[c, 0] = 1e-3 * h2 * scales[c]
     acc = bench.accuracy_leg(b, Qn, Mn)
     assert acc["mass_defect_rel_max_all_cells"] == pytest.approx(1e-3, rel=1e-9)
+
+
+def test_tuning_key_normalises_parameters_without_effect():
+    t = lambda dj, fft, sj: {"threads": 256, "direct_j": dj, "line_chunks": 0, "loss_fft": fft, "scan_j": sj}
+    nt = {16: 3, 32: 7, 48: 10, 64: 14}
+    a = bench.tuning_key({16: t(2, 2, 14), 32: t(1, 2, 10), 48: t(2, 2, 0), 64: t(0, 2, 0)}, nt)
+    b = bench.tuning_key({16: t(2, 2, 0), 32: t(2, 2, 0), 48: t(2, 2, 0), 64: t(2, 2, 0)}, nt)
+    assert a == b == "16=256,2,2,0 32=256,2,2,0 48=256,2,2,0 64=256,2,2,0"
+    assert bench.tuning_key({64: t(2, 2, 14)}, {64: 14}) == "64=256,2,2,14"
+    assert bench.tuning_key({16: t(1, 0, 5)}, {16: 3}) == "16=256,1,0,0"
