@@ -64,10 +64,10 @@ qdvm_status fused2d_eval_batched(const BatchDev& b, const qdvm_tuning& tu, int n
     size_t smem = 0;
     for (int i = 0; i < b.n_plans; ++i) {
         smem = std::max(smem, fused2d_smem_bytes(b.p[i].N, b.p[i].Ntilde, prec, b.p[i].tfft));
-        // 16^2 FP32 cells go four at a time on 256 threads (quad16)
-        if (prec != QDVM_F64 && tu.threads == 256 &&
-            quad16_eligible<float, 256>(b.p[i].N, b.p[i].Ntilde, b.p[i].khat != nullptr, b.p[i].tfft, b.p[i].tsj))
-            smem = std::max(smem, 4 * quad16_bytes<float>());
+        // small FP32 cells go several at a time on 256 threads (cell_groups)
+        if (prec != QDVM_F64 && tu.threads == 256)
+            smem = std::max(smem, group_smem_bytes<float>(cell_groups<float, 256>(
+                                      b.p[i].N, b.p[i].Ntilde, b.p[i].khat != nullptr, b.p[i].tfft, b.p[i].tsj)));
     }
     switch (prec) {
         case QDVM_F64:

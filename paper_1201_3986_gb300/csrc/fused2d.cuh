@@ -725,7 +725,7 @@ __device__ __forceinline__ void strip_walk(const T* __restrict__ sF, T* __restri
 // W_e + i W_{e^perp} (both real: f is real and the window transforms even),
 // and the loss takes one of fhat Ktilde; the cell is copied afterwards for
 // the direct gathers of the remaining pairs.
-// SUB > 0 (16^2 FP32 cells, see quad16): the block evaluates several cells
+// SUB > 0 (small FP32 cells, see cell_groups): the block evaluates several cells
 // at once, SUB = NT threads each with their own shared memory; store is
 // false for a group without a cell of its own (it runs on another group's
 // data so that every barrier is reached, and writes nothing).
@@ -742,7 +742,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
     constexpr bool VEC = !SCAN && sizeof(T) == 4 && (N == 32 || N == 64);
     using PM = PointMap<N, NT, VEC>;
     constexpr int PPT = PM::PPT;
-    static_assert(SUB == 0 || (SUB == NT && !SCAN && !VEC), "a sub-block body is the plain FFT body");
+    static_assert(SUB == 0 || (SUB == NT && !SCAN), "a sub-block body is the plain FFT body");
     const int tid = SUB ? (int)(threadIdx.x % SUB) : (int)threadIdx.x;
     T* sF = reinterpret_cast<T*>(smem);
     T* sRe = reinterpret_cast<T*>(smem + cell_bytes<T, N, H, SCAN>());
@@ -1196,19 +1196,90 @@ __global__ void k_reduce_partials(const T* __restrict__ part, int S, int n, T* _
     Q[i] = KAHAN ? s + c : s;
 }
 
-// 16^2 cells in FP32 with the plain FFT body (loss_fft 1 or 2, no SCAN) on
-// 256 threads go four at a time, 64 threads per cell (quad16): the FFT passes
-// of a lone 16^2 cell keep only 64 of 256 threads busy and each of its ~13
-// barriers serves one cell; four cells share them.
+// Small cells in FP32 with the plain FFT body (loss_fft 1 or 2, no SCAN) on
+// 256 threads go several at a time: four 16^2 cells of 64 threads each, two
+// 32^2 cells of 128.  A lone 16^2 cell keeps only 64 of 256 threads busy in
+// its FFT passes (a lone 32^2 cell 128 in its radix-8 passes), and each of
+// its ~13 barriers serves one cell; the cells of a group share them.
+// cell_groups returns the group size, 0 for one cell at a time.
 template <typename T, int NT>
-__host__ __device__ constexpr bool quad16_eligible(const int N, const int Nt, const bool khat, const int fft,
-                                                   const int sj) {
-    return NT == 256 && sizeof(T) == 4 && N == 16 && Nt == 3 && khat && (fft == 1 || fft == 2) &&
-           !(sj > 0 && sj <= 3);
+__host__ __device__ constexpr int cell_groups(const int N, const int Nt, const bool khat, const int fft, const int sj) {
+    if (!(NT == 256 && sizeof(T) == 4 && khat && (fft == 1 || fft == 2) && !(sj > 0 && sj <= Nt))) return 0;
+    return (N == 16 && Nt == 3) ? 4 : ((N == 32 && Nt == 7) ? 2 : 0);
+}
+// shared memory of one cell of a group, 128-byte aligned
+template <typename T, int N, int H>
+__host__ __device__ constexpr size_t group_cell_bytes() {
+    return (cell_bytes<T, N, H, false>() + 2 * (size_t)N * (N + 1) * sizeof(typename Cplx<T>::type) + 127) / 128 * 128;
 }
 template <typename T>
-__host__ __device__ constexpr size_t quad16_bytes() {  // shared memory of one 16^2 cell, 128-byte aligned
-    return (cell_bytes<T, 16, 3, false>() + 2 * 16 * 17 * sizeof(typename Cplx<T>::type) + 127) / 128 * 128;
+__host__ __device__ constexpr size_t group_smem_bytes(const int G) {
+    return G == 4 ? 4 * group_cell_bytes<T, 16, 3>() : (G == 2 ? 2 * group_cell_bytes<T, 32, 7>() : 0);
+}
+
+// One pass of the group body: thread group g (NT / G threads) evaluates cell
+// cg when mine, else runs on cell `fallback` and stores nothing.  A cell of
+// a groupable plan always goes through this body, whichever group takes it,
+// so its moments come out of the same reduction.
+template <typename T, bool KAHAN, int NT, int N, int H, int G>
+__device__ __forceinline__ void group_pass(const PlanDev& P, const int cg, const bool mine, const int fallback,
+                                           const int64_t* __restrict__ cell_offset, const T* __restrict__ f,
+                                           T* __restrict__ Q, double* __restrict__ moments, unsigned char* smem_raw,
+                                           double* red) {
+    constexpr int SUBT = NT / G;
+    const int g = threadIdx.x / SUBT;
+    const int src = mine ? cg : fallback;
+    const int64_t offg = cell_offset[src];
+    fftloss_body<T, KAHAN, N, H, SUBT, false, SUBT>(P, 0, P.n_pairs, f + offg, Q + offg,
+                                                    moments ? moments + (size_t)src * 4 : nullptr,
+                                                    smem_raw + g * group_cell_bytes<T, N, H>(), red + g * (128 / G),
+                                                    true, 0, P.tfft == 2, false, mine);
+    __syncthreads();
+}
+
+// A group of G cells of plan P (index pi): thread group g takes the first
+// cell (g = 0) or the g-th drawn one when it is of the same plan.  Drawn
+// cells of another plan then run one at a time: through their own group
+// body when their plan is groupable (group 0 takes the cell), else through
+// the one-cell body.
+template <typename T, bool KAHAN, int NT, int N, int H, int G>
+__device__ __forceinline__ void run_cell_group(const BatchDev& B, const PlanDev& P, const int cell, const int pi,
+                                               const int* more, PlanDev* s_plan, const int* __restrict__ cell_plan,
+                                               const int64_t* __restrict__ cell_offset, const T* __restrict__ f,
+                                               T* __restrict__ Q, double* __restrict__ moments,
+                                               unsigned char* smem_raw, double* red) {
+    constexpr int SUBT = NT / G;
+    const int g = threadIdx.x / SUBT;
+    const int cg = g == 0 ? cell : more[g - 1];
+    group_pass<T, KAHAN, NT, N, H, G>(P, cg, cg >= 0 && cell_plan[cg] == pi, cell, cell_offset, f, Q, moments,
+                                      smem_raw, red);
+    for (int k = 0; k < G - 1; ++k) {
+        const int ck = more[k];
+        if (ck < 0 || cell_plan[ck] == pi) continue;
+        if (threadIdx.x == 0) {
+            const int pk = cell_plan[ck];
+#pragma unroll
+            for (int q = 0; q < QDVM_MAX_BATCH_PLANS; ++q)
+                if (q == pk) *s_plan = B.p[q];
+        }
+        __syncthreads();
+        const PlanDev Pk = *s_plan;
+        const int Gk = cell_groups<T, NT>(Pk.N, Pk.Ntilde, Pk.khat != nullptr, Pk.tfft, Pk.tsj);
+        if (Gk == 4) {
+            group_pass<T, KAHAN, NT, 16, 3, 4>(Pk, ck, threadIdx.x < NT / 4, ck, cell_offset, f, Q, moments, smem_raw,
+                                               red);
+        } else if (Gk == 2) {
+            group_pass<T, KAHAN, NT, 32, 7, 2>(Pk, ck, threadIdx.x < NT / 2, ck, cell_offset, f, Q, moments, smem_raw,
+                                               red);
+        } else {
+            const int64_t offk = cell_offset[ck];
+            T* sFk = reinterpret_cast<T*>(smem_raw);
+            T* sPk = sFk + buf_f_elems(Pk.N, Pk.Ntilde);
+            run_cell<T, KAHAN, NT>(Pk, 0, Pk.n_pairs, f + offk, Q + offk, moments ? moments + (size_t)ck * 4 : nullptr,
+                                   sFk, sPk, red, Pk.tjd, Pk.tfft, Pk.tsj, true);
+            __syncthreads();
+        }
+    }
 }
 
 template <typename T, bool KAHAN, int NT>
@@ -1232,12 +1303,13 @@ __global__ void __launch_bounds__(NT, 2) k_fused2d_batched(BatchDev B, int n_cel
 #pragma unroll
                 for (int q = 0; q < QDVM_MAX_BATCH_PLANS; ++q)
                     if (q == pi) s_plan = B.p[q];
-                // the schedule lists cells plan by plan, so the next three
-                // entries are almost always cells of the same 16^2 plan
-                if (quad16_eligible<T, NT>(s_plan.N, s_plan.Ntilde, s_plan.khat != nullptr, s_plan.tfft,
-                                           s_plan.tsj)) {
-                    const int c2 = atomicAdd(counter, 3);
-                    for (int k = 0; k < 3; ++k) s_more[k] = c2 + k < n_cells ? order[c2 + k] : -1;
+                // the schedule lists cells plan by plan, so the next entries
+                // are almost always cells of the same plan
+                const int G = cell_groups<T, NT>(s_plan.N, s_plan.Ntilde, s_plan.khat != nullptr, s_plan.tfft,
+                                                 s_plan.tsj);
+                if (G > 1) {
+                    const int c2 = atomicAdd(counter, G - 1);
+                    for (int k = 0; k < G - 1; ++k) s_more[k] = c2 + k < n_cells ? order[c2 + k] : -1;
                 }
             }
         }
@@ -1245,40 +1317,16 @@ __global__ void __launch_bounds__(NT, 2) k_fused2d_batched(BatchDev B, int n_cel
         const int cell = s_cell;
         if (cell < 0) break;
         const PlanDev P = s_plan;
-        if constexpr (quad16_eligible<T, NT>(16, 3, true, 1, 0)) {
-            if (quad16_eligible<T, NT>(P.N, P.Ntilde, P.khat != nullptr, P.tfft, P.tsj)) {
-                // group g (64 threads) takes cell g: the first cell, then the
-                // three more ones of the same plan; a group without one runs
-                // on the first cell's data and stores nothing
-                const int g = threadIdx.x / 64;
-                const int cg = g == 0 ? cell : s_more[g - 1];
-                const bool mine = cg >= 0 && cell_plan[cg] == s_pi;
-                const int src = mine ? cg : cell;
-                const int64_t offg = cell_offset[src];
-                fftloss_body<T, KAHAN, 16, 3, 64, false, 64>(
-                    P, 0, P.n_pairs, f + offg, Q + offg, moments ? moments + (size_t)src * 4 : nullptr,
-                    smem_raw + g * quad16_bytes<T>(), red + g * 32, true, 0, P.tfft == 2, false, mine);
-                __syncthreads();
-                // drawn cells of another plan, one at a time
-                for (int k = 0; k < 3; ++k) {
-                    const int ck = s_more[k];
-                    if (ck < 0 || cell_plan[ck] == s_pi) continue;
-                    if (threadIdx.x == 0) {
-                        const int pk = cell_plan[ck];
-#pragma unroll
-                        for (int q = 0; q < QDVM_MAX_BATCH_PLANS; ++q)
-                            if (q == pk) s_plan = B.p[q];
-                    }
-                    __syncthreads();
-                    const PlanDev Pk = s_plan;
-                    const int64_t offk = cell_offset[ck];
-                    T* sFk = reinterpret_cast<T*>(smem_raw);
-                    T* sPk = sFk + buf_f_elems(Pk.N, Pk.Ntilde);
-                    run_cell<T, KAHAN, NT>(Pk, 0, Pk.n_pairs, f + offk, Q + offk,
-                                           moments ? moments + (size_t)ck * 4 : nullptr, sFk, sPk, red, Pk.tjd,
-                                           Pk.tfft, Pk.tsj, true);
-                    __syncthreads();
-                }
+        if constexpr (NT == 256 && sizeof(T) == 4) {
+            const int G = cell_groups<T, NT>(P.N, P.Ntilde, P.khat != nullptr, P.tfft, P.tsj);
+            if (G == 4) {
+                run_cell_group<T, KAHAN, NT, 16, 3, 4>(B, P, cell, s_pi, s_more, &s_plan, cell_plan, cell_offset, f, Q,
+                                                       moments, smem_raw, red);
+                continue;
+            }
+            if (G == 2) {
+                run_cell_group<T, KAHAN, NT, 32, 7, 2>(B, P, cell, s_pi, s_more, &s_plan, cell_plan, cell_offset, f, Q,
+                                                       moments, smem_raw, red);
                 continue;
             }
         }

@@ -347,3 +347,46 @@ def test_quad16_tails_and_other_plans(q, torch, n16, n12, loss_fft):
         mref = oracle.moments(b.cell(c, Qn), 8.0)
         h2 = (16.0 / b.Ns[c]) ** 2
         assert np.allclose(Mn[c], mref, rtol=0, atol=1e-12 * h2 * np.sum(np.abs(b.cell(c, Qn))) * 64)
+
+
+@pytest.mark.parametrize("n32,n24", [(1, 0), (3, 2), (4, 1)])
+def test_pair32_tails_and_other_plans(q, torch, n32, n24):
+    """32^2 FP32 cells go two to a CTA (128 threads each): odd counts, and
+    24^2 cells drawn along, against the oracle cell by cell."""
+    b32 = synth.batch_2d(n32, Ns=(32,), L=8.0, seed=80 + n32)
+    b24 = synth.batch_2d(max(n24, 1), Ns=(24,), L=8.0, seed=90 + n24)
+    Ns = np.concatenate([b32.Ns, b24.Ns[:n24]])
+    f = np.concatenate([b32.f, b24.f[: n24 * 576]])
+    b = synth.Batch(2, 8.0, Ns, f)
+    plans = [q.Plan(2, 32, 8, 8.0), q.Plan(2, 24, 8, 8.0)]
+    for p in plans:
+        p.set_tuning(threads=256, loss_fft=2, scan_j=0)
+    cp = torch.tensor([0 if n == 32 else 1 for n in b.Ns], dtype=torch.int32, device="cuda")
+    co = torch.tensor(b.offsets, dtype=torch.int64, device="cuda")
+    ft = torch.tensor(b.f, dtype=torch.float32, device="cuda")
+    Q, M = q.qdvm_eval_batched(plans, cp, co, ft, "f32_kahan")
+    Qn = Q.cpu().numpy().astype(np.float64)
+    Mn = M.cpu().numpy()
+    fin = ft.cpu().numpy().astype(np.float64)
+    for c in range(b.n_cells):
+        r = oracle.q(b.cell(c, fin), 8.0, 8)
+        assert oracle.rel_linf(b.cell(c, Qn), r["Q"], r["scale"]) <= 1e-5, f"cell {c} (N={b.Ns[c]})"
+        h2 = (16.0 / b.Ns[c]) ** 2
+        mref = oracle.moments(b.cell(c, Qn), 8.0)
+        assert np.allclose(Mn[c], mref, rtol=0, atol=1e-12 * h2 * np.sum(np.abs(b.cell(c, Qn))) * 64)
+
+
+def test_batched_results_repeat_bit_for_bit(q, torch):
+    """The 4096-cell mixed batch evaluated three times: Q and the moments are
+    identical bit for bit, whichever CTA draws which cell (the persistent
+    schedule is a race on an atomic counter; a cell's arithmetic must not
+    depend on it)."""
+    Ns = (16, 32, 48, 64)
+    b = synth.batch_2d(4096, Ns=Ns, L=8.0, seed=0)
+    plans = [q.Plan(2, n, 8, 8.0, kernel="unit") for n in Ns]
+    for p in plans:
+        p.set_tuning(threads=256, loss_fft=2, scan_j=0)
+    cp, co, f = _batch_tensors(torch, b, Ns, "f32_kahan")
+    runs = [q.qdvm_eval_batched(plans, cp, co, f, "f32_kahan") for _ in range(3)]
+    for Q, M in runs[1:]:
+        assert torch.equal(Q, runs[0][0]) and torch.equal(M, runs[0][1])
