@@ -99,7 +99,7 @@ enum { QDVM_ENGINE_AUTO = 0, QDVM_ENGINE_DIRECT = 1, QDVM_ENGINE_SCAN = 2 };
  *   loss_fft    1: the loss part sum_e c_e f V_e is evaluated as one
  *               convolution per cell, f (K * f) with K the weighted
  *               displacement histogram of the terms, by an on-chip 2D FFT
- *               (mixed radix 3/4/8; cells of 16, 32, 48 or 64 points per axis
+ *               (mixed radix 4/6/8; cells of 16, 32, 48 or 64 points per axis
  *               with the default truncation); the lines then only sum the
  *               gain.  Rounding differs from the direct sums (no longer
  *               bit-exact on integer data).  0: direct sums.

@@ -5,7 +5,7 @@
 // displacement histogram of all (k, l) terms (its transform is the plan's
 // Ktilde, factorised line by line).  A work item (cell, chunk of lines)
 // therefore only sums the gain c_e W_e P_e of its lines; the first chunk of
-// a cell also evaluates K * f with a 3D Stockham FFT (mixed radix 2/4) over
+// a cell also evaluates K * f with a 3D Stockham FFT (mixed radix 4/8) over
 // the CTA's global scratch.  Without V there is no P buffer and no barrier
 // per line: each thread owns z-columns of 8 points at a fixed (y, x), runs
 // the item's lines for one column at a time and keeps the sums in
@@ -72,7 +72,7 @@ __device__ __forceinline__ C* fft3_passes(C* a, C* b, const C* tw) {
 
 template <typename C, int N, bool INV, int AXIS>
 __device__ __forceinline__ C* fft3_axis(C* a, C* b, const C* tw) {
-    if constexpr (N == 32) return fft3_passes<C, N, INV, AXIS, 1, 2, 4, 4>(a, b, tw);
+    if constexpr (N == 32) return fft3_passes<C, N, INV, AXIS, 1, 4, 8>(a, b, tw);
     else return fft3_passes<C, N, INV, AXIS, 1, 4, 4>(a, b, tw);  // N == 16
 }
 

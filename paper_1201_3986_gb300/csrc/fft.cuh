@@ -1,6 +1,6 @@
 // Small complex FFT building blocks shared by the on-chip 2D FFT (fused2d.cuh)
 // and the 3D FFT over global scratch (fast3d.cu): complex type per real
-// type, complex product, and in-register DFTs of radix 2, 3, 4 and 8.
+// type, complex product, and in-register DFTs of radix 2, 3, 4, 6 and 8.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -48,6 +48,24 @@ __device__ __forceinline__ void dft_small(C (&v)[R]) {
         v[1].y = m.y + sy;
         v[2].x = m.x - sx;
         v[2].y = m.y - sy;
+    } else if constexpr (R == 6) {
+        // X[k] = E[k] + w^k O[k], X[k+3] = E[k] - w^k O[k] (k < 3) with E, O
+        // the 3-point DFTs of the even and odd samples, w = exp(-+ 2 pi i / 6)
+        C e[3] = {v[0], v[2], v[4]};
+        C o[3] = {v[1], v[3], v[5]};
+        dft_small<3, INV>(e);
+        dft_small<3, INV>(o);
+        const S h = S(0.8660254037844386467637231707529362);  // sqrt(3)/2
+        // forward: w = 1/2 - i h, w^2 = -1/2 - i h; inverse: conjugates
+        const S s1 = INV ? h : -h;
+        const C o1 = {S(0.5) * o[1].x - s1 * o[1].y, S(0.5) * o[1].y + s1 * o[1].x};
+        const C o2 = {-S(0.5) * o[2].x - s1 * o[2].y, -S(0.5) * o[2].y + s1 * o[2].x};
+        v[0] = C{e[0].x + o[0].x, e[0].y + o[0].y};
+        v[3] = C{e[0].x - o[0].x, e[0].y - o[0].y};
+        v[1] = C{e[1].x + o1.x, e[1].y + o1.y};
+        v[4] = C{e[1].x - o1.x, e[1].y - o1.y};
+        v[2] = C{e[2].x + o2.x, e[2].y + o2.y};
+        v[5] = C{e[2].x - o2.x, e[2].y - o2.y};
     } else if constexpr (R == 8) {
         // X[k] = E[k] + w^k O[k], X[k+4] = E[k] - w^k O[k] (k < 4) with E, O
         // the 4-point DFTs of the even and odd samples, w = exp(-+ 2 pi i / 8)

@@ -492,7 +492,7 @@ __device__ __forceinline__ void fixed_body(const int4* __restrict__ pairs, const
 // Loss as one convolution (the paper's remark that the loss part is a plain
 // convolution): sum_e c_e V_e(i) = sum_m K(m) f(i + m) = (K * f)(i), K the
 // weighted displacement histogram of the terms (plan table, transformed).
-// An on-chip 2D FFT (Stockham, mixed radix 3/4/8, ping-pong between two
+// An on-chip 2D FFT (Stockham, mixed radix 4/6/8, ping-pong between two
 // N x (N+1) complex buffers) gives K * f for the whole cell; the pair loop
 // then only sums the gain 2 c_e W_e W_{e^perp} -- no P buffer, no barrier.
 
@@ -566,7 +566,7 @@ template <typename C, int N, int LD, bool INV, bool COLS, int KH = 0, int SUB = 
 __device__ __forceinline__ C* fft_lines(C* a, C* b, const C* tw, const decltype(C::x)* kh = nullptr,
                                         const decltype(C::x)* dw = nullptr) {
     if constexpr (N == 64) return fft_passes<C, N, LD, INV, COLS, KH, SUB, 1, 8, 8>(a, b, tw, kh, dw);
-    else if constexpr (N == 48) return fft_passes<C, N, LD, INV, COLS, KH, SUB, 1, 3, 4, 4>(a, b, tw, kh, dw);
+    else if constexpr (N == 48) return fft_passes<C, N, LD, INV, COLS, KH, SUB, 1, 6, 8>(a, b, tw, kh, dw);
     else if constexpr (N == 32) return fft_passes<C, N, LD, INV, COLS, KH, SUB, 1, 4, 8>(a, b, tw, kh, dw);
     else return fft_passes<C, N, LD, INV, COLS, KH, SUB, 1, 4, 4>(a, b, tw, kh, dw);  // N == 16
 }
@@ -612,7 +612,7 @@ template <typename C, int N, int LD, typename Mul>
 __device__ __forceinline__ C* ifft2_from(const C* F, C* A, C* B, const C* tw, Mul mul) {
     C* r;
     if constexpr (N == 64) r = icols_from<C, N, LD, 8, 8>(F, A, B, tw, mul);
-    else if constexpr (N == 48) r = icols_from<C, N, LD, 3, 4, 4>(F, A, B, tw, mul);
+    else if constexpr (N == 48) r = icols_from<C, N, LD, 6, 8>(F, A, B, tw, mul);
     else if constexpr (N == 32) r = icols_from<C, N, LD, 4, 8>(F, A, B, tw, mul);
     else r = icols_from<C, N, LD, 4, 4>(F, A, B, tw, mul);  // N == 16
     return fft_lines<C, N, LD, true, false>(r, r == A ? B : A, tw);
