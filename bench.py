@@ -1048,11 +1048,14 @@ def run_gpu_workload(args):
         fs = [torch.tensor(b.f, dtype=torch.float32, device=dev) for _ in range(rot)]
         ats = [torch.tensor(a_np, dtype=torch.float32, device=dev) for _ in range(rot)]
         outs = [torch.empty_like(fs[0]) for _ in range(rot)]
-        # room for both forward evaluators (line engine, FFT loss) and the derivatives
+        # room for both forward evaluators (line engine, FFT loss), the
+        # derivatives and every line-chunk count the autotuner tries (up to 16)
         wsb = []
         for fft in (0, 1):
-            plan.set_tuning(loss_fft=fft)
-            wsb.append(q.batched_workspace_bytes([plan], b.n_cells, "f32"))
+            for ch in (0, 16):
+                plan.set_tuning(loss_fft=fft, line_chunks=ch)
+                wsb.append(q.batched_workspace_bytes([plan], b.n_cells, "f32"))
+        plan.set_tuning(line_chunks=0)
         ws = torch.empty(2 * max(wsb), dtype=torch.uint8, device=dev)
         plan.set_tuning(loss_fft=1 if args.loss_fft is None else args.loss_fft)
         if wl == "batch3d":

@@ -222,7 +222,7 @@ extern "C" qdvm_status qdvm_tune_batched(const qdvm_plan_t* plans, int n_plans, 
     } else {
         const qdvm_tuning fft{saved.threads, saved.direct_j, 0, 1, saved.scan_j};
         const bool f3 = use_fast3d(QDVM_MODE_FWD, b, fft, prec);
-        for (int c : {0, 1, 2, 3, 4, 6, 8}) {
+        for (int c : {0, 1, 2, 3, 4, 6, 8, 12, 16}) {
             if (engine_workspace(QDVM_MODE_FWD, b, n_cells, prec, false, c) <= ws_bytes)
                 cand.push_back(qdvm_tuning{saved.threads, saved.direct_j, c, 0, saved.scan_j});
             if (f3 && fast3d_workspace(QDVM_MODE_FWD, b, n_cells, prec, false, c) <= ws_bytes)

@@ -981,11 +981,31 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
             if (active) {
                 int pr = pb;
                 if (wax) {
+                    // W_(0,1) along the row for both points of a pair from
+                    // the segment x - H .. x + H + 1 (H + 1 aligned 8-byte
+                    // loads: a0 - H is even), the centres left out:
+                    // W(x) = v[0] + A + v[H+1] + B, W(x+1) = A + v[H] + B + v[2H+1]
+                    // with A, B the sums of v[1..H-1] and v[H+2..2H]
                     const T c2 = pair_weight<T>(P.pair_c, P.pair_c2f, pr++) * dw[N];  // dw[N] = 1 / s
                     T pp[PPT];
 #pragma unroll
-                    for (int k = 0; k < PPT; ++k) pp[k] = T(0);
-                    for (int j = 1; j <= H; ++j) vgather(pp, j);  // W_(0,1), along the row
+                    for (int m = 0; m < PPT / 2; ++m) {
+                        const C* b = reinterpret_cast<const C*>(sF + a0 - H + m * PM::R * RS);
+                        T v[2 * H + 2];
+#pragma unroll
+                        for (int t = 0; t <= H; ++t) {
+                            const C u = b[t];
+                            v[2 * t] = u.x;
+                            v[2 * t + 1] = u.y;
+                        }
+                        T A = T(0), Bs = T(0);
+#pragma unroll
+                        for (int k = 1; k < H; ++k) A += v[k];
+#pragma unroll
+                        for (int k = H + 2; k <= 2 * H; ++k) Bs += v[k];
+                        pp[2 * m] = (v[0] + A) + (v[H + 1] + Bs);
+                        pp[2 * m + 1] = (A + v[H]) + (Bs + v[2 * H + 1]);
+                    }
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) comp_add<T, KAHAN>(acc[k], cmp[k], c2 * wx[k] * pp[k]);
                 }
