@@ -8,10 +8,17 @@ size_t fused2d_smem_bytes(int N, int H, int prec, int fft) {
     size_t b = (buf_f_elems(N, H) + buf_p_elems(N, H)) * es;
     if (fft) {
         // the FFT body's layouts for the compile-time cell sizes (GeoF):
-        // without SCAN the cell with an H halo followed by the FFT buffers;
-        // with SCAN the cell with a 2H halo and the two window fields, the
-        // FFT buffers aliasing them
-        const size_t W = N + 2 * H, RS = W + (((N % 32) - (W % 32) + 32) % 32), LD = N + 1;
+        // without SCAN the cell with an H halo (with the STAIR point map of
+        // FP32 cells, XR more columns and an odd stride, largest over the
+        // CTA sizes) followed by the FFT buffers; with SCAN the cell with a
+        // 2H halo and the two window fields, the FFT buffers aliasing them
+        int xr = 0;
+        if (prec != QDVM_F64 && N == 64) xr = std::max(body_xr<float, 64, 256>(), body_xr<float, 64, 512>());
+        if (prec != QDVM_F64 && N == 32)
+            xr = std::max({body_xr<float, 32, 128>(), body_xr<float, 32, 256>(), body_xr<float, 32, 512>()});
+        const size_t W = N + 2 * H, LD = N + 1;
+        size_t RS = W + (((N % 32) - (W % 32) + 32) % 32);
+        if (xr) RS = std::max(RS, (W + xr) | 1);
         const size_t fftb = 2 * (size_t)N * LD * 2 * es;
         const size_t direct = (W * RS * es + 15) / 16 * 16 + fftb;
         const size_t scan = std::max(fftb, (buf_f_elems(N, H) * es + 15) / 16 * 16 + 2 * (size_t)N * N * es);

@@ -628,7 +628,13 @@ __device__ __forceinline__ C* ifft2_from(const C* F, C* A, C* B, const C* tw, Mu
 // (FP32 cells of 32^2 and 64^2) a thread owns pairs of neighbouring points
 // (y0 + m R, x + c), x even, c = 0, 1 (point k = 2 m + c), so that every
 // gather reads the two values of a pair with one 8-byte load; a warp's 32
-// pairs are 64 consecutive points of a row, or two rows of 32.
+// pairs are 64 consecutive points of a row, or two rows of 32.  STAIR (VEC
+// with an even number NP >= 4 of pairs per thread): the pairs of a thread
+// climb the diagonal instead, pair m at (y0 + m, x + m + c), y0 = NP g for
+// the thread's row group g, so that they lie on two lines of direction
+// (1,1), which the diagonal pair's window walks as a running sum.  Their
+// columns reach XR = NP - 1 past the row's end (read from the cell's
+// halo, taken modulo N for the FFT buffers and the output).
 template <int N, int NT, bool VEC = false>
 struct PointMap {
     static constexpr bool TILE = !VEC && N == 48 && NT == 256;
@@ -637,10 +643,16 @@ struct PointMap {
     static constexpr int PPT = TILE ? 9 : (VEC ? 2 : 1) * ((N + R - 1) / R);
     static constexpr int ACT = TILE ? NT : R * XW;  // threads that own points
     static constexpr bool PARTIAL = !TILE && (N % R) != 0;
-    __host__ __device__ static constexpr int dy(int k) { return TILE ? (k / 3) * 16 : (VEC ? (k / 2) * R : k * R); }
-    __host__ __device__ static constexpr int dx(int k) { return TILE ? (k % 3) * 16 : (VEC ? k % 2 : 0); }
+    static constexpr bool STAIR = VEC && N % R == 0 && N / R >= 4 && (N / R) % 2 == 0;
+    static constexpr int XR = STAIR ? N / R - 1 : 0;
+    __host__ __device__ static constexpr int dy(int k) {
+        return TILE ? (k / 3) * 16 : (STAIR ? k / 2 : (VEC ? (k / 2) * R : k * R));
+    }
+    __host__ __device__ static constexpr int dx(int k) {
+        return TILE ? (k % 3) * 16 : (STAIR ? k / 2 + k % 2 : (VEC ? k % 2 : 0));
+    }
     __device__ static int x0(int tid) { return TILE ? tid % 16 : (VEC ? 2 * (tid % XW) : tid % N); }
-    __device__ static int y0(int tid) { return TILE ? tid / 16 : tid / XW; }
+    __device__ static int y0(int tid) { return TILE ? tid / 16 : (STAIR ? (tid / XW) * (N / R) : tid / XW); }
 };
 
 // Layouts of the FFT body.  Without the SCAN engine: the cell with a
@@ -649,17 +661,25 @@ struct PointMap {
 // (S - 1 + 2J)|e|_inf <= 4H rows or columns across, so the cell carries a
 // 2H halo, followed by the two N x N window fields; the FFT buffers of the
 // loss phase alias both (a cell of 64^2 FP32 fits twice per SM either way).
-template <int N, int H, bool SCAN>
+// XR > 0 (the STAIR point map): XR more halo columns on the right, and an
+// odd row stride, so that a step along (1,1), RS + 1 words, keeps the
+// parity of an address and all pairs of a thread share one alignment.
+template <int N, int H, bool SCAN, int XR = 0>
 struct GeoF {
     static constexpr int HW = SCAN ? 2 * H : H;  // halo width of the cell copy
-    static constexpr int W = N + 2 * HW;
-    static constexpr int RS = W + (((N % 32) - (W % 32) + 32) % 32);
+    static constexpr int W = N + 2 * HW;         // rows (and columns without XR)
+    static constexpr int RS = XR ? ((W + XR) | 1) : W + (((N % 32) - (W % 32) + 32) % 32);
     static constexpr int LD = N + 1;
 };
 
-template <typename T, int N, int H, bool SCAN>
+template <typename T, int N, int H, bool SCAN, int XR = 0>
 __host__ __device__ constexpr size_t cell_bytes() {
-    return ((size_t)GeoF<N, H, SCAN>::W * GeoF<N, H, SCAN>::RS * sizeof(T) + 15) / 16 * 16;
+    return ((size_t)GeoF<N, H, SCAN, XR>::W * GeoF<N, H, SCAN, XR>::RS * sizeof(T) + 15) / 16 * 16;
+}
+// the extra halo columns of the FFT body's cell for NT threads (no SCAN)
+template <typename T, int N, int NT>
+__host__ __device__ constexpr int body_xr() {
+    return PointMap<N, NT, sizeof(T) == 4 && (N == 32 || N == 64)>::XR;
 }
 
 // floor(a / D) from the plan's magic number m = ceil(2^32 / D) (m = 0 for
@@ -735,19 +755,22 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
                                              double* red, const bool do_loss, const int scan_j, const bool wfft,
                                              const bool fwin = false, const bool store = true) {
     using C = typename Cplx<T>::type;
-    using G = GeoF<N, H, SCAN>;
-    constexpr int W = G::W, RS = G::RS, HW = G::HW, LD = G::LD;
     // FP32 cells of 32^2 and 64^2 without SCAN: pairs of neighbouring points
     // per thread, gathered with 8-byte loads (PointMap)
     constexpr bool VEC = !SCAN && sizeof(T) == 4 && (N == 32 || N == 64);
     using PM = PointMap<N, NT, VEC>;
-    constexpr int PPT = PM::PPT;
+    constexpr int PPT = PM::PPT, XR = PM::XR;
+    using G = GeoF<N, H, SCAN, XR>;
+    constexpr int W = G::W, RS = G::RS, HW = G::HW, LD = G::LD;
+    // the parity of a0 (x, y0 and, with an even stride, RS are even; with
+    // STAIR, RS is odd and a0 = (y0 + HW) RS + x + HW is even)
+    constexpr int A0P = PM::STAIR ? 0 : (HW & 1);
     static_assert(SUB == 0 || (SUB == NT && !SCAN), "a sub-block body is the plain FFT body");
     const int tid = SUB ? (int)(threadIdx.x % SUB) : (int)threadIdx.x;
     T* sF = reinterpret_cast<T*>(smem);
-    T* sRe = reinterpret_cast<T*>(smem + cell_bytes<T, N, H, SCAN>());
+    T* sRe = reinterpret_cast<T*>(smem + cell_bytes<T, N, H, SCAN, XR>());
     T* sRp = sRe + N * N;
-    C* A = reinterpret_cast<C*>(SCAN ? smem : smem + cell_bytes<T, N, H, SCAN>());
+    C* A = reinterpret_cast<C*>(SCAN ? smem : smem + cell_bytes<T, N, H, SCAN, XR>());
     C* B = A + N * LD;
     // with VEC: the cell shifted by one word, sS[i] = sF[i + 1], built in the
     // FFT buffers once the loss transform is done, so that a pair of points
@@ -755,7 +778,9 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
     // 8-byte load from sS
     T* sS = reinterpret_cast<T*>(A);
     static_assert(!VEC || W * RS <= 4 * N * LD, "the shifted cell fits in the FFT buffers");
-    static_assert(!VEC || (RS % 2 == 0 && (PM::R * RS) % 2 == 0), "even strides keep pairs aligned");
+    static_assert(!VEC || (PM::STAIR ? RS % 2 == 1 : (RS % 2 == 0 && (PM::R * RS) % 2 == 0)),
+                  "the strides keep the pairs of a thread at one alignment");
+    static_assert(2 * HW + XR < N, "one periodic image per axis");
     const C* tw;
     const T* kh;
     if constexpr (sizeof(T) == 8) {
@@ -769,21 +794,26 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
     const bool active = tid < PM::ACT;
     const int x = PM::x0(tid), y0 = PM::y0(tid);  // the thread's first point; point k at + (dy(k), dx(k))
     const int a0 = (y0 + HW) * RS + x + HW;
+    // the column of point k in [0, N) (a STAIR run may pass the row's end)
+    auto colk = [&](const int k) {
+        const int c = x + PM::dx(k);
+        return (PM::STAIR && c >= N) ? c - N : c;
+    };
     const bool last_ok = !PM::PARTIAL || (y0 + PM::dy(PPT - 1) < N);
     T acc[PPT], cmp[PPT];
 
     // VEC: add the values at +-off from every owned pair to arr.  The
-    // address a0 + off has the parity of HW + off (x and the strides are
-    // even): even, an aligned 8-byte load from the cell; odd, from sS.
+    // address of pair m, a0 + off + dy RS + dx, has the parity of A0P + off
+    // for every m: even, an aligned 8-byte load from the cell; odd, from sS.
     auto vgather = [&](T (&arr)[PPT], const int off) {
         if constexpr (VEC) {
-            const bool al = ((HW + off) & 1) == 0;
+            const bool al = ((A0P + off) & 1) == 0;
             const T* bp = al ? sF + a0 + off : sS + a0 + off - 1;
             const T* bm = al ? sF + a0 - off : sS + a0 - off - 1;
 #pragma unroll
             for (int m = 0; m < PPT / 2; ++m) {
-                const C u = *reinterpret_cast<const C*>(bp + m * PM::R * RS);
-                const C v = *reinterpret_cast<const C*>(bm + m * PM::R * RS);
+                const C u = *reinterpret_cast<const C*>(bp + PM::dy(2 * m) * RS + PM::dx(2 * m));
+                const C v = *reinterpret_cast<const C*>(bm + PM::dy(2 * m) * RS + PM::dx(2 * m));
                 arr[2 * m] += u.x + v.x;
                 arr[2 * m + 1] += u.y + v.y;
             }
@@ -819,6 +849,54 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
         for (int k = 0; k < PPT; ++k)
             if (k < PPT - 1 || last_ok) comp_add<T, KAHAN>(acc[k], cmp[k], c2 * w[k] * pp[k]);
     };
+    // STAIR: the gain of the diagonal pair (|e_1| = |e_2| = 1, J = H).  The
+    // thread's pairs P_0 .. P_{NP-1} lie on one run along (1,1), P_i the
+    // pair at a0 + i (RS + 1), so their windows along (1,1) come from one
+    // running sum, R_0 = P_{-H} + ... + P_H, R_m = R_{m-1} + P_{m+H} - P_{m-1-H},
+    // W_m = R_m - P_m: 2H + 2NP - 1 loads where direct gathers take 2H NP.
+    // The window along (1,-1) is gathered directly.
+    auto gain_diag = [&](const T c2) {
+        if constexpr (PM::STAIR) {
+            constexpr int NP = PPT / 2, D = RS + 1;
+            T w[PPT], pp[PPT];
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) w[k] = pp[k] = T(0);
+            for (int j = 1; j <= H; ++j) vgather(pp, j * (RS - 1));
+            auto ld = [&](const int i) { return *reinterpret_cast<const C*>(sF + a0 + i * D); };  // a0 even
+            T rx = T(0), ry = T(0);
+#pragma unroll
+            for (int i = -H; i <= H; ++i) {
+                const C u = ld(i);
+                rx += u.x;
+                ry += u.y;
+                if (i >= 0 && i < NP) {
+                    w[2 * i] -= u.x;
+                    w[2 * i + 1] -= u.y;
+                }
+            }
+            w[0] += rx;
+            w[1] += ry;
+#pragma unroll
+            for (int m = 1; m < NP; ++m) {
+                const C a = ld(m + H), b = ld(m - 1 - H);
+                rx += a.x - b.x;
+                ry += a.y - b.y;
+                if (m + H < NP) {
+                    w[2 * (m + H)] -= a.x;
+                    w[2 * (m + H) + 1] -= a.y;
+                }
+                w[2 * m] += rx;
+                w[2 * m + 1] += ry;
+            }
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) comp_add<T, KAHAN>(acc[k], cmp[k], c2 * w[k] * pp[k]);
+        }
+    };
+    // DIRECT gathers for pair e, or the running sum for the diagonal pair
+    auto gain_pair = [&](const int4 e, const T c2) {
+        if (PM::STAIR && abs(e.x) == 1 && abs(e.y) == 1 && e.z == H) gain_diag(c2);
+        else gain_direct(e, c2);
+    };
     // the loss -f (K * f) from the FFT buffers A, B (K's transform in kh);
     // fk(k) gives f at the k-th owned point.  With dw (the axis window's
     // transform, scaled by a power of two s to the size of Ktilde) the
@@ -837,7 +915,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
         if (active) {
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-                if (k < PPT - 1 || last_ok) acc[k] = -fk(k) * r[(y0 + PM::dy(k)) * LD + x + PM::dx(k)].x;
+                if (k < PPT - 1 || last_ok) acc[k] = -fk(k) * r[(y0 + PM::dy(k)) * LD + colk(k)].x;
             }
         }
         return static_cast<const C*>(r);
@@ -849,7 +927,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
         T w[PPT], pp[PPT];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-            w[k] = (k < PPT - 1 || last_ok) ? rw[(y0 + PM::dy(k)) * LD + x + PM::dx(k)].y : T(0);
+            w[k] = (k < PPT - 1 || last_ok) ? rw[(y0 + PM::dy(k)) * LD + colk(k)].y : T(0);
             pp[k] = T(0);
         }
         for (int j = 1; j <= H; ++j) {
@@ -864,15 +942,16 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
         for (int k = 0; k < PPT; ++k)
             if (k < PPT - 1 || last_ok) comp_add<T, KAHAN>(acc[k], cmp[k], c2 * w[k] * pp[k]);
     };
-    // The cell copy with its periodic halo of width HW (2 HW < N, so a point
-    // has at most one image per axis), and optionally the FFT input: the N^2
+    // The cell copy with its periodic halo of width HW, XR more columns on
+    // the right (2 HW + XR < N, so a point has at most one image per axis),
+    // and optionally the FFT input: the N^2
     // points are read once; consecutive threads take consecutive points, so
     // a warp's loads are coalesced and its stores hit distinct banks.
     auto fill_cell = [&](const bool fft_in) {
         auto put = [&](const int y, const int x, const T v) {
             const int a = (y + HW) * RS + x + HW;
             const int dy = y < HW ? N * RS : (y >= N - HW ? -N * RS : 0);
-            const int dx = x < HW ? N : (x >= N - HW ? -N : 0);
+            const int dx = x < HW + XR ? N : (x >= N - HW ? -N : 0);
             sF[a] = v;
             if (dy) sF[a + dy] = v;
             if (dx) sF[a + dx] = v;
@@ -891,7 +970,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
             if constexpr (sizeof(T) == 8) djt = P.dj;
             else djt = P.dj_f;
             C* F = reinterpret_cast<C*>(smem);
-            static_assert((size_t)N * LD * sizeof(C) <= cell_bytes<T, N, H, false>(), "fhat fits in the cell's place");
+            static_assert((size_t)N * LD * sizeof(C) <= cell_bytes<T, N, H, false, XR>(), "fhat fits in the cell's place");
             for (int i = tid; i < N * N; i += NT) A[(i / N) * LD + (i % N)] = C{fcell[i], T(0)};
             __syncthreads();
             C* r = fft_lines<C, N, LD, false, false>(A, B, tw);
@@ -917,7 +996,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
                         if (k < PPT - 1 || last_ok) {
-                            const C w = q[(y0 + PM::dy(k)) * LD + x + PM::dx(k)];
+                            const C w = q[(y0 + PM::dy(k)) * LD + colk(k)];
                             comp_add<T, KAHAN>(acc[k], cmp[k], c2 * w.x * w.y);
                         }
                     }
@@ -936,7 +1015,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
                 for (int k = 0; k < PPT; ++k)
                     if (k < PPT - 1 || last_ok)
                         comp_add<T, KAHAN>(acc[k], cmp[k],
-                                           -sF[a0 + PM::dy(k) * RS + PM::dx(k)] * q[(y0 + PM::dy(k)) * LD + x + PM::dx(k)].x);
+                                           -sF[a0 + PM::dy(k) * RS + PM::dx(k)] * q[(y0 + PM::dy(k)) * LD + colk(k)].x);
             }
             if constexpr (VEC) {
                 __syncthreads();  // the loss result is read: the FFT buffers take the shifted cell
@@ -946,7 +1025,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
             if (active)
                 for (int pr = pb; pr < pe; ++pr) {
                     const int4 e = P.pairs[pr];
-                    if (e.z < scan_j) gain_direct(e, pair_weight<T>(P.pair_c, P.pair_c2f, pr));
+                    if (e.z < scan_j) gain_pair(e, pair_weight<T>(P.pair_c, P.pair_c2f, pr));
                 }
         } else {
         fill_cell(do_loss);
@@ -974,7 +1053,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
             // s W_(1,0) leaves the FFT buffers before they take the shifted cell
             T wx[PPT];
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) wx[k] = (wax && active) ? rw[(y0 + PM::dy(k)) * LD + x + PM::dx(k)].y : T(0);
+            for (int k = 0; k < PPT; ++k) wx[k] = (wax && active) ? rw[(y0 + PM::dy(k)) * LD + colk(k)].y : T(0);
             __syncthreads();
             for (int i = tid; i < W * RS - 1; i += NT) sS[i] = sF[i + 1];
             __syncthreads();
@@ -983,14 +1062,15 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
                 if (wax) {
                     // W_(0,1) along the row for both points of a pair from
                     // the segment x - H .. x + H + 1 (H + 1 aligned 8-byte
-                    // loads: a0 - H is even), the centres left out:
+                    // loads, from sS when a0 - H is odd), the centres left out:
                     // W(x) = v[0] + A + v[H+1] + B, W(x+1) = A + v[H] + B + v[2H+1]
                     // with A, B the sums of v[1..H-1] and v[H+2..2H]
                     const T c2 = pair_weight<T>(P.pair_c, P.pair_c2f, pr++) * dw[N];  // dw[N] = 1 / s
+                    const T* sb = ((A0P - H) & 1) ? sS + a0 - H - 1 : sF + a0 - H;
                     T pp[PPT];
 #pragma unroll
                     for (int m = 0; m < PPT / 2; ++m) {
-                        const C* b = reinterpret_cast<const C*>(sF + a0 - H + m * PM::R * RS);
+                        const C* b = reinterpret_cast<const C*>(sb + PM::dy(2 * m) * RS + PM::dx(2 * m));
                         T v[2 * H + 2];
 #pragma unroll
                         for (int t = 0; t <= H; ++t) {
@@ -1009,7 +1089,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) comp_add<T, KAHAN>(acc[k], cmp[k], c2 * wx[k] * pp[k]);
                 }
-                for (; pr < pe; ++pr) gain_direct(P.pairs[pr], pair_weight<T>(P.pair_c, P.pair_c2f, pr));
+                for (; pr < pe; ++pr) gain_pair(P.pairs[pr], pair_weight<T>(P.pair_c, P.pair_c2f, pr));
             }
         } else if (active) {
             int pr = pb;
@@ -1055,7 +1135,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
 #pragma unroll
                 for (int k = 0; k < PPT; ++k)
                     if (k < PPT - 1 || last_ok)
-                        wf[h0 + PM::dy(k) * N + PM::dx(k)] = r[(y0 + PM::dy(k)) * LD + x + PM::dx(k)].y;
+                        wf[h0 + PM::dy(k) * N + PM::dx(k)] = r[(y0 + PM::dy(k)) * LD + colk(k)].y;
             }
             __syncthreads();
         }
@@ -1119,7 +1199,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
             if (k < PPT - 1 || last_ok) {
-                const int y = y0 + PM::dy(k), xk = x + PM::dx(k);
+                const int y = y0 + PM::dy(k), xk = colk(k);
                 const T q = KAHAN ? acc[k] + cmp[k] : acc[k];
                 if (store) qcell[y * N + xk] = q;
                 if (mom) cm.add(q, y, xk);
@@ -1227,14 +1307,15 @@ __host__ __device__ constexpr int cell_groups(const int N, const int Nt, const b
     if (!(NT == 256 && sizeof(T) == 4 && khat && (fft == 1 || fft == 2) && !(sj > 0 && sj <= Nt))) return 0;
     return (N == 16 && Nt == 3) ? 4 : ((N == 32 && Nt == 7) ? 2 : 0);
 }
-// shared memory of one cell of a group, 128-byte aligned
-template <typename T, int N, int H>
+// shared memory of one cell of a group of NT threads, 128-byte aligned
+template <typename T, int N, int H, int NT>
 __host__ __device__ constexpr size_t group_cell_bytes() {
-    return (cell_bytes<T, N, H, false>() + 2 * (size_t)N * (N + 1) * sizeof(typename Cplx<T>::type) + 127) / 128 * 128;
+    return (cell_bytes<T, N, H, false, body_xr<T, N, NT>()>() + 2 * (size_t)N * (N + 1) * sizeof(typename Cplx<T>::type) +
+            127) / 128 * 128;
 }
 template <typename T>
 __host__ __device__ constexpr size_t group_smem_bytes(const int G) {
-    return G == 4 ? 4 * group_cell_bytes<T, 16, 3>() : (G == 2 ? 2 * group_cell_bytes<T, 32, 7>() : 0);
+    return G == 4 ? 4 * group_cell_bytes<T, 16, 3, 64>() : (G == 2 ? 2 * group_cell_bytes<T, 32, 7, 128>() : 0);
 }
 
 // One pass of the group body: thread group g (NT / G threads) evaluates cell
@@ -1252,7 +1333,7 @@ __device__ __forceinline__ void group_pass(const PlanDev& P, const int cg, const
     const int64_t offg = cell_offset[src];
     fftloss_body<T, KAHAN, N, H, SUBT, false, SUBT>(P, 0, P.n_pairs, f + offg, Q + offg,
                                                     moments ? moments + (size_t)src * 4 : nullptr,
-                                                    smem_raw + g * group_cell_bytes<T, N, H>(), red + g * (128 / G),
+                                                    smem_raw + g * group_cell_bytes<T, N, H, SUBT>(), red + g * (128 / G),
                                                     true, 0, P.tfft == 2, false, mine);
     __syncthreads();
 }
