@@ -58,6 +58,30 @@ qdvm_status fused2d_eval_single(const qdvm_plan_s* p, const void* f, void* Q, in
     }
 }
 
+// Shared memory of the batched evaluator's CTA for one plan: the layout of
+// the FFT body (body_smem) for the cell sizes it is compiled for, when the
+// plan runs it (loss_fft set, the loss kernel's transform present); the
+// buffers of the line-engine body otherwise.
+static size_t batched_plan_smem(const PlanDev& p, int prec, int threads) {
+    const int N = p.N, H = p.Ntilde, fft = p.tfft, sj = p.tsj;
+    if (fft && p.khat) {
+#define QDVM_BODY_SMEM(NN, HH)                                                                       \
+    if (N == NN && H == HH) {                                                                        \
+        if (prec == QDVM_F64)                                                                        \
+            return threads == 512 ? body_smem<double, NN, HH, 512>(fft, sj)                          \
+                                  : body_smem<double, NN, HH, 256>(fft, sj);                         \
+        return threads == 512 ? body_smem<float, NN, HH, 512>(fft, sj) : body_smem<float, NN, HH, 256>(fft, sj); \
+    }
+        QDVM_BODY_SMEM(64, 14)
+        QDVM_BODY_SMEM(48, 10)
+        QDVM_BODY_SMEM(32, 7)
+        QDVM_BODY_SMEM(16, 3)
+#undef QDVM_BODY_SMEM
+    }
+    const size_t es = prec == QDVM_F64 ? sizeof(double) : sizeof(float);
+    return (buf_f_elems(N, H) + buf_p_elems(N, H)) * es;
+}
+
 qdvm_status fused2d_eval_batched(const BatchDev& b, const qdvm_tuning& tu, int n_cells, const int* cell_plan,
                                  const int64_t* cell_offset, const void* f, void* Q, double* moments, int prec,
                                  void* ws, cudaStream_t st) {
@@ -70,7 +94,7 @@ qdvm_status fused2d_eval_batched(const BatchDev& b, const qdvm_tuning& tu, int n
     // block size is tu's
     size_t smem = 0;
     for (int i = 0; i < b.n_plans; ++i) {
-        smem = std::max(smem, fused2d_smem_bytes(b.p[i].N, b.p[i].Ntilde, prec, b.p[i].tfft));
+        smem = std::max(smem, batched_plan_smem(b.p[i], prec, tu.threads));
         // small FP32 cells go several at a time on 256 threads (cell_groups)
         if (prec != QDVM_F64 && tu.threads == 256)
             smem = std::max(smem, group_smem_bytes<float>(cell_groups<float, 256>(

@@ -767,17 +767,24 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
     constexpr int A0P = PM::STAIR ? 0 : (HW & 1);
     static_assert(SUB == 0 || (SUB == NT && !SCAN), "a sub-block body is the plain FFT body");
     const int tid = SUB ? (int)(threadIdx.x % SUB) : (int)threadIdx.x;
+    // with VEC: the cell shifted by one word, sS[i] = sF[i + 1], so that a
+    // pair of points whose gather address is odd loads its two values with
+    // one aligned 8-byte load from sS.  VEC without the FFT window engine
+    // (late): the cell and sS are written after the loss transform, from the
+    // f values each thread holds in registers, so that they alias the FFT
+    // buffers (sF and A at 0, sS at the cell's size, B at N LD complex;
+    // body_smem).  Otherwise the FFT buffers follow the cell, and sS (VEC)
+    // takes their place once the loss transform is done.
+    constexpr size_t CB = cell_bytes<T, N, H, SCAN, XR>();
+    const bool late = VEC && !fwin;
     T* sF = reinterpret_cast<T*>(smem);
-    T* sRe = reinterpret_cast<T*>(smem + cell_bytes<T, N, H, SCAN, XR>());
+    T* sRe = reinterpret_cast<T*>(smem + CB);
     T* sRp = sRe + N * N;
-    C* A = reinterpret_cast<C*>(SCAN ? smem : smem + cell_bytes<T, N, H, SCAN, XR>());
+    C* A = reinterpret_cast<C*>((SCAN || late) ? smem : smem + CB);
     C* B = A + N * LD;
-    // with VEC: the cell shifted by one word, sS[i] = sF[i + 1], built in the
-    // FFT buffers once the loss transform is done, so that a pair of points
-    // whose gather address is odd loads its two values with one aligned
-    // 8-byte load from sS
-    T* sS = reinterpret_cast<T*>(A);
+    T* sS = late ? reinterpret_cast<T*>(smem + CB) : reinterpret_cast<T*>(A);
     static_assert(!VEC || W * RS <= 4 * N * LD, "the shifted cell fits in the FFT buffers");
+    static_assert(!VEC || (N * N) % NT == 0, "the cell's points split evenly over the threads");
     static_assert(!VEC || (PM::STAIR ? RS % 2 == 1 : (RS % 2 == 0 && (PM::R * RS) % 2 == 0)),
                   "the strides keep the pairs of a thread at one alignment");
     static_assert(2 * HW + XR < N, "one periodic image per axis");
@@ -959,7 +966,35 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
             if (fft_in) A[y * LD + x] = C{v, T(0)};
         };
 #pragma unroll 4
-        for (int i = tid; i < N * N; i += NT) put(i / N, i % N, fcell[i]);
+        for (int i = tid; i < N * N; i += NT) put(i / N, i % N, __ldcs(fcell + i));
+    };
+    // late: the cell and sS from the values fv[r] of the points tid + r NT
+    // (every image a of a point also goes to sS[a - 1]; a = 0, possible for
+    // a corner image only, has no place in sS and is never read from there)
+    constexpr int NFV = VEC ? N * N / NT : 1;
+    auto fill_late = [&](const T (&fv)[NFV]) {
+#pragma unroll
+        for (int r = 0; r < NFV; ++r) {
+            const int i = tid + r * NT, y = i / N, x = i % N;
+            const int a = (y + HW) * RS + x + HW;
+            const int dy = y < HW ? N * RS : (y >= N - HW ? -N * RS : 0);
+            const int dx = x < HW + XR ? N : (x >= N - HW ? -N : 0);
+            const T v = fv[r];
+            sF[a] = v;
+            sS[a - 1] = v;
+            if (dy) {
+                sF[a + dy] = v;
+                sS[a + dy - 1] = v;
+            }
+            if (dx) {
+                sF[a + dx] = v;
+                sS[a + dx - 1] = v;
+            }
+            if (dy && dx) {
+                sF[a + dy + dx] = v;
+                if (a + dy + dx > 0) sS[a + dy + dx - 1] = v;
+            }
+        }
     };
 
     if constexpr (!SCAN) {
@@ -1028,7 +1063,19 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
                     if (e.z < scan_j) gain_pair(e, pair_weight<T>(P.pair_c, P.pair_c2f, pr));
                 }
         } else {
-        fill_cell(do_loss);
+        // VEC (late): f into registers and the FFT input; the cell follows
+        // the transform.  Otherwise the cell and the FFT input at once.
+        T fv[NFV];
+        if constexpr (VEC) {
+#pragma unroll
+            for (int r = 0; r < NFV; ++r) {
+                const int i = tid + r * NT;
+                fv[r] = __ldcs(fcell + i);
+                if (do_loss) A[(i / N) * LD + i % N] = C{fv[r], T(0)};
+            }
+        } else {
+            fill_cell(do_loss);
+        }
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
@@ -1047,16 +1094,24 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
             if constexpr (sizeof(T) == 8) dw = P.dwin;
             else dw = P.dwin_f;
         }
+        // VEC: the loss leaves the transform as -(K * f), to be multiplied by
+        // f at the owned points once the cell is in place
         const C* rw = nullptr;
-        if (do_loss) rw = loss_fft([&](int k) { return sF[a0 + PM::dy(k) * RS + PM::dx(k)]; }, dw);
+        if (do_loss)
+            rw = loss_fft([&](int k) { return VEC ? T(1) : sF[a0 + PM::dy(k) * RS + PM::dx(k)]; }, dw);
         if constexpr (VEC) {
-            // s W_(1,0) leaves the FFT buffers before they take the shifted cell
+            // s W_(1,0) leaves the FFT buffers before they take the cell and sS
             T wx[PPT];
 #pragma unroll
             for (int k = 0; k < PPT; ++k) wx[k] = (wax && active) ? rw[(y0 + PM::dy(k)) * LD + colk(k)].y : T(0);
             __syncthreads();
-            for (int i = tid; i < W * RS - 1; i += NT) sS[i] = sF[i + 1];
+            fill_late(fv);
             __syncthreads();
+            if (do_loss && active) {
+#pragma unroll
+                for (int k = 0; k < PPT; ++k)
+                    if (k < PPT - 1 || last_ok) acc[k] *= sF[a0 + PM::dy(k) * RS + PM::dx(k)];
+            }
             if (active) {
                 int pr = pb;
                 if (wax) {
@@ -1201,7 +1256,7 @@ __device__ __forceinline__ void fftloss_body(const PlanDev& P, const int pb, con
             if (k < PPT - 1 || last_ok) {
                 const int y = y0 + PM::dy(k), xk = colk(k);
                 const T q = KAHAN ? acc[k] + cmp[k] : acc[k];
-                if (store) qcell[y * N + xk] = q;
+                if (store) __stcs(qcell + y * N + xk, q);
                 if (mom) cm.add(q, y, xk);
             }
         }
@@ -1307,11 +1362,28 @@ __host__ __device__ constexpr int cell_groups(const int N, const int Nt, const b
     if (!(NT == 256 && sizeof(T) == 4 && khat && (fft == 1 || fft == 2) && !(sj > 0 && sj <= Nt))) return 0;
     return (N == 16 && Nt == 3) ? 4 : ((N == 32 && Nt == 7) ? 2 : 0);
 }
+// Shared memory of the FFT body (fftloss_body) of an N^2 cell on NT threads
+// for the tuning fft (loss_fft) and sj (scan_j): with SCAN the cell with a
+// 2H halo and the two window fields, the FFT buffers aliasing them; with
+// paired points (FP32, 32^2 and 64^2) and no FFT window engine the larger of
+// the cell with its shifted copy and the FFT buffers, which alias; else the
+// cell followed by the FFT buffers (also with the FFT window engine, fft = 3,
+// whose threshold sj is).
+template <typename T, int N, int H, int NT>
+__host__ __device__ constexpr size_t body_smem(const int fft, const int sj) {
+    constexpr size_t fftb = 2 * (size_t)N * (N + 1) * sizeof(typename Cplx<T>::type);
+    constexpr size_t cb = cell_bytes<T, N, H, false, body_xr<T, N, NT>()>();
+    constexpr size_t cs = cell_bytes<T, N, H, true>() + 2 * (size_t)N * N * sizeof(T);
+    constexpr bool vec = sizeof(T) == 4 && (N == 32 || N == 64);
+    if (fft == 3) return cb + fftb;  // sj is the FFT window threshold here
+    if (sj > 0 && sj <= H) return cs > fftb ? cs : fftb;
+    if (vec) return 2 * cb > fftb ? 2 * cb : fftb;
+    return cb + fftb;
+}
 // shared memory of one cell of a group of NT threads, 128-byte aligned
 template <typename T, int N, int H, int NT>
 __host__ __device__ constexpr size_t group_cell_bytes() {
-    return (cell_bytes<T, N, H, false, body_xr<T, N, NT>()>() + 2 * (size_t)N * (N + 1) * sizeof(typename Cplx<T>::type) +
-            127) / 128 * 128;
+    return (body_smem<T, N, H, NT>(2, 0) + 127) / 128 * 128;
 }
 template <typename T>
 __host__ __device__ constexpr size_t group_smem_bytes(const int G) {
