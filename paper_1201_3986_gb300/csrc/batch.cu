@@ -7,70 +7,94 @@
 
 namespace {
 
-__device__ int block_excl_scan(int x, int* total) {
-    __shared__ int ws[32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int incl = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) ws[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-        int s = lane < nw ? ws[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, s, o);
-            if (lane >= o) s += y;
+// Single block of 1024 threads (32 warps): order = cells grouped by plan,
+// plans by decreasing cost (N^d x lines), cells ascending within a plan;
+// cells with an out-of-range plan index are left out and the tail of order
+// is filled with -1.  Also resets the work counter of the persistent
+// kernels.  Two passes over cell_plan, whatever the number of plans: first
+// the cells of every plan (one warp ballot per plan and 32 cells), then, per
+// chunk of 1024 cells, each cell's place = its plan's next free place + the
+// plan's cells in the chunk's earlier warps + its rank among its warp's
+// cells of that plan.
+__global__ void __launch_bounds__(1024) k_schedule(BatchDev B, int n_cells, const int* __restrict__ cell_plan,
+                                                   int* __restrict__ order, int* __restrict__ counter) {
+    constexpr int NP = QDVM_MAX_BATCH_PLANS;
+    __shared__ int s_wc[32][NP];  // per warp and plan: cells (pass 1: all chunks; pass 2: this chunk, then places)
+    __shared__ int s_base[NP];    // each plan's next free place in order
+    __shared__ int s_total;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, np = B.n_plans;
+    const unsigned lt = (1u << lane) - 1u;
+    int cnt = 0;  // lane r < np: cells of plan r seen by this warp
+    for (int c0 = 0; c0 < n_cells; c0 += 1024) {
+        const int i = c0 + threadIdx.x;
+        const int q = i < n_cells ? cell_plan[i] : -1;
+        for (int r = 0; r < np; ++r) {
+            const unsigned m = __ballot_sync(0xffffffffu, q == r);
+            if (lane == r) cnt += __popc(m);
         }
-        if (lane < nw) ws[lane] = s;
+    }
+    if (lane < NP) s_wc[wid][lane] = cnt;
+    __syncthreads();
+    if (wid < np) {  // warp r: the cells of plan r over all warps
+        int v = s_wc[lane][wid];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_base[wid] = v;  // the count for now
     }
     __syncthreads();
-    const int base = wid > 0 ? ws[wid - 1] : 0;
-    *total = ws[nw - 1];
-    __syncthreads();
-    return base + incl - x;
-}
-
-// Single block: order = cells grouped by plan, plans by decreasing cost
-// (N^d x lines), cells ascending within a plan; cells with an out-of-range
-// plan index are left out and the tail of order is filled with -1.  Also
-// resets the work counter of the persistent kernels.
-__global__ void k_schedule(BatchDev B, int n_cells, const int* __restrict__ cell_plan, int* __restrict__ order,
-                           int* __restrict__ counter) {
-    __shared__ int rank_plan[QDVM_MAX_BATCH_PLANS];
     if (threadIdx.x == 0) {
-        double cost[QDVM_MAX_BATCH_PLANS];
-        for (int q = 0; q < B.n_plans; ++q) {
+        double cost[NP];
+        int rank_plan[NP];
+        for (int q = 0; q < np; ++q) {
             double nd = 1.0;
             for (int a = 0; a < B.p[q].d; ++a) nd *= B.p[q].N;
             cost[q] = nd * (double)B.p[q].n_lines;
             rank_plan[q] = q;
         }
-        for (int i = 1; i < B.n_plans; ++i)  // insertion sort, stable, descending
+        for (int i = 1; i < np; ++i)  // insertion sort, stable, descending
             for (int j = i; j > 0 && cost[rank_plan[j]] > cost[rank_plan[j - 1]]; --j) {
-                int t = rank_plan[j];
+                const int t = rank_plan[j];
                 rank_plan[j] = rank_plan[j - 1];
                 rank_plan[j - 1] = t;
             }
+        int base = 0;
+        for (int k = 0; k < np; ++k) {
+            const int q = rank_plan[k], c = s_base[q];
+            s_base[q] = base;
+            base += c;
+        }
+        s_total = base;
         *counter = 0;
     }
     __syncthreads();
-    int base = 0;
-    for (int r = 0; r < B.n_plans; ++r) {
-        const int q = rank_plan[r];
-        for (int c0 = 0; c0 < n_cells; c0 += blockDim.x) {
-            const int i = c0 + threadIdx.x;
-            const bool ok = i < n_cells && cell_plan[i] == q;
-            int tot;
-            const int pos = block_excl_scan(ok ? 1 : 0, &tot);
-            if (ok) order[base + pos] = i;
-            base += tot;
+    for (int c0 = 0; c0 < n_cells; c0 += 1024) {
+        const int i = c0 + threadIdx.x;
+        const int q = i < n_cells ? cell_plan[i] : -1;
+        int rank = 0;
+        for (int r = 0; r < np; ++r) {
+            const unsigned m = __ballot_sync(0xffffffffu, q == r);
+            if (q == r) rank = __popc(m & lt);
+            if (lane == r) s_wc[wid][r] = __popc(m);
         }
+        __syncthreads();
+        if (wid < np) {  // warp r: exclusive scan of plan r's counts over the warps
+            const int v = s_wc[lane][wid];
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int b = s_base[wid];
+            s_wc[lane][wid] = b + incl - v;
+            __syncwarp();
+            if (lane == 31) s_base[wid] = b + incl;
+        }
+        __syncthreads();
+        if (q >= 0 && q < np) order[s_wc[wid][q] + rank] = i;
+        __syncthreads();
     }
-    for (int i = base + threadIdx.x; i < n_cells; i += blockDim.x) order[i] = -1;
+    for (int i = s_total + threadIdx.x; i < n_cells; i += blockDim.x) order[i] = -1;
 }
 
 template <typename T>
