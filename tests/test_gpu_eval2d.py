@@ -390,3 +390,31 @@ def test_batched_results_repeat_bit_for_bit(q, torch):
     runs = [q.qdvm_eval_batched(plans, cp, co, f, "f32_kahan") for _ in range(3)]
     for Q, M in runs[1:]:
         assert torch.equal(Q, runs[0][0]) and torch.equal(M, runs[0][1])
+
+
+def test_schedule_order(q, torch):
+    """The order in which the persistent evaluator draws cells, read back from
+    the workspace (a 256-byte counter, then one int per cell): plans by
+    decreasing cost (N^2 x lines, ties by plan index), cells ascending within
+    a plan, out-of-range plan indices left out, the tail -1.  5000 cells (more
+    chunks of 1024 than the schedule keeps in registers), five plans, the
+    indices -1 and 5 mixed in."""
+    Ns = (8, 12, 16, 10, 14)
+    plans = [q.Plan(2, n, 2, 8.0) for n in Ns]
+    rng = np.random.default_rng(11)
+    n_cells = 5000
+    cpn = rng.integers(-1, len(Ns) + 1, size=n_cells).astype(np.int32)
+    sizes = np.array([Ns[c] ** 2 if 0 <= c < len(Ns) else 64 for c in cpn], dtype=np.int64)
+    offs = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    f = torch.rand(int(sizes.sum()), dtype=torch.float32, device="cuda")
+    cp = torch.tensor(cpn, device="cuda")
+    co = torch.tensor(offs, device="cuda")
+    ws = torch.zeros(q.batched_workspace_bytes(plans, n_cells, "f32"), dtype=torch.uint8, device="cuda")
+    q.qdvm_eval_batched(plans, cp, co, f, "f32", moments=False, workspace=ws)
+    torch.cuda.synchronize()
+    order = ws[256:256 + 4 * n_cells].view(torch.int32).cpu().numpy()
+    cost = [p.N ** 2 * p.n_lines for p in plans]
+    rank = sorted(range(len(plans)), key=lambda k: -cost[k])
+    ref = [i for k in rank for i in range(n_cells) if cpn[i] == k]
+    ref = np.array(ref + [-1] * (n_cells - len(ref)), dtype=np.int32)
+    assert np.array_equal(order, ref)
